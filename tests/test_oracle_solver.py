@@ -1,0 +1,280 @@
+"""Pins of the oracle's time stepper: conservation across interfaces, reductions to uniform
+grids, closed-form decay and sound speed, the level schedule, and the Sod exact solution."""
+import numpy as np
+import pytest
+
+from oracle import grid as G
+from oracle import lattices as L
+from oracle import solver as S
+from paper_2504_04465_b300 import inputs as I
+
+from .riemann import sample
+
+
+def _tg_solver(lat, model, coarse_n, lo, hi, nl, nu_c, u0=0.05):
+    spec = I.taylor_green_spec(coarse_n, lo, hi, nl)
+    g = G.build(spec, lat)
+    s = S.Solver(g, model, nu0=nu_c * 2 ** (nl - 1))
+    fields = []
+    for lv in g.levels:
+        c = I.cell_centres(lv.coords, lv.level)
+        rho, u = I.taylor_green_fields(c, coarse_n, nl, u0, lat.cs2)
+        fields.append((rho, u, None))
+    s.init_fields(fields)
+    return s
+
+
+def _smooth_comp_solver(latname, model, T0, spec, A=1.5):
+    lat = L.LATTICES[latname]
+    g = G.build(spec, lat)
+    s = S.Solver(g, model, nu0=0.01, T0=T0, sensor_A=A)
+    fields = []
+    ext = np.array(spec.extent, float)
+    for lv in g.levels:
+        c = I.cell_centres(lv.coords, lv.level)
+        rho = 1 + 0.1 * np.exp(-((c - ext / 2) ** 2).sum(1) / 64)
+        u = np.stack([0.1 + 0 * rho, 0.05 * np.sin(2 * np.pi * c[:, 0] / ext[0])])
+        T = s.T0 * (1 + 0.05 * np.cos(2 * np.pi * c[:, 1] / ext[1]))
+        fields.append((rho, u, T))
+    s.init_fields(fields)
+    return s
+
+
+@pytest.mark.parametrize("model", ["bgk", "rr"])
+@pytest.mark.parametrize("nl,lo,hi", [(2, 8, 24), (3, 8, 24)])
+def test_ledger_weak_d2q9(model, nl, lo, hi):
+    lat = L.D2Q9
+    spec = I.taylor_green_spec(32, lo, hi, nl)
+    if nl == 3:   # a level-0 box inside the level-1 box
+        spec.boxes.append((0, (12 * 4, 12 * 4), (20 * 4, 20 * 4)))
+    g = G.build(spec, lat)
+    s = S.Solver(g, model, nu0=0.02 * 2 ** (nl - 1))
+    fields = []
+    for lv in g.levels:
+        c = I.cell_centres(lv.coords, lv.level)
+        rho, u = I.taylor_green_fields(c, 32, nl, 0.05, lat.cs2)
+        u = u + 0.01 * np.stack([I.uniform_at(7, lv.level, lv.coords, k) for k in range(2)])
+        fields.append((rho, u, None))
+    s.init_fields(fields)
+    l0 = s.ledger()
+    for _ in range(100 if nl == 2 else 40):
+        s.step_coarse(1)
+    l1 = s.ledger()
+    assert abs(l1[0] - l0[0]) < 1e-13 * l0[0]
+    assert np.abs(l1[1:3] - l0[1:3]).max() < 1e-13 * l0[0]
+    # a perturbation of the coupling breaks it (the pin is sensitive): drop the 1/N_f
+    s2 = S.Solver(g, model, nu0=0.02 * 2 ** (nl - 1))
+    s2.init_fields(fields)
+    orig = s2._coalesced
+
+    def bad(lev):
+        f, gg, lam = orig(lev)
+        return f * 1.0001, gg, lam
+    s2._coalesced = bad
+    l0 = s2.ledger()
+    s2.step_coarse(3)
+    assert abs(s2.ledger()[0] - l0[0]) > 1e-9 * l0[0]
+
+
+def test_ledger_d3q27_rr():
+    lat = L.D3Q27
+    spec = I.GridSpec(3, (32, 32, 32), 2, [(0, (8, 8, 8), (24, 24, 20))], (True, True, True))
+    g = G.build(spec, lat)
+    s = S.Solver(g, "rr", nu0=0.02)
+    fields = []
+    for lv in g.levels:
+        u = 0.03 * np.stack([I.uniform_at(3900, lv.level, lv.coords, k) for k in range(3)])
+        rho = 1 + 0.01 * I.uniform_at(3900, lv.level, lv.coords, 5)
+        fields.append((rho, u, None))
+    s.init_fields(fields)
+    l0 = s.ledger()
+    s.step_coarse(10)
+    l1 = s.ledger()
+    assert abs(l1[0] - l0[0]) < 1e-13 * l0[0]
+    assert np.abs(l1[1:4] - l0[1:4]).max() < 1e-13 * l0[0]
+
+
+@pytest.mark.parametrize("latname,model,T0", [("D2Q37", "poly_ddf", None), ("D2Q21", "num_ddf", 0.9)])
+def test_ledger_compressible(latname, model, T0):
+    spec = I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True))
+    s = _smooth_comp_solver(latname, model, T0, spec)
+    l0 = s.ledger()
+    s.step_coarse(10)
+    l1 = s.ledger()
+    scale = l0[0]
+    assert abs(l1[0] - l0[0]) < 1e-13 * scale
+    assert np.abs(l1[1:3] - l0[1:3]).max() < 1e-13 * scale
+    assert abs(l1[3] - l0[3]) < 1e-11 * l0[3]         # energy: Newton tolerance 1e-12
+
+
+def test_ledger_mass_with_solid():
+    lat = L.D2Q9
+    spec = I.taylor_green_spec(32, 8, 24, 2)
+    spec.solids = [{"kind": "sphere", "center": (32.0, 32.0), "radius": 5.0}]
+    g = G.build(spec, lat)
+    assert (g.levels[0].ctype == G.SOLID).sum() > 50
+    s = S.Solver(g, "rr", nu0=0.04)
+    fields = []
+    for lv in g.levels:
+        c = I.cell_centres(lv.coords, lv.level)
+        rho, u = I.taylor_green_fields(c, 32, 2, 0.05, lat.cs2)
+        fields.append((rho, u, None))
+    s.init_fields(fields)
+    l0 = s.ledger()
+    s.step_coarse(50)
+    l1 = s.ledger()
+    # solid cells carry no mass: the ledger counts fluid only
+    assert abs(l1[0] - l0[0]) < 1e-13 * l0[0]
+
+
+def _by_coords(level):
+    return {tuple(c): i for i, c in enumerate(level.coords)}
+
+
+def test_full_patch_equals_uniform_fine_bitwise():
+    lat = L.D2Q9
+    # two levels whose finest region is the whole domain: level 1 is empty
+    two = I.GridSpec(2, (32, 32), 2, [(0, (0, 0), (32, 32))], (True, True))
+    one = I.GridSpec(2, (32, 32), 1, [], (True, True))
+    outs = []
+    for spec in (two, one):
+        g = G.build(spec, lat)
+        s = S.Solver(g, "rr", nu0=0.02)
+        lv = g.levels[0]
+        c = I.cell_centres(lv.coords, 0)
+        rho, u = I.taylor_green_fields(c, 32, 1, 0.05, lat.cs2)
+        fields = [(rho, u, None)] + [(np.zeros(0), np.zeros((2, 0)), None)] * (len(g.levels) - 1)
+        s.init_fields(fields)
+        s.step_fine(12)
+        outs.append(s.f[0])
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_empty_patch_equals_uniform_coarse_bitwise():
+    lat = L.D2Q9
+    two = I.GridSpec(2, (64, 64), 2, [], (True, True))       # level 0 empty
+    one = I.GridSpec(2, (32, 32), 1, [], (True, True))
+    g2, g1 = G.build(two, lat), G.build(one, lat)
+    s2 = S.Solver(g2, "bgk", nu0=0.02)          # level-1 viscosity 0.01
+    s1 = S.Solver(g1, "bgk", nu0=0.01)
+    c = I.cell_centres(g1.levels[0].coords, 0)
+    rho, u = I.taylor_green_fields(c, 32, 1, 0.05, lat.cs2)
+    s2.init_fields([(np.zeros(0), np.zeros((2, 0)), None), (rho, u, None)])
+    s1.init_fields([(rho, u, None)])
+    s2.step_fine(20)       # 10 coarse steps
+    s1.step_fine(10)
+    assert np.array_equal(s2.f[1], s1.f[0])
+
+
+@pytest.mark.parametrize("nl,lo,hi", [(1, 0, 0), (2, 16, 48)])
+def test_taylor_green_decay_rate(nl, lo, hi):
+    lat = L.D2Q9
+    nu_c = 0.01
+    s = _tg_solver(lat, "rr", 64, lo, hi, nl, nu_c)
+    k = 2 * np.pi / 64
+    ts, E = [], []
+    for t in range(0, 301, 30):
+        s.step_coarse(t - s.t // 2 ** (nl - 1))
+        e = 0.0
+        for lev, lv in enumerate(s.g.levels):
+            rho, u, _ = s.moments(lev)
+            m = (lv.ctype == G.FLUID)
+            e += 4 ** lev * (rho[m] * (u[:, m] ** 2).sum(0)).sum()
+        ts.append(t)
+        E.append(e)
+    slope = np.polyfit(np.array(ts[2:], float), np.log(E[2:]), 1)[0]
+    nu_fit = -slope / (4 * k * k)        # kinetic energy ~ exp(-4 nu k^2 t)
+    assert abs(nu_fit / nu_c - 1) < 0.01
+
+
+@pytest.mark.parametrize("latname,model,T0,c_expect", [
+    ("D2Q9", "bgk", None, np.sqrt(1 / 3)),
+    ("D2Q21", "num_ddf", 0.9, np.sqrt(1.4 * 0.9)),
+])
+def test_acoustic_pulse_speed(latname, model, T0, c_expect):
+    lat = L.LATTICES[latname]
+    nx = 400
+    spec = I.GridSpec(2, (nx, 4), 1, [], (True, True))
+    g = G.build(spec, lat)
+    s = S.Solver(g, model, nu0=0.01, T0=T0)
+    lv = g.levels[0]
+    c = I.cell_centres(lv.coords, 0)
+    x0 = nx / 4
+    rho = 1 + 1e-3 * np.exp(-((c[:, 0] - x0) ** 2) / 16.0)
+    u = np.zeros((2, rho.size))
+    T = np.full(rho.size, s.T0)
+    s.init_fields([(rho, u, T if s.comp else None)])
+    row = lv.coords[:, 1] == 0
+    order = np.argsort(lv.coords[row, 0])
+
+    def peak():
+        r = s.moments(0)[0][row][order] - 1
+        j = np.argmax(np.where(np.arange(nx) > x0, r, -1))
+        # parabolic refinement of the maximum
+        a, b, cc = r[j - 1], r[j], r[j + 1]
+        return j + 0.5 + 0.5 * (a - cc) / (a - 2 * b + cc)
+    s.step_fine(60)
+    p1 = peak()
+    s.step_fine(120)
+    p2 = peak()
+    speed = (p2 - p1) / 120
+    assert abs(speed / c_expect - 1) < 0.01
+
+
+def test_schedule_order():
+    lat = L.D2Q9
+    spec = I.GridSpec(2, (256, 256), 5, [(3, (32, 32), (224, 224)), (2, (64, 64), (192, 192)),
+                                         (1, (96, 96), (160, 160)), (0, (112, 112), (144, 144))],
+                      (True, True))
+    g = G.build(spec, lat)
+    s = S.Solver(g, "bgk", nu0=0.02)
+    calls = []
+    s.coupling = lambda lev: calls.append(("c", lev))
+    s.collide_and_stream = lambda lev: calls.append(("s", lev))
+    s.step_fine(16)
+    expect = []
+    for t in range(16):
+        for lev in range(4, 0, -1):
+            if t % 2 ** lev == 0:
+                expect += [("c", lev), ("s", lev)]
+        expect.append(("s", 0))
+    assert calls == expect
+
+
+def _sod_l1(latname, model, T0, nx, nl=1, band=None):
+    lat = L.LATTICES[latname]
+    spec = I.sod_spec(nx, 4, nl, band)
+    g = G.build(spec, lat)
+    s = S.Solver(g, model, nu0=0.0, T0=T0, sensor_A=1.5)
+    fields = []
+    for lv in g.levels:
+        c = I.cell_centres(lv.coords, lv.level)
+        fields.append(I.sod_fields(c, nx, s.T0))
+    s.init_fields(fields)
+    tc = nx / np.sqrt(1.4 * s.T0)
+    s.step_coarse(int(round(0.25 * tc / 2 ** (nl - 1))))
+    t = s.t
+    xs, rs = [], []
+    for lev, lv in enumerate(g.levels):
+        rho, _, _ = s.moments(lev)
+        m = (lv.coords[:, 1] == 0) & (lv.ctype == G.FLUID)
+        xs.append((lv.coords[m, 0] + 0.5) * 2 ** lev)
+        rs.append(rho[m])
+    x, r = np.concatenate(xs), np.concatenate(rs)
+    T0v = s.T0
+    ex = sample((1.0, 0.0, T0v), (0.125, 0.0, 0.1 * T0v), 1.4, (x - nx / 2) / t)
+    return np.abs(r - ex[0]).mean()
+
+
+@pytest.mark.parametrize("latname,model,T0", [("D2Q37", "poly_ddf", None), ("D2Q21", "num_ddf", 0.9)])
+def test_sod_converges_to_exact_solution(latname, model, T0):
+    e1 = _sod_l1(latname, model, T0, 128)
+    e2 = _sod_l1(latname, model, T0, 256)
+    assert e2 < 0.75 * e1
+    assert e2 < 0.02
+
+
+def test_sod_refined_band_close_to_uniform():
+    e_band = _sod_l1("D2Q37", "poly_ddf", None, 256, nl=2, band=(64, 192))
+    e_fine = _sod_l1("D2Q37", "poly_ddf", None, 256)
+    assert e_band < 2.5 * e_fine and e_band < 0.03
