@@ -1,0 +1,200 @@
+/*
+ * lbmtree.h -- C ABI of the B300 collide-and-stream library for cell-centred, non-uniform
+ * (quadtree/octree) lattice Boltzmann grids.
+ *
+ * The calls follow the statement of the problem in Coreixas & Latt, arXiv 2504.04465:
+ * build the tree and its neighbour lists on the host (Secs. 4.3-4.4), choose the lattice and
+ * collision model (Appendix A), set the boundaries (Appendix A.3), advance the levels with the
+ * asynchronous schedule of Sec. 4.5 and the Rohde coalescence/explosion of Sec. 3.2, and read
+ * the macroscopic fields.
+ *
+ * Conventions
+ *   - Every function returns an int status: LBM_OK (0) or a negative LBM_ERR_* code.  The
+ *     message of the last failure on the calling thread is returned by lbm_last_error(); the
+ *     string is owned by the library and valid until the next call on that thread.
+ *   - No C++ exception crosses the ABI.  Device code never traps: kernels that detect a problem
+ *     (non-converged Newton solve) record it in a device status word that lbm_sync() returns.
+ *   - The library owns every device array.  Host input arrays are copied during the call and may
+ *     be freed afterwards.  Host views returned by the library stay valid until lbm_destroy().
+ *   - All device work is issued on the stream given to lbm_create() (NULL = the legacy default
+ *     stream).  lbm_step() is asynchronous; calls that return host data synchronise the stream.
+ *   - Levels: level 0 is the finest; a level-i cell has edge 2^i in finest units.  Coordinates
+ *     are integer cell indices at the cell's own level.
+ */
+#ifndef LBMTREE_H
+#define LBMTREE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define LBM_OK               0
+#define LBM_ERR_ARG         -1   /* invalid argument (null pointer, out-of-range enum)        */
+#define LBM_ERR_STATE       -2   /* call out of order (e.g. step before build/init)           */
+#define LBM_ERR_CUDA        -3   /* a CUDA runtime call failed                                 */
+#define LBM_ERR_OOM         -4   /* device or host allocation failed                           */
+#define LBM_ERR_GRID        -5   /* the requested grid violates a builder invariant            */
+#define LBM_ERR_NEWTON      -6   /* a Newton solve did not converge (result still written)     */
+#define LBM_ERR_NONFINITE   -7   /* a NaN/Inf was found by a reduction                        */
+#define LBM_ERR_UNSUPPORTED -10  /* combination of lattice/model/storage not built            */
+
+/* ---------------------------------------------------------------- enums */
+/* Velocity sets of Appendix A, Tab. lattices_structure (D3Q27: tensor product of D1Q3). */
+#define LBM_D2Q9   9
+#define LBM_D2Q21 21
+#define LBM_D2Q37 37
+#define LBM_D3Q27 27
+
+/* Collision models (Appendix A): BGK and recursive regularization with the Hermite equilibrium
+ * of Eq. GenEq (weakly compressible); compressible polyatomic DDF (Eqs. gEq, polyTemp) with the
+ * thermal polynomial equilibrium (D2Q37) or with the numerical max-entropy equilibrium of
+ * Eq. exponential solved by Newton-Raphson in FP64 (D2Q21). */
+#define LBM_BGK             1
+#define LBM_RR              2
+#define LBM_COMP_POLY       3
+#define LBM_COMP_NUMERICAL  4
+
+/* Population storage.  F64/F32: plain values.  F16DEV: binary16 deviations
+ * delta_i = f_i/(w_i rho_ref) - 1 (and for g: g_i/(w_i rho_ref (2Cv-D) T0) - 1), arithmetic in
+ * FP32.  The Newton solve and the conservation reductions are FP64 in every storage mode. */
+#define LBM_F64     1
+#define LBM_F32     2
+#define LBM_F16DEV  3
+
+/* Boundary kinds for the six faces (Appendix A.3), applied on `reach` layers.  PERIODIC wraps.
+ * EQ_DIRICHLET imposes rho, u, T through the equilibrium; EQ_DIRICHLET_RHO imposes u, T and
+ * extrapolates rho from the nearest interior cell along the face normal; NEUMANN copies every
+ * population of that interior cell.  Faces: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+. */
+#define LBM_PERIODIC          0
+#define LBM_EQ_DIRICHLET      1
+#define LBM_EQ_DIRICHLET_RHO  2
+#define LBM_NEUMANN           3
+
+/* Initial guess of the Newton solve.  WARM: the multipliers stored in the cell (carried through
+ * coalescence/explosion, Sec. 3.2).  ZERO: lambda = 0.  POLY: weighted least-squares fit of
+ * -1 - ln f_poly (f_poly the thermal Hermite equilibrium, positive populations only). */
+#define LBM_GUESS_WARM  0
+#define LBM_GUESS_ZERO  1
+#define LBM_GUESS_POLY  2
+
+/* Analytic solids (cells whose centre lies inside are solid, level 0 only). */
+#define LBM_SOLID_SPHERE 1   /* p = {cx, cy, cz, radius}                (finest units)      */
+#define LBM_SOLID_NACA   2   /* p = {chord, x_le, y_axis, thickness}    symmetric 4-digit,
+                                closed trailing edge, zero angle of attack (2D)          */
+
+/* Cell types reported by lbm_cells(). */
+#define LBM_CELL_FLUID   1
+#define LBM_CELL_CGHOST  2   /* coarse ghost: collides, coalesced from / exploded to children */
+#define LBM_CELL_FGHOST  3   /* fine ghost: streams only                                       */
+#define LBM_CELL_BC      4   /* boundary layer cell                                            */
+#define LBM_CELL_SOLID   5
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef struct {
+    double nu0;          /* kinematic viscosity in level-0 lattice units (0 = inviscid)        */
+    double T0;           /* reference temperature (compressible); 0 = lattice c_s^2             */
+    double gamma;        /* specific heat ratio of the DDF (Cv = 1/(gamma-1))                   */
+    int    sensor_on;    /* kinetic shock sensor, Eqs. DeltaAvg / shock_function                */
+    double sensor_A;     /* value of alpha on [0.1, 1)                                          */
+    double newton_tol;   /* stop when max |G| < tol (1e-12 in FP64)                             */
+    int    newton_max_iter;
+    int    guess;        /* LBM_GUESS_*                                                         */
+    double rho_ref;      /* reference density of the F16DEV storage (1.0)                       */
+} lbm_collision_params;
+
+typedef struct { int level; int64_t lo[3]; int64_t hi[3]; } lbm_box;     /* finest units */
+typedef struct { int kind; double p[8]; } lbm_shape;
+
+typedef struct {
+    int64_t n_cells[8];          /* allocated non-absent cells per level                      */
+    int64_t n_blocks[8];
+    double  n_eq;                /* sum_i n_i / 2^i over non-solid cells (Sec. 6.3)            */
+    int     n_levels;
+    int     block[3];            /* cell block shape                                          */
+    int64_t newton_iter_sum;     /* Newton iterations summed over all collisions              */
+    int64_t newton_updates;      /* collisions that ran a Newton solve                        */
+    int64_t newton_nonconverged;
+    int64_t newton_hist[16];     /* histogram of iterations per collision (last bin: >= 15)   */
+    int64_t fine_iterations;     /* fine iterations advanced since initialisation             */
+    int64_t kernel_launches;     /* step-kernel launches issued since initialisation          */
+    int64_t device_bytes;        /* device memory held by the context                         */
+    int64_t cell_updates;        /* cell updates per coarse step (sum_i n_i 2^(L-1-i))          */
+} lbm_stats_t;
+
+/* ---------------------------------------------------------------- lifecycle */
+/* Create a context bound to `device` and `stream` (cudaStream_t or NULL).  dim = 2 or 3.
+ * device < 0 makes a host-only context: grids can be built and inspected, nothing runs. */
+int lbm_create(lbm_ctx** out, int dim, int device, void* stream);
+/* Release every device and host resource of the context.  NULL is accepted. */
+int lbm_destroy(lbm_ctx* ctx);
+const char* lbm_last_error(void);
+
+/* ---------------------------------------------------------------- configuration */
+int lbm_set_lattice(lbm_ctx* ctx, int lattice);
+int lbm_set_collision(lbm_ctx* ctx, int model, const lbm_collision_params* params);
+int lbm_set_precision(lbm_ctx* ctx, int storage);
+/* face 0..5; kind LBM_*; rho_u_T = {rho, ux, uy, uz, T} (ignored for PERIODIC/NEUMANN). */
+int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);
+/* Block shape of the cell layout (x, y, z; z = 1 in 2D).  Defaults 16x16 (2D), 8x4x4 (3D).
+ * Each extent must be even and at least the lattice reach.  Must precede lbm_build_grid(). */
+int lbm_set_block(lbm_ctx* ctx, int bx, int by, int bz);
+
+/* ---------------------------------------------------------------- grid (Secs. 3.2, 4.3-4.4) */
+/* Build the levels, neighbour tables, ghost layers and boundary layers, and allocate the
+ * device arrays.  extent: finest-level extent per axis (divisible by 2^(n_levels-1)).
+ * boxes: refinement boxes, box.level in [0, n_levels-2]; the region of level i is the union of
+ * its boxes (the whole domain for the coarsest level), aligned to 2^(i+1) finest units, each box
+ * inside a box of the next coarser level.  solids: analytic shapes at level 0.  Returns
+ * LBM_ERR_GRID with a message when an invariant fails (misaligned or non-nested boxes, ghost
+ * layers overlapping, a region touching a non-periodic face, a solid closer than the reach to
+ * a ghost or boundary layer). */
+int lbm_build_grid(lbm_ctx* ctx, const int64_t extent[3], int n_levels,
+                   const lbm_box* boxes, int n_boxes, const lbm_shape* solids, int n_solids);
+/* Library-owned host view of the cells (levels ascending, then Morton order of blocks, then
+ * x-fastest inside a block).  xyz is n_cells x 3 (z = 0 in 2D).  Valid until lbm_destroy(). */
+int lbm_cells(lbm_ctx* ctx, int64_t* n_cells, const int32_t** level, const int32_t** xyz,
+              const uint8_t** type);
+/* Velocities of the lattice: xi[Q*3] (library-owned), in the population order of the
+ * readout calls. */
+int lbm_velocities(lbm_ctx* ctx, int* Q, const int32_t** xi);
+
+/* ---------------------------------------------------------------- fields */
+/* Initialise every cell at equilibrium (Appendix A.3) from host arrays in lbm_cells() order:
+ * rho[n], u[dim*n] (SoA: u[d*n + i]), T[n] (NULL for weakly compressible models).  Resets the
+ * iteration counter.  Newton multipliers start from the POLY guess. */
+int lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* T);
+
+/* ---------------------------------------------------------------- stepping (Sec. 4.5) */
+/* Advance n_coarse coarse steps (2^(n_levels-1) fine iterations each).  Asynchronous. */
+int lbm_step(lbm_ctx* ctx, int64_t n_coarse);
+/* Advance n_fine fine iterations (any count; levels stay on the schedule). */
+int lbm_step_fine(lbm_ctx* ctx, int64_t n_fine);
+/* Use (1) or stop using (0) a captured CUDA graph of two coarse periods in lbm_step(). */
+int lbm_use_graph(lbm_ctx* ctx, int on);
+/* Wait for the context's stream; return the first device status (LBM_OK, LBM_ERR_NEWTON). */
+int lbm_sync(lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------- outputs */
+/* rho[n], u[dim*n], T[n] (T may be NULL) of every cell in lbm_cells() order, computed from the
+ * populations a cell would collide at the current fine iteration (its streamed populations,
+ * with boundary layers applied; coarse-ghost unknowns are not coalesced).  Synchronises. */
+int lbm_read_moments(lbm_ctx* ctx, double* rho, double* u, double* T);
+/* which = 0: f, 1: g, 2: lambda.  out[Q*n] (lambda: 8*n), SoA by population, in lbm_cells()
+ * order, population order of lbm_velocities().  Same state as lbm_read_moments(). */
+int lbm_read_populations(lbm_ctx* ctx, int which, double* out);
+/* Conserved totals at a coarse synchronisation instant (iteration multiple of 2^(L-1)):
+ * out = {mass, momentum_x, momentum_y, momentum_z, energy}, each the sum over bulk, boundary and
+ * coarse-ghost cells (unknowns coalesced) of the cell volume 2^(i D) times sum f, sum xi f and
+ * sum (|xi|^2 f + g)/2.  FP64, deterministic (fixed-order two-pass reduction through a
+ * library-owned scratch array).  LBM_ERR_STATE off a synchronisation instant. */
+int lbm_conserved(lbm_ctx* ctx, double out[5]);
+int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMTREE_H */

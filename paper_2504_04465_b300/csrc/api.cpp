@@ -1,0 +1,717 @@
+// C ABI of the library (include/lbmtree.h): context, grid upload, level scheduler, CUDA graph,
+// readout and the conservation ledger.
+//
+// Scheduler (Sec. 4.5 of arXiv 2504.04465): at fine iteration t the levels i with t % 2^i == 0
+// are active; the coarsest goes first.  All active levels of an iteration run in ONE launch (the
+// kernel maps each CTA to a (level, block) pair); the coupling of level i with i-1 is fused into
+// level i's coarse ghosts.  Level i reads buffer (t / 2^i) & 1, so the launch arguments repeat
+// with period 2 * 2^(L-1) fine iterations, which is the span captured in the CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmtree.h"
+#include "builder.h"
+#include "kernels.h"
+
+using namespace lbm;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e__ = (call);                                                                        \
+        if (e__ != cudaSuccess) return fail(LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+struct DevLevel {
+    int* nbr = nullptr;
+    unsigned char* type = nullptr;
+    unsigned char* bflag = nullptr;
+    int* rec_id = nullptr;
+    CellRecDev* recs = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    double* lam = nullptr;
+};
+
+struct Constants {
+    double w37[37], H37[37 * 15], cs2_37, w21[21], H21[21 * 10];
+    Constants() { lattice_constants(w37, H37, &cs2_37, w21, H21); }
+};
+const Constants& constants() {
+    static Constants c;
+    return c;
+}
+
+std::mutex g_upload_mu;
+bool g_uploaded[256] = {false};
+
+bool find_kernels(int lattice, int model, int storage, const int* blk, KernelSet& out) {
+    switch (lattice) {
+        case LBM_D2Q9: return find_kernels_d2q9(model, storage, blk, out);
+        case LBM_D3Q27: return find_kernels_d3q27(model, storage, blk, out);
+        case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, out);
+        case LBM_D2Q21: return find_kernels_d2q21(model, storage, blk, out);
+    }
+    return false;
+}
+}  // namespace
+
+struct lbm_ctx {
+    int dim = 2, device = 0;
+    bool host_only = false;
+    cudaStream_t stream = nullptr;
+    int lattice = 0, model = 0, storage = LBM_F64;
+    bool params_set = false;
+    lbm_collision_params params{};
+    FaceSpec faces[6];
+    int block[3] = {16, 16, 1};
+    BuiltGrid grid;
+    bool built = false;
+    KernelSet ks;
+    // host views
+    std::vector<int32_t> h_level, h_xyz;
+    std::vector<uint8_t> h_type;
+    std::vector<int64_t> h_slot;
+    std::vector<int64_t> level_first;
+    std::vector<int32_t> h_xi;
+    // device
+    DevLevel dl[MAX_LEVELS];
+    int* d_status = nullptr;
+    unsigned long long* d_nstat = nullptr;
+    double* d_partial = nullptr;
+    double* d_out5 = nullptr;
+    std::vector<void*> allocs;
+    int64_t dev_bytes = 0;
+    int64_t t = 0;
+    bool initialized = false;
+    int64_t launches = 0;
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t total_blocks = 0;
+
+    void* dalloc(size_t bytes) {
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        dev_bytes += (int64_t)bytes;
+        return p;
+    }
+    void release() {
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+        dev_bytes = 0;
+        for (auto& d : dl) d = DevLevel{};
+        d_status = nullptr; d_nstat = nullptr; d_partial = nullptr; d_out5 = nullptr;
+    }
+    int L() const { return grid.n_levels; }
+    int64_t period() const { return int64_t(1) << (grid.n_levels - 1); }
+    // buffer holding the current state of level i after tt iterations: ceil(tt / 2^i) steps done
+    int cur(int i, int64_t tt) const { return int(((tt + (int64_t(1) << i) - 1) >> i) & 1); }
+    bool comp() const { return model == LBM_COMP_POLY || model == LBM_COMP_NUMERICAL; }
+    double T0() const {
+        if (params.T0 > 0) return params.T0;
+        if (lattice == LBM_D2Q21) return 2.0 / 3.0;
+        if (lattice == LBM_D2Q37) return constants().cs2_37;
+        return 1.0 / 3.0;
+    }
+};
+
+namespace {
+
+int check_ctx(lbm_ctx* c) {
+    if (!c) return fail(LBM_ERR_ARG, "null context");
+    return LBM_OK;
+}
+
+void fill_args(const lbm_ctx* c, StepArgs& a) {
+    std::memset(&a, 0, sizeof(a));
+    const int L = c->L();
+    a.n_levels = L;
+    const int BS = c->grid.BS;
+    // tau = nu / theta + 1/2 in each level's units, nu_i = nu_0 / 2^i (Eq. tau_fine_to_coarse);
+    // theta = c_s^2 for the weakly compressible models and T0 for the compressible ones
+    const double theta = c->comp() ? c->T0() : 1.0 / 3.0;
+    for (int i = 0; i < L; ++i) {
+        const BuiltLevel& bl = c->grid.levels[i];
+        LevelDev& d = a.lv[i];
+        d.nb = bl.nb;
+        d.ncell = bl.nb * BS;
+        d.nbr = c->dl[i].nbr;
+        d.type = c->dl[i].type;
+        d.bflag = c->dl[i].bflag;
+        d.rec_id = c->dl[i].rec_id;
+        d.recs = c->dl[i].recs;
+        d.f[0] = c->dl[i].f[0]; d.f[1] = c->dl[i].f[1];
+        d.g[0] = c->dl[i].g[0]; d.g[1] = c->dl[i].g[1];
+        d.lam = c->dl[i].lam;
+        const double nu = c->params.nu0 / double(int64_t(1) << i);
+        d.tau = nu / theta + 0.5;
+    }
+    ModelDev& m = a.m;
+    m.cs2 = theta;
+    m.T0 = c->T0();
+    m.Cv = 1.0 / (c->params.gamma - 1.0);
+    m.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : 1.0;
+    m.sensor_on = c->params.sensor_on;
+    m.sensor_A = c->params.sensor_A;
+    m.newton_tol = c->params.newton_tol > 0 ? c->params.newton_tol : 1e-12;
+    m.newton_max_iter = c->params.newton_max_iter > 0 ? c->params.newton_max_iter : 50;
+    m.guess = c->params.guess;
+    for (int f = 0; f < 6; ++f) {
+        m.faces[f].kind = c->faces[f].kind;
+        m.faces[f].rho = c->faces[f].rho;
+        for (int d = 0; d < 3; ++d) m.faces[f].u[d] = c->faces[f].u[d];
+        m.faces[f].T = c->faces[f].T > 0 ? c->faces[f].T : m.T0;
+    }
+    a.status = c->d_status;
+    a.nstat = c->d_nstat;
+}
+
+// arguments of fine iteration t
+int64_t iteration_args(const lbm_ctx* c, int64_t t, StepArgs& a) {
+    fill_args(c, a);
+    const int L = c->L();
+    int n = 0;
+    int64_t off = 0;
+    for (int i = L - 1; i >= 0; --i) {
+        if (t % (int64_t(1) << i)) continue;
+        if (c->grid.levels[i].nb == 0) continue;
+        a.active[n] = i;
+        a.block_off[n] = off;
+        off += c->grid.levels[i].nb;
+        ++n;
+    }
+    a.block_off[n] = off;
+    a.n_active = n;
+    for (int i = 0; i < L; ++i) {
+        a.rd[i] = int((t >> i) & 1);
+        a.sync_fg[i] = (i + 1 < L) && (t % (int64_t(2) << i) == 0);
+    }
+    return off;
+}
+
+// arguments for readout / ledger at the current time: every level, current buffers
+int64_t current_args(const lbm_ctx* c, StepArgs& a) {
+    fill_args(c, a);
+    const int L = c->L();
+    int n = 0;
+    int64_t off = 0;
+    for (int i = L - 1; i >= 0; --i) {
+        if (c->grid.levels[i].nb == 0) continue;
+        a.active[n] = i;
+        a.block_off[n] = off;
+        off += c->grid.levels[i].nb;
+        ++n;
+    }
+    a.block_off[n] = off;
+    a.n_active = n;
+    for (int i = 0; i < L; ++i) a.rd[i] = c->cur(i, c->t);
+    return off;
+}
+
+int ready(lbm_ctx* c) {
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (c->host_only) return fail(LBM_ERR_STATE, "host-only context (device < 0)");
+    if (!c->initialized) return fail(LBM_ERR_STATE, "fields not initialised");
+    return LBM_OK;
+}
+
+int launch_iterations(lbm_ctx* c, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        StepArgs a;
+        const int64_t nb = iteration_args(c, c->t, a);
+        if (nb) {
+            c->ks.step(a, nb, c->stream);
+            c->launches++;
+        }
+        c->t++;
+    }
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+int build_graph(lbm_ctx* c) {
+    if (c->gexec) return LBM_OK;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t span = 2 * c->period();
+    for (int64_t k = 0; k < span; ++k) {
+        StepArgs a;
+        const int64_t nb = iteration_args(c, k, a);
+        if (nb) c->ks.step(a, nb, c->stream);
+    }
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int launches_per_span(const lbm_ctx* c) {
+    int n = 0;
+    for (int64_t k = 0; k < 2 * c->period(); ++k)
+        for (int i = c->L() - 1; i >= 0; --i)
+            if (k % (int64_t(1) << i) == 0 && c->grid.levels[i].nb) { ++n; break; }
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
+    if (!out) return fail(LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(LBM_ERR_ARG, "dim must be 2 or 3");
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(LBM_ERR_OOM, "context allocation");
+    c->dim = dim;
+    c->device = device;
+    c->host_only = device < 0;
+    c->stream = (cudaStream_t)stream;
+    if (dim == 3) { c->block[0] = 8; c->block[1] = 4; c->block[2] = 4; }
+    c->params.gamma = 1.4;
+    c->params.rho_ref = 1.0;
+    c->params.newton_tol = 1e-12;
+    c->params.newton_max_iter = 50;
+    c->params.sensor_A = 1.5;
+    if (!c->host_only) {
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+        }
+        std::lock_guard<std::mutex> lk(g_upload_mu);
+        if (device < 256 && !g_uploaded[device]) {
+            const Constants& k = constants();
+            e = upload_tables_d2q37(k.w37, k.H37, k.cs2_37);
+            if (e == cudaSuccess) e = upload_tables_d2q21(k.w21, k.H21);
+            if (e != cudaSuccess) {
+                delete c;
+                return fail(LBM_ERR_CUDA, std::string("constant upload: ") + cudaGetErrorString(e));
+            }
+            g_uploaded[device] = true;
+        }
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    if (!c->host_only) cudaSetDevice(c->device);
+    c->release();
+    delete c;
+    return LBM_OK;
+}
+
+int lbm_set_lattice(lbm_ctx* c, int lattice) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q21 && lattice != LBM_D2Q37 && lattice != LBM_D3Q27)
+        return fail(LBM_ERR_ARG, "unknown lattice");
+    if ((lattice == LBM_D3Q27) != (c->dim == 3)) return fail(LBM_ERR_ARG, "lattice dimension differs from the context");
+    if (c->built) return fail(LBM_ERR_STATE, "lattice must be set before lbm_build_grid");
+    c->lattice = lattice;
+    return LBM_OK;
+}
+
+int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (model < LBM_BGK || model > LBM_COMP_NUMERICAL) return fail(LBM_ERR_ARG, "unknown collision model");
+    if (c->built) return fail(LBM_ERR_STATE, "collision model must be set before lbm_build_grid");
+    if (p) {
+        if (p->nu0 < 0) return fail(LBM_ERR_ARG, "negative viscosity");
+        if (p->gamma <= 1.0 && model >= LBM_COMP_POLY) return fail(LBM_ERR_ARG, "gamma must exceed 1");
+        if (p->guess < 0 || p->guess > LBM_GUESS_POLY) return fail(LBM_ERR_ARG, "unknown Newton guess");
+        c->params = *p;
+        if (c->params.gamma <= 1.0) c->params.gamma = 1.4;
+        if (c->params.rho_ref <= 0) c->params.rho_ref = 1.0;
+    }
+    c->model = model;
+    c->params_set = true;
+    return LBM_OK;
+}
+
+int lbm_set_precision(lbm_ctx* c, int storage) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16DEV) return fail(LBM_ERR_ARG, "unknown storage");
+    if (c->built) return fail(LBM_ERR_STATE, "precision must be set before lbm_build_grid");
+    c->storage = storage;
+    return LBM_OK;
+}
+
+int lbm_set_boundary(lbm_ctx* c, int face, int kind, const double* v) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (face < 0 || face > 5) return fail(LBM_ERR_ARG, "face out of range");
+    if (kind < LBM_PERIODIC || kind > LBM_NEUMANN) return fail(LBM_ERR_ARG, "unknown boundary kind");
+    if ((kind == LBM_EQ_DIRICHLET || kind == LBM_EQ_DIRICHLET_RHO) && !v) return fail(LBM_ERR_ARG, "Dirichlet values missing");
+    if (c->built) return fail(LBM_ERR_STATE, "boundaries must be set before lbm_build_grid");
+    FaceSpec& f = c->faces[face];
+    f.kind = kind;
+    if (v) { f.rho = v[0]; f.u[0] = v[1]; f.u[1] = v[2]; f.u[2] = v[3]; f.T = v[4]; }
+    return LBM_OK;
+}
+
+int lbm_set_block(lbm_ctx* c, int bx, int by, int bz) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (c->built) return fail(LBM_ERR_STATE, "block shape must be set before lbm_build_grid");
+    if (bx < 2 || by < 2 || bz < 1 || (c->dim == 2 && bz != 1) || bx * by * bz > 1024)
+        return fail(LBM_ERR_ARG, "bad block shape");
+    c->block[0] = bx; c->block[1] = by; c->block[2] = bz;
+    return LBM_OK;
+}
+
+int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_box* boxes, int n_boxes,
+                   const lbm_shape* solids, int n_solids) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!extent || (n_boxes > 0 && !boxes) || (n_solids > 0 && !solids)) return fail(LBM_ERR_ARG, "null array");
+    if (!c->lattice || !c->params_set) return fail(LBM_ERR_STATE, "set lattice and collision model first");
+    if (c->built) return fail(LBM_ERR_STATE, "grid already built");
+    const bool weak = c->model == LBM_BGK || c->model == LBM_RR;
+    if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27)) ||
+        (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
+        (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21))
+        return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
+    if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->ks))
+        return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
+    GridInput in;
+    in.dim = c->dim;
+    for (int d = 0; d < 3; ++d) in.extent[d] = extent[d];
+    in.n_levels = n_levels;
+    for (int k = 0; k < n_boxes; ++k) {
+        BoxSpec b;
+        b.level = boxes[k].level;
+        for (int d = 0; d < 3; ++d) { b.lo[d] = boxes[k].lo[d]; b.hi[d] = boxes[k].hi[d]; }
+        in.boxes.push_back(b);
+    }
+    for (int k = 0; k < n_solids; ++k) {
+        ShapeSpec s;
+        s.kind = solids[k].kind;
+        std::memcpy(s.p, solids[k].p, sizeof(s.p));
+        in.solids.push_back(s);
+    }
+    for (int f = 0; f < 6; ++f) in.faces[f] = c->faces[f];
+    for (int d = 0; d < 3; ++d) in.block[d] = c->block[d];
+    in.lattice = c->lattice;
+    std::string err;
+    try {
+        err = build_grid(in, c->grid);
+    } catch (const std::bad_alloc&) {
+        return fail(LBM_ERR_OOM, "host allocation in the grid builder");
+    } catch (...) {
+        return fail(LBM_ERR_GRID, "grid builder failed");
+    }
+    if (!err.empty()) return fail(LBM_ERR_GRID, err);
+    const int BS = c->grid.BS;
+    c->h_level.clear(); c->h_xyz.clear(); c->h_type.clear(); c->h_slot.clear(); c->level_first.clear();
+    for (int i = 0; i < c->L(); ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        c->level_first.push_back((int64_t)c->h_type.size());
+        for (int64_t b = 0; b < lv.nb; ++b)
+            for (int l = 0; l < BS; ++l) {
+                const uint8_t t = lv.type[b * BS + l];
+                if (t == C_ABSENT) continue;
+                const int lx = l % c->block[0], ly = (l / c->block[0]) % c->block[1], lz = l / (c->block[0] * c->block[1]);
+                c->h_level.push_back(i);
+                c->h_xyz.push_back(lv.bxyz[3 * b] * c->block[0] + lx);
+                c->h_xyz.push_back(lv.bxyz[3 * b + 1] * c->block[1] + ly);
+                c->h_xyz.push_back(lv.bxyz[3 * b + 2] * c->block[2] + lz);
+                c->h_type.push_back(t);
+                c->h_slot.push_back(b * BS + l);
+            }
+    }
+    c->level_first.push_back((int64_t)c->h_type.size());
+    c->h_xi.clear();
+    for (int q = 0; q < c->grid.lat.Q; ++q)
+        for (int d = 0; d < 3; ++d) c->h_xi.push_back(c->grid.lat.xi[q][d]);
+    c->built = true;
+    if (c->host_only) return LBM_OK;
+    CU(cudaSetDevice(c->device));
+    const int Q = c->grid.lat.Q;
+    const size_t es = c->storage == LBM_F64 ? 8 : c->storage == LBM_F32 ? 4 : 2;
+    const bool has_g = c->comp();
+    const bool has_lam = c->model == LBM_COMP_NUMERICAL;
+    c->total_blocks = 0;
+    for (int i = 0; i < c->L(); ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        DevLevel& d = c->dl[i];
+        const int64_t ncell = lv.nb * BS;
+        c->total_blocks += lv.nb;
+        d.nbr = (int*)c->dalloc(lv.nbr.size() * 4);
+        d.type = (unsigned char*)c->dalloc(lv.type.size());
+        d.bflag = (unsigned char*)c->dalloc(lv.bflag.size());
+        d.rec_id = (int*)c->dalloc(lv.rec_id.size() * 4);
+        d.recs = (CellRecDev*)c->dalloc(lv.recs.size() * sizeof(CellRecDev));
+        for (int k = 0; k < 2; ++k) {
+            d.f[k] = c->dalloc(size_t(Q) * ncell * es);
+            if (has_g) d.g[k] = c->dalloc(size_t(Q) * ncell * es);
+        }
+        if (has_lam) d.lam = (double*)c->dalloc(size_t(2) * 8 * ncell * 8);
+        if (!d.nbr || !d.type || !d.bflag || !d.rec_id || !d.recs || !d.f[0] || !d.f[1] ||
+            (has_g && (!d.g[0] || !d.g[1])) || (has_lam && !d.lam)) {
+            c->release();
+            c->built = false;
+            return fail(LBM_ERR_OOM, "device allocation of level " + std::to_string(i));
+        }
+        CU(cudaMemcpy(d.nbr, lv.nbr.data(), lv.nbr.size() * 4, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d.type, lv.type.data(), lv.type.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d.bflag, lv.bflag.data(), lv.bflag.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d.rec_id, lv.rec_id.data(), lv.rec_id.size() * 4, cudaMemcpyHostToDevice));
+        if (!lv.recs.empty())
+            CU(cudaMemcpy(d.recs, lv.recs.data(), lv.recs.size() * sizeof(CellRecDev), cudaMemcpyHostToDevice));
+    }
+    c->d_status = (int*)c->dalloc(sizeof(int));
+    c->d_nstat = (unsigned long long*)c->dalloc(19 * sizeof(unsigned long long));
+    c->d_partial = (double*)c->dalloc(size_t(c->total_blocks + 1) * 5 * sizeof(double));
+    c->d_out5 = (double*)c->dalloc(5 * sizeof(double));
+    if (!c->d_status || !c->d_nstat || !c->d_partial || !c->d_out5) {
+        c->release();
+        c->built = false;
+        return fail(LBM_ERR_OOM, "device allocation");
+    }
+    CU(cudaMemset(c->d_status, 0, sizeof(int)));
+    CU(cudaMemset(c->d_nstat, 0, 19 * sizeof(unsigned long long)));
+    return LBM_OK;
+}
+
+int lbm_cells(lbm_ctx* c, int64_t* n, const int32_t** level, const int32_t** xyz, const uint8_t** type) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (n) *n = (int64_t)c->h_type.size();
+    if (level) *level = c->h_level.data();
+    if (xyz) *xyz = c->h_xyz.data();
+    if (type) *type = c->h_type.data();
+    return LBM_OK;
+}
+
+int lbm_velocities(lbm_ctx* c, int* Q, const int32_t** xi) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (Q) *Q = c->grid.lat.Q;
+    if (xi) *xi = c->h_xi.data();
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double* T) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (c->host_only) return fail(LBM_ERR_STATE, "host-only context");
+    const bool comp = c->comp();
+    if (!rho || !u || (comp && !T)) return fail(LBM_ERR_ARG, "null field array");
+    CU(cudaSetDevice(c->device));
+    const int64_t n = (int64_t)c->h_type.size();
+    const int BS = c->grid.BS;
+    StepArgs a;
+    fill_args(c, a);
+    int rc = LBM_OK;
+    for (int i = 0; i < c->L() && rc == LBM_OK; ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * BS;
+        if (!ncell) continue;
+        std::vector<double> hr(ncell, 1.0), hu(size_t(3) * ncell, 0.0), hT(ncell, c->T0());
+        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
+            const int64_t s = c->h_slot[k];
+            hr[s] = rho[k];
+            for (int d = 0; d < c->dim; ++d) hu[d * ncell + s] = u[d * n + k];
+            if (comp) hT[s] = T[k];
+        }
+        double *pr = nullptr, *pu = nullptr, *pT = nullptr;
+        if (cudaMalloc(&pr, ncell * 8) != cudaSuccess || cudaMalloc(&pu, 3 * ncell * 8) != cudaSuccess ||
+            cudaMalloc(&pT, ncell * 8) != cudaSuccess) {
+            rc = fail(LBM_ERR_OOM, "initialisation staging");
+        } else if (cudaMemcpy(pr, hr.data(), ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(pu, hu.data(), 3 * ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(pT, hT.data(), ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = fail(LBM_ERR_CUDA, "initialisation upload");
+        } else {
+            c->ks.init(a, i, pr, pu, pT, c->stream);
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) rc = fail(LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+        }
+        cudaFree(pr);
+        cudaFree(pu);
+        cudaFree(pT);
+    }
+    if (rc) return rc;
+    int st = 0;
+    CU(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemset(c->d_status, 0, sizeof(int)));
+    CU(cudaMemset(c->d_nstat, 0, 19 * sizeof(unsigned long long)));
+    c->t = 0;
+    c->launches = 0;
+    c->initialized = true;
+    if (st) return fail(st, "initialisation: a Newton solve did not converge");
+    return LBM_OK;
+}
+
+int lbm_step_fine(lbm_ctx* c, int64_t n) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (int r = ready(c)) return r;
+    if (n < 0) return fail(LBM_ERR_ARG, "negative step count");
+    return launch_iterations(c, n);
+}
+
+int lbm_use_graph(lbm_ctx* c, int on) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    c->use_graph = on != 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t n_coarse) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (int r = ready(c)) return r;
+    if (n_coarse < 0) return fail(LBM_ERR_ARG, "negative step count");
+    const int64_t P = c->period();
+    int64_t n = n_coarse * P;
+    if (!c->use_graph) return launch_iterations(c, n);
+    const int64_t span = 2 * P;
+    while (n > 0 && c->t % span) {         // align to the captured span with plain launches
+        if (int r = launch_iterations(c, 1)) return r;
+        --n;
+    }
+    if (n >= span) {
+        if (int r = build_graph(c)) return r;
+        const int per = launches_per_span(c);
+        for (; n >= span; n -= span) {
+            CU(cudaGraphLaunch(c->gexec, c->stream));
+            c->t += span;
+            c->launches += per;
+        }
+    }
+    return launch_iterations(c, n);
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (c->host_only || !c->built) return LBM_OK;
+    CU(cudaStreamSynchronize(c->stream));
+    int st = 0;
+    CU(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) return fail(st, "device status " + std::to_string(st));
+    return LBM_OK;
+}
+
+static int read_common(lbm_ctx* c, int which, int ncomp, std::vector<std::vector<double>>& per_level) {
+    if (int r = ready(c)) return r;
+    StepArgs a;
+    current_args(c, a);
+    const int BS = c->grid.BS;
+    per_level.assign(c->L(), {});
+    for (int i = 0; i < c->L(); ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * BS;
+        if (!ncell) continue;
+        double* d = nullptr;
+        if (cudaMalloc(&d, size_t(ncomp) * ncell * 8) != cudaSuccess) return fail(LBM_ERR_OOM, "readout buffer");
+        cudaMemsetAsync(d, 0, size_t(ncomp) * ncell * 8, c->stream);
+        c->ks.read(a, i, which, d, c->stream);
+        per_level[i].resize(size_t(ncomp) * ncell);
+        cudaError_t e1 = cudaMemcpyAsync(per_level[i].data(), d, size_t(ncomp) * ncell * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(d);
+        if (e1 != cudaSuccess || e2 != cudaSuccess)
+            return fail(LBM_ERR_CUDA, std::string("readout: ") + cudaGetErrorString(e2 != cudaSuccess ? e2 : e1));
+    }
+    return LBM_OK;
+}
+
+int lbm_read_moments(lbm_ctx* c, double* rho, double* u, double* T) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!rho || !u) return fail(LBM_ERR_ARG, "null output");
+    std::vector<std::vector<double>> pl;
+    if (int r = read_common(c, 0, 5, pl)) return r;
+    const int64_t n = (int64_t)c->h_type.size();
+    const int BS = c->grid.BS;
+    for (int i = 0; i < c->L(); ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * BS;
+        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
+            const int64_t s = c->h_slot[k];
+            rho[k] = pl[i][s];
+            for (int d = 0; d < c->dim; ++d) u[d * n + k] = pl[i][(1 + d) * ncell + s];
+            if (T) T[k] = pl[i][4 * ncell + s];
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_read_populations(lbm_ctx* c, int which, double* out) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!out || which < 0 || which > 2) return fail(LBM_ERR_ARG, "bad arguments");
+    if (which == 1 && !c->comp()) return fail(LBM_ERR_ARG, "model has no g populations");
+    if (which == 2 && c->model != LBM_COMP_NUMERICAL) return fail(LBM_ERR_ARG, "model has no multipliers");
+    const int ncomp = which == 2 ? 8 : c->grid.lat.Q;
+    std::vector<std::vector<double>> pl;
+    if (int r = read_common(c, which + 1, ncomp, pl)) return r;
+    const int64_t n = (int64_t)c->h_type.size();
+    const int BS = c->grid.BS;
+    for (int i = 0; i < c->L(); ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * BS;
+        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
+            const int64_t s = c->h_slot[k];
+            for (int q = 0; q < ncomp; ++q) out[q * n + k] = pl[i][q * ncell + s];
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_conserved(lbm_ctx* c, double out[5]) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!out) return fail(LBM_ERR_ARG, "null output");
+    if (int r = ready(c)) return r;
+    if (c->t % c->period()) return fail(LBM_ERR_STATE, "not at a coarse synchronisation instant");
+    StepArgs a;
+    const int64_t nb = current_args(c, a);
+    c->ks.ledger(a, nb, c->d_partial, c->d_out5, c->stream);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out, c->d_out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_stats(lbm_ctx* c, lbm_stats_t* s) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!s) return fail(LBM_ERR_ARG, "null output");
+    std::memset(s, 0, sizeof(*s));
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    s->n_levels = c->L();
+    for (int d = 0; d < 3; ++d) s->block[d] = c->block[d];
+    for (int i = 0; i < c->L() && i < 8; ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        s->n_blocks[i] = lv.nb;
+        s->n_cells[i] = lv.count[1] + lv.count[2] + lv.count[3] + lv.count[4] + lv.count[5];
+        const int64_t live = lv.count[1] + lv.count[2] + lv.count[3] + lv.count[4];
+        s->cell_updates += live << (c->L() - 1 - i);
+    }
+    s->n_eq = c->grid.n_eq;
+    s->fine_iterations = c->t;
+    s->kernel_launches = c->launches;
+    s->device_bytes = c->dev_bytes;
+    if (!c->host_only && c->d_nstat) {
+        unsigned long long h[19];
+        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaMemcpy(h, c->d_nstat, sizeof(h), cudaMemcpyDeviceToHost));
+        s->newton_iter_sum = (int64_t)h[0];
+        s->newton_updates = (int64_t)h[1];
+        s->newton_nonconverged = (int64_t)h[2];
+        for (int k = 0; k < 16; ++k) s->newton_hist[k] = (int64_t)h[3 + k];
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Launch descriptors shared by the host scheduler (api.cpp) and the kernels.
+#pragma once
+#include <cstdint>
+
+namespace lbm {
+
+constexpr int MAX_LEVELS = 8;
+enum : int { ST_F64 = 1, ST_F32 = 2, ST_F16DEV = 3 };
+
+struct CellRecDev {
+    unsigned long long mask;
+    int a;
+    int b;
+};
+
+struct LevelDev {
+    long long nb;            // blocks
+    long long ncell;         // nb * BS: SoA stride
+    const int* nbr;          // nb * 27
+    const unsigned char* type;
+    const unsigned char* bflag;
+    const int* rec_id;
+    const CellRecDev* recs;
+    void* f[2];
+    void* g[2];
+    double* lam;             // 2 buffers x 8 x ncell (numerical equilibrium)
+    double tau;
+};
+
+struct FaceDev {
+    int kind;
+    double rho, u[3], T;
+};
+
+struct ModelDev {
+    double cs2;              // theta of the viscosity relation
+    double T0;               // reference temperature (compressible)
+    double Cv;               // 1/(gamma - 1)
+    double rho_ref;          // F16DEV reference density
+    int sensor_on;
+    double sensor_A;
+    double newton_tol;
+    int newton_max_iter;
+    int guess;
+    FaceDev faces[6];
+};
+
+struct StepArgs {
+    LevelDev lv[MAX_LEVELS];
+    int n_levels;
+    int n_active;
+    int active[MAX_LEVELS];           // active levels, coarsest first
+    long long block_off[MAX_LEVELS + 1];
+    int rd[MAX_LEVELS];               // buffer index read by each level this iteration
+    int sync_fg[MAX_LEVELS];          // 1: the level's fine ghosts receive an explosion now
+    ModelDev m;
+    int* status;                      // first error code (atomicCAS from 0)
+    unsigned long long* nstat;        // newton: [0] iter sum, [1] updates, [2] nonconverged, [3..18] hist
+};
+
+}  // namespace lbm

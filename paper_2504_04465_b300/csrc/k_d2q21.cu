@@ -1,0 +1,80 @@
+// D2Q21 compressible double-distribution kernels with the numerical (max-entropy) equilibrium
+// of Eq. exponential solved by Newton-Raphson in FP64, and the kinetic shock sensor
+// (Appendix A of arXiv 2504.04465).  The multipliers are stored per cell (warm start) and carried
+// through coalescence/explosion (Sec. 3.2).  The polynomial guess fits -1 - ln f_poly, f_poly the
+// 3rd-order thermal Hermite equilibrium about theta = 2/3 (positive populations only), onto the
+// eight basis functions by weighted least squares.
+#include "kernels_impl.cuh"
+
+namespace lbm {
+
+static __constant__ double cw21[21];
+static __constant__ double cH21[21][10];
+
+__device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, double* lam) {
+    double a[15];
+    thermal_moments<double>(1.0, ux, uy, Tt - 2.0 / 3.0, 3, a);
+    double A[36], b[8];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 21; ++q) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) s += cH21[q][k] * a[k];
+        const double fp = cw21[q] * s;
+        if (fp > 0.0) {
+            const double y = -1.0 - log(fp);
+            const double w = cw21[q];
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                b[i] += w * MB<21>::m(q, i) * y;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) A[k++] += w * (MB<21>::m(q, i) * MB<21>::m(q, j));
+            }
+        }
+    }
+    chol8_solve(A, b, lam);
+}
+
+struct D2Q21M {
+    static constexpr int D = 2, Q = 21;
+    static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
+    __host__ __device__ static constexpr int cx(int q) { return Lat<21>::cx(q); }
+    __host__ __device__ static constexpr int cy(int q) { return Lat<21>::cy(q); }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __device__ static double w(int q) { return cw21[q]; }
+    template <int ST>
+    __device__ static void feq(const ModelDev& m, typename Store<ST>::T rho, typename Store<ST>::T ux,
+                               typename Store<ST>::T uy, typename Store<ST>::T Tt, double* lam,
+                               typename Store<ST>::T* f, int* iters, int* conv) {
+        using T = typename Store<ST>::T;
+        if (m.guess == 1) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a) lam[a] = 0.0;
+        } else if (m.guess == 2) {
+            poly_guess21((double)ux, (double)uy, (double)Tt, lam);
+        }
+        double e[21];
+        *iters = newton_solve<21>((double)ux, (double)uy, (double)Tt, lam, e, m.newton_tol, m.newton_max_iter, conv);
+#pragma unroll
+        for (int q = 0; q < 21; ++q) f[q] = T((double)rho * e[q]);
+    }
+    __device__ static void init_guess(double ux, double uy, double Tt, double* lam) { poly_guess21(ux, uy, Tt, lam); }
+};
+
+bool find_kernels_d2q21(int model, int storage, const int* blk, KernelSet& out) {
+    if (model == 4 && blk[0] == 16 && blk[1] == 16 && blk[2] == 1) return pick_storage<D2Q21M, 16, 16, 1>(storage, out);
+    return false;
+}
+
+cudaError_t upload_tables_d2q21(const double* w21, const double* H21) {
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(cw21, w21, sizeof(double) * 21)) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(cH21, H21, sizeof(double) * 21 * 10);
+}
+
+}  // namespace lbm

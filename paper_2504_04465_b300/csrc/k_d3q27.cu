@@ -1,0 +1,26 @@
+// D3Q27 weakly compressible BGK and recursive-regularized kernels (Appendix A of
+// arXiv 2504.04465; the D3Q27 basis is every Hermite tensor with each axis at most twice).
+#include "kernels_impl.cuh"
+
+namespace lbm {
+
+template <bool RR_> struct D3Q27M {
+    static constexpr int D = 3, Q = 27;
+    static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
+    __host__ __device__ static constexpr int cx(int q) { return TP<3>::cx(q); }
+    __host__ __device__ static constexpr int cy(int q) { return TP<3>::cy(q); }
+    __host__ __device__ static constexpr int cz(int q) { return TP<3>::cz(q); }
+    __host__ __device__ static constexpr double w(int q) { return tp_w<3>(q); }
+};
+
+bool find_kernels_d3q27(int model, int storage, const int* blk, KernelSet& out) {
+    if (blk[0] == 8 && blk[1] == 4 && blk[2] == 4) {
+        if (model == 1) return pick_storage<D3Q27M<false>, 8, 4, 4>(storage, out);
+        if (model == 2) return pick_storage<D3Q27M<true>, 8, 4, 4>(storage, out);
+    }
+    if (blk[0] == 16 && blk[1] == 4 && blk[2] == 2 && model == 2) return pick_storage<D3Q27M<true>, 16, 4, 2>(storage, out);
+    if (blk[0] == 8 && blk[1] == 8 && blk[2] == 2 && model == 2) return pick_storage<D3Q27M<true>, 8, 8, 2>(storage, out);
+    return false;
+}
+
+}  // namespace lbm

@@ -1,0 +1,31 @@
+// Host-visible entry points of the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device_types.h"
+
+namespace lbm {
+
+struct KernelSet {
+    void (*step)(const StepArgs&, long long nblocks, cudaStream_t) = nullptr;
+    void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
+    void (*ledger)(const StepArgs&, long long nblocks, double* partial, double* out, cudaStream_t) = nullptr;
+    void (*init)(const StepArgs&, int lev, const double* rho, const double* u, const double* T, cudaStream_t) = nullptr;
+    const void* step_kernel = nullptr;
+    int block_threads = 0;
+};
+
+// Kernels for (model, storage, block shape) of each lattice; false if that combination is not built.
+bool find_kernels_d2q9(int model, int storage, const int* block, KernelSet& out);
+bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out);
+bool find_kernels_d2q37(int model, int storage, const int* block, KernelSet& out);
+bool find_kernels_d2q21(int model, int storage, const int* block, KernelSet& out);
+
+// Constant tables of the D2Q37 and D2Q21 translation units (current device).
+cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37);
+cudaError_t upload_tables_d2q21(const double* w21, const double* H21);
+
+// weights.cpp: D2Q37 weights re-derived from isotropy, Hermite tables of both lattices
+void lattice_constants(double w37[37], double H37[37 * 15], double* cs2_37, double w21[21], double H21[21 * 10]);
+
+}  // namespace lbm

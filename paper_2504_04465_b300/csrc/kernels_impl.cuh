@@ -1,0 +1,580 @@
+// Kernel templates of the CUDA path: fused collide-and-stream over all active levels,
+// initialisation, moment/population readout and the FP64 conservation ledger.  Each lattice's
+// translation unit (k_d2q9.cu, k_d3q27.cu, k_d2q37.cu, k_d2q21.cu) defines its model policy and
+// instantiates them.
+//
+// One launch per fine iteration covers every level active at that iteration (Sec. 4.5 of
+// arXiv 2504.04465 runs them one after the other; the paper's future work proposes loading the
+// GPU with all active levels at once).  This is race-free in the pull form: level i reads its
+// own buffer rd_i and writes rd_i ^ 1; the coupling of level i with i-1 (Sec. 3.2) is fused into
+// level i's coarse-ghost cells, which read level i-1's buffer rd_{i-1} (coalescence) and write the
+// fine-ghost slots of rd_{i-1} ^ 1 (explosion); level i-1 skips its fine ghosts at that iteration.
+//
+// Model policy M: D, Q, HAS_G, HAS_LAM, RR, cx/cy/cz(q), w(q); compressible models also
+//   template <int ST> static void feq(m, rho, ux, uy, T, lam, feq, iters, conv)
+//   static void init_guess(ux, uy, T, lam)
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "models.cuh"
+#include "models_comp.cuh"
+
+namespace lbm {
+
+enum Mode { MODE_STEP = 0, MODE_READ = 1, MODE_LEDGER = 2 };
+
+template <class M, int ST>
+struct Cell {
+    using T = typename Store<ST>::T;
+    T f[M::Q];
+    T g[M::HAS_G ? M::Q : 1];
+    double lam[M::HAS_LAM ? 8 : 1];
+};
+
+template <class M, int ST>
+__device__ __forceinline__ typename Store<ST>::T ref_f(const ModelDev& m, int q) {
+    return typename Store<ST>::T(M::w(q) * m.rho_ref);
+}
+template <class M, int ST>
+__device__ __forceinline__ typename Store<ST>::T ref_g(const ModelDev& m, int q) {
+    return typename Store<ST>::T(M::w(q) * m.rho_ref * (2.0 * m.Cv - M::D) * m.T0);
+}
+
+template <class M, int ST>
+__device__ __forceinline__ void load_pop(const LevelDev& L, int buf, long long src, int q, const ModelDev& m,
+                                         typename Store<ST>::T& fo, typename Store<ST>::T& go) {
+    using T = typename Store<ST>::T;
+    if (src < 0) {
+        fo = T(0);
+        go = T(0);
+        return;
+    }
+    fo = Store<ST>::load(L.f[buf], (long long)q * L.ncell + src, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) go = Store<ST>::load(L.g[buf], (long long)q * L.ncell + src, ref_g<M, ST>(m, q));
+    else go = T(0);
+}
+
+template <class M, int ST>
+__device__ __forceinline__ void store_pop(const LevelDev& L, int buf, long long cell, int q, const ModelDev& m,
+                                          typename Store<ST>::T fv, typename Store<ST>::T gv) {
+    Store<ST>::store(L.f[buf], (long long)q * L.ncell + cell, fv, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) Store<ST>::store(L.g[buf], (long long)q * L.ncell + cell, gv, ref_g<M, ST>(m, q));
+}
+
+// macroscopic moments (rho, u, T) of f, g (T from Eq. polyTemp)
+template <class M, int ST>
+__device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c, typename Store<ST>::T& rho,
+                                        typename Store<ST>::T* u, typename Store<ST>::T& Tt) {
+    using T = typename Store<ST>::T;
+    T r = 0, jx = 0, jy = 0, jz = 0, e2 = 0, gs = 0;
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) {
+        const T v = c.f[q];
+        r += v;
+        if (M::cx(q)) jx += T(M::cx(q)) * v;
+        if (M::cy(q)) jy += T(M::cy(q)) * v;
+        if (M::cz(q)) jz += T(M::cz(q)) * v;
+        if constexpr (M::HAS_G) {
+            e2 += T(M::cx(q) * M::cx(q) + M::cy(q) * M::cy(q)) * v;
+            gs += c.g[q];
+        }
+    }
+    rho = r;
+    u[0] = jx / r;
+    u[1] = jy / r;
+    u[2] = jz / r;
+    Tt = T(0);
+    if constexpr (M::HAS_G) Tt = (e2 + gs - r * (u[0] * u[0] + u[1] * u[1])) / (T(2) * r * T(m.Cv));
+}
+
+// ------------------------------------------------------------------ state assembly
+// Pre-collision state of the cell (level lev, block b, local l) at the current iteration:
+//   FLUID : pull gather, bounce-back on blocked links
+//   CGHOST: pull gather; in STEP/LEDGER modes the unknown populations are the mean of the
+//           children's streamed populations (Eq. coalescence) and lambda the children's mean
+//   FGHOST: pull gather (pure streaming), lambda carried
+//   BC    : Neumann copies the partner's gathered state (and lambda); Dirichlet sets the
+//           equilibrium of (rho_bc or the partner's rho, u_bc, T_bc)
+template <class M, int ST, int BX, int BY, int BZ, int MODE>
+__device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b, int l, int type, bool simple,
+                                         const int* nbr_s, Cell<M, ST>& c, int* conv_out) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    const LevelDev& L = a.lv[lev];
+    const int rd = a.rd[lev];
+    const long long cell = b * BS + l;
+    const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+    *conv_out = 1;
+    if (type != C_BC) {
+        unsigned long long bmask = 0ull, umask = 0ull;
+        long long child = -1;
+        if (!simple && type != C_FGHOST) {
+            const int r = L.rec_id[cell];
+            if (r >= 0) {
+                const CellRecDev rec = L.recs[r];
+                if (type == C_FLUID) {
+                    bmask = rec.mask;
+                } else {
+                    umask = rec.mask;
+                    child = rec.a;
+                }
+            }
+        }
+        const bool coal = (type == C_CGHOST) && (MODE != MODE_READ);
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) {
+            T gv = T(0);
+            if (bmask & (1ull << q)) {
+                load_pop<M, ST>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
+            } else if (coal && (umask & (1ull << q))) {
+                const LevelDev& F = a.lv[lev - 1];
+                const int rdf = a.rd[lev - 1];
+                constexpr int NK = (M::D == 3) ? 8 : 4;
+                T sf = 0, sg = 0;
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
+                    const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, M::cx(q), M::cy(q), M::cz(q));
+                    T vf, vg;
+                    load_pop<M, ST>(F, rdf, s, q, a.m, vf, vg);
+                    sf += vf;
+                    sg += vg;
+                }
+                c.f[q] = sf / T(NK);
+                gv = sg / T(NK);
+            } else {
+                const long long s = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(q), M::cy(q), M::cz(q));
+                load_pop<M, ST>(L, rd, s, q, a.m, c.f[q], gv);
+            }
+            if constexpr (M::HAS_G) c.g[q] = gv;
+        }
+        if constexpr (M::HAS_LAM) {
+            if (coal) {
+                const LevelDev& F = a.lv[lev - 1];
+                const int rdf = a.rd[lev - 1];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX;
+                        s += F.lam[((long long)rdf * 8 + i) * F.ncell + ch];
+                    }
+                    c.lam[i] = s / 4.0;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) c.lam[i] = L.lam[((long long)rd * 8 + i) * L.ncell + cell];
+            }
+        }
+        return;
+    }
+    // boundary layer cell
+    const CellRecDev rec = L.recs[L.rec_id[cell]];
+    const long long P = rec.a;
+    const int kind = rec.b & 15, face = rec.b >> 4;
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) {
+        const long long s = src_cell_g<BX, BY, BZ>(L.nbr, P, M::cx(q), M::cy(q), M::cz(q));
+        T gv;
+        load_pop<M, ST>(L, rd, s, q, a.m, c.f[q], gv);
+        if constexpr (M::HAS_G) c.g[q] = gv;
+    }
+    if constexpr (M::HAS_LAM) {
+        const long long src = (kind == 3) ? P : cell;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c.lam[i] = L.lam[((long long)rd * 8 + i) * L.ncell + src];
+    }
+    if (kind == 3) return;                                     // Neumann
+    const FaceDev& fd = a.m.faces[face];
+    T rho = T(fd.rho);
+    if (kind == 2) {                                           // extrapolated density
+        T r = 0;
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) r += c.f[q];
+        rho = r;
+    }
+    if constexpr (!M::HAS_G) {
+        weak_feq<M::D, T>(rho, T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), c.f);
+    } else {
+        int it = 0, conv = 1;
+        M::template feq<ST>(a.m, rho, T(fd.u[0]), T(fd.u[1]), T(fd.T), c.lam, c.f, &it, &conv);
+        const T gfac = T((2.0 * a.m.Cv - M::D) * fd.T);
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) c.g[q] = gfac * c.f[q];
+        *conv_out = conv;
+    }
+}
+
+// ------------------------------------------------------------------ collision
+template <class M, int ST>
+__device__ __forceinline__ int collide(const ModelDev& m, double tau, Cell<M, ST>& c, int* conv) {
+    using T = typename Store<ST>::T;
+    *conv = 1;
+    if constexpr (!M::HAS_G) {
+        weak_collide<M::D, M::RR, T>(c.f, T(1.0 / tau));
+        return 0;
+    } else {
+        T rho, u[3], Tt;
+        moments<M, ST>(m, c, rho, u, Tt);
+        T feq[M::Q];
+        int it = 0;
+        M::template feq<ST>(m, rho, u[0], u[1], Tt, c.lam, feq, &it, conv);
+        T tau_eff = T(tau);
+        if (m.sensor_on) {
+            T eps = 0;
+            const T tiny = (sizeof(T) == 8) ? T(1e-300) : T(1e-30);
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q)
+                if (feq[q] > tiny) eps += fabs(c.f[q] - feq[q]) / feq[q];
+            eps /= T(M::Q);
+            tau_eff = T(tau) * sensor_alpha<T>(eps, T(tau), T(m.sensor_A));
+        }
+        const T gfac = T(2.0 * m.Cv - M::D) * Tt;
+        const T om = T(1) / tau_eff;
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) {
+            c.f[q] -= (c.f[q] - feq[q]) * om;
+            c.g[q] -= (c.g[q] - gfac * feq[q]) * om;
+        }
+        return it;
+    }
+}
+
+__device__ __forceinline__ int find_level(const StepArgs& a, long long bid, long long* b) {
+    int k = 0;
+    while (k + 1 < a.n_active && bid >= a.block_off[k + 1]) ++k;
+    *b = bid - a.block_off[k];
+    return a.active[k];
+}
+
+// ------------------------------------------------------------------ step kernel
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_step(const StepArgs a) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    __shared__ int nbr_s[27];
+    __shared__ unsigned long long s_nstat[19];
+    long long b;
+    const int lev = find_level(a, blockIdx.x, &b);
+    const LevelDev& L = a.lv[lev];
+    const int l = threadIdx.x;
+    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
+    __syncthreads();
+    const long long cell = b * BS + l;
+    const int rd = a.rd[lev], wr = rd ^ 1;
+    const bool simple = L.bflag[b] != 0;
+    const int type = simple ? (int)C_FLUID : (int)L.type[cell];
+    const bool work = !(type == C_ABSENT || type == C_SOLID || (type == C_FGHOST && a.sync_fg[lev]));
+    int iters = -1;
+    if (work) {
+        Cell<M, ST> c;
+        int conv = 1, conv2 = 1;
+        assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+        if (type != C_FGHOST) {
+            const int it = collide<M, ST>(a.m, L.tau, c, &conv2);
+            if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
+            if (!conv || !conv2) set_status(a.status, -6);
+        }
+        // fine ghosts stream purely: stored as gathered (post-collision = pre-collision)
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, wr, cell, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) L.lam[((long long)wr * 8 + i) * L.ncell + cell] = c.lam[i];
+        }
+        if (type == C_CGHOST) {
+            // uniform explosion (Eq. explosion_uniform) into every child's slot of the buffer the
+            // finer level writes at this iteration
+            const LevelDev& F = a.lv[lev - 1];
+            const int wrf = a.rd[lev - 1] ^ 1;
+            const long long child = L.recs[L.rec_id[cell]].a;
+            constexpr int NK = (M::D == 3) ? 8 : 4;
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                const long long ch = child + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
+#pragma unroll
+                for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(F, wrf, ch, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+                if constexpr (M::HAS_LAM) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) F.lam[((long long)wrf * 8 + i) * F.ncell + ch] = c.lam[i];
+                }
+            }
+        }
+    }
+    if constexpr (M::HAS_LAM) {
+        if (iters >= 0) {
+            const int nc = iters >= 1000;
+            const int it = iters - 1000 * nc;
+            atomicAdd(&s_nstat[0], (unsigned long long)it);
+            atomicAdd(&s_nstat[1], 1ull);
+            if (nc) atomicAdd(&s_nstat[2], 1ull);
+            atomicAdd(&s_nstat[3 + (it < 15 ? it : 15)], 1ull);
+        }
+        __syncthreads();
+        if (l < 19 && s_nstat[l]) atomicAdd(&a.nstat[l], s_nstat[l]);
+    }
+}
+
+// ------------------------------------------------------------------ readout
+// out (FP64, SoA over the level's slots): which = 0 moments (rho, ux, uy, uz, T),
+// 1 populations f, 2 populations g, 3 lambda
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev, int which, double* out) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    __shared__ int nbr_s[27];
+    const LevelDev& L = a.lv[lev];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    __syncthreads();
+    const long long cell = b * BS + l;
+    const bool simple = L.bflag[b] != 0;
+    const int type = simple ? (int)C_FLUID : (int)L.type[cell];
+    if (type == C_ABSENT || type == C_SOLID) return;
+    Cell<M, ST> c;
+    int conv;
+    assemble<M, ST, BX, BY, BZ, MODE_READ>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+    if (which == 0) {
+        T rho, u[3], Tt;
+        moments<M, ST>(a.m, c, rho, u, Tt);
+        out[0 * L.ncell + cell] = rho;
+        out[1 * L.ncell + cell] = u[0];
+        out[2 * L.ncell + cell] = u[1];
+        out[3 * L.ncell + cell] = u[2];
+        out[4 * L.ncell + cell] = Tt;
+    } else if (which == 1) {
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) out[(long long)q * L.ncell + cell] = c.f[q];
+    } else if (which == 2) {
+        if constexpr (M::HAS_G) {
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) out[(long long)q * L.ncell + cell] = c.g[q];
+        }
+    } else if (which == 3) {
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) out[(long long)i * L.ncell + cell] = c.lam[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ ledger (FP64, deterministic)
+// Per block: the volume-weighted sums of the cells of the block, reduced in a fixed tree order
+// into partial[block * 5 + j]; a second kernel reduces the partials in a fixed order.
+template <class M, int ST, int BX, int BY, int BZ>
+__device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, double* partial) {
+    constexpr int BS = BX * BY * BZ;
+    __shared__ int nbr_s[27];
+    __shared__ double red[5][BS];
+    long long b;
+    const int lev = find_level(a, bid, &b);
+    const LevelDev& L = a.lv[lev];
+    const int l = threadIdx.x;
+    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    __syncthreads();
+    const long long cell = b * BS + l;
+    const bool simple = L.bflag[b] != 0;
+    const int type = simple ? (int)C_FLUID : (int)L.type[cell];
+    double v[5] = {0, 0, 0, 0, 0};
+    if (type == C_FLUID || type == C_BC || type == C_CGHOST) {
+        Cell<M, ST> c;
+        int conv;
+        assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+        const double V = double(1ll << (lev * M::D));
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) {
+            const double fq = (double)c.f[q];
+            v[0] += fq;
+            v[1] += M::cx(q) * fq;
+            v[2] += M::cy(q) * fq;
+            v[3] += M::cz(q) * fq;
+            v[4] += 0.5 * double(M::cx(q) * M::cx(q) + M::cy(q) * M::cy(q) + M::cz(q) * M::cz(q)) * fq;
+            if constexpr (M::HAS_G) v[4] += 0.5 * (double)c.g[q];
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] *= V;
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[j][l] = v[j];
+    __syncthreads();
+    for (int s = BS / 2; s > 0; s >>= 1) {
+        if (l < s) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) red[j][l] += red[j][l + s];
+        }
+        __syncthreads();
+    }
+    if (l < 5) partial[bid * 5 + l] = red[l][0];
+}
+
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_ledger(const StepArgs a, double* partial) {
+    ledger_block<M, ST, BX, BY, BZ>(a, blockIdx.x, partial);
+}
+
+static __global__ void __launch_bounds__(256) k_ledger_final(const double* partial, long long n, double* out) {
+    __shared__ double red[5][256];
+    const int l = threadIdx.x;
+    double v[5] = {0, 0, 0, 0, 0};
+    for (long long i = l; i < n; i += 256)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] += partial[i * 5 + j];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[j][l] = v[j];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (l < s) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) red[j][l] += red[j][l + s];
+        }
+        __syncthreads();
+    }
+    if (l < 5) out[l] = red[l][0];
+}
+
+// ------------------------------------------------------------------ initialisation
+// Pass 1: equilibrium E of the given fields into buffer 1 (and lambda into both lambda buffers).
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int lev, const double* rho_in,
+                                                          const double* u_in, const double* T_in) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    const LevelDev& L = a.lv[lev];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    const long long cell = b * BS + l;
+    const int type = L.bflag[b] ? (int)C_FLUID : (int)L.type[cell];
+    if (type == C_ABSENT || type == C_SOLID) return;
+    const long long n = L.ncell;
+    const T rho = T(rho_in[cell]);
+    const T ux = T(u_in[cell]), uy = T(u_in[n + cell]), uz = T(M::D == 3 ? u_in[2 * n + cell] : 0.0);
+    T feq[M::Q];
+    if constexpr (!M::HAS_G) {
+        weak_feq<M::D, T>(rho, ux, uy, uz, feq);
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, 1, cell, q, a.m, feq[q], T(0));
+    } else {
+        const T Tt = T(T_in[cell]);
+        double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int it, conv;
+        if constexpr (M::HAS_LAM) M::init_guess((double)ux, (double)uy, (double)Tt, lam);
+        ModelDev m = a.m;
+        m.guess = 0;              // start from the polynomial guess computed above
+        M::template feq<ST>(m, rho, ux, uy, Tt, lam, feq, &it, &conv);
+        if (!conv) set_status(a.status, -6);
+        const T gfac = T((2.0 * a.m.Cv - M::D) * (double)Tt);
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, 1, cell, q, a.m, feq[q], gfac * feq[q]);
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                L.lam[((long long)0 * 8 + i) * n + cell] = lam[i];
+                L.lam[((long long)1 * 8 + i) * n + cell] = lam[i];
+            }
+        }
+    }
+}
+
+// Pass 2: stored_q(y) = E_q(y + xi_q), or E_qbar(y) where y's link qbar is blocked, so that the
+// first gather reproduces E at every cell (the stored state is post-collision populations).
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs a, int lev) {
+    using S = typename Store<ST>::S;
+    constexpr int BS = BX * BY * BZ;
+    __shared__ int nbr_s[27];
+    const LevelDev& L = a.lv[lev];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    __syncthreads();
+    const long long cell = b * BS + l;
+    const int type = L.bflag[b] ? (int)C_FLUID : (int)L.type[cell];
+    if (type == C_ABSENT || type == C_SOLID) return;
+    unsigned long long bmask = 0ull;
+    if (!L.bflag[b] && type == C_FLUID) {
+        const int r = L.rec_id[cell];
+        if (r >= 0) bmask = L.recs[r].mask;
+    }
+    const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+    const S* Ef = (const S*)L.f[1];
+    const S* Eg = (const S*)L.g[1];
+    S* Of = (S*)L.f[0];
+    S* Og = (S*)L.g[0];
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) {
+        const int qb = M::Q - 1 - q;
+        long long src;
+        int qs;
+        if (bmask & (1ull << qb)) {
+            src = cell;
+            qs = qb;
+        } else {
+            src = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, -M::cx(q), -M::cy(q), -M::cz(q));
+            qs = q;
+            if (src >= 0) {
+                const int st = L.type[src];
+                if (st == C_ABSENT || st == C_SOLID) src = -1;
+            }
+        }
+        S vf, vg;
+        if (src >= 0) {
+            vf = Ef[(long long)qs * L.ncell + src];
+            if constexpr (M::HAS_G) vg = Eg[(long long)qs * L.ncell + src];
+        } else {
+            // zero population (a deviation of -1 in the binary16 format)
+            vf = S(ST == ST_F16DEV ? -1.0f : 0.0f);
+            vg = vf;
+        }
+        Of[(long long)q * L.ncell + cell] = vf;
+        if constexpr (M::HAS_G) Og[(long long)q * L.ncell + cell] = vg;
+    }
+}
+
+// ------------------------------------------------------------------ host launchers
+template <class M, int ST, int BX, int BY, int BZ>
+struct Launch {
+    static void step(const StepArgs& a, long long nblocks, cudaStream_t s) {
+        k_step<M, ST, BX, BY, BZ><<<(unsigned)nblocks, BX * BY * BZ, 0, s>>>(a);
+    }
+    static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
+        if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);
+    }
+    static void ledger(const StepArgs& a, long long nblocks, double* partial, double* out, cudaStream_t s) {
+        if (nblocks) k_ledger<M, ST, BX, BY, BZ><<<(unsigned)nblocks, BX * BY * BZ, 0, s>>>(a, partial);
+        k_ledger_final<<<1, 256, 0, s>>>(partial, nblocks, out);
+    }
+    static void init(const StepArgs& a, int lev, const double* r, const double* u, const double* t, cudaStream_t s) {
+        if (!a.lv[lev].nb) return;
+        k_init_eq<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, r, u, t);
+        k_init_prestream<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
+    }
+};
+
+template <class M, int ST, int BX, int BY, int BZ>
+KernelSet make_set() {
+    KernelSet k;
+    k.step = &Launch<M, ST, BX, BY, BZ>::step;
+    k.read = &Launch<M, ST, BX, BY, BZ>::read;
+    k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;
+    k.init = &Launch<M, ST, BX, BY, BZ>::init;
+    k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ>;
+    k.block_threads = BX * BY * BZ;
+    return k;
+}
+
+template <class M, int BX, int BY, int BZ>
+bool pick_storage(int storage, KernelSet& out) {
+    switch (storage) {
+        case ST_F64: out = make_set<M, ST_F64, BX, BY, BZ>(); return true;
+        case ST_F32: out = make_set<M, ST_F32, BX, BY, BZ>(); return true;
+        case ST_F16DEV: out = make_set<M, ST_F16DEV, BX, BY, BZ>(); return true;
+    }
+    return false;
+}
+
+}  // namespace lbm

@@ -1,0 +1,116 @@
+// Velocity sets and cell types of the CUDA path (host and device).
+//
+// Appendix A, Tab. lattices_structure of arXiv 2504.04465 gives the symmetry groups of D2Q9,
+// D2Q21 and D2Q37; D3Q27 is the tensor product of the 1D three-velocity set.  The CUDA path
+// orders every 2D set row-major over (y, x) in [-r, r]^2 and D3Q27 as x + 3y + 9z with
+// components in {-1, 0, 1}.  Both orders are point-symmetric, so the opposite of velocity q is
+// Q - 1 - q.  Weights are not stored here: D2Q9/D2Q21/D3Q27 use the printed fractions and D2Q37
+// re-derives its weights at start-up (weights.cpp).
+#pragma once
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define LBM_HD __host__ __device__
+#else
+#define LBM_HD
+#endif
+
+namespace lbm {
+
+// cell types of the layout (host builder and kernels)
+enum CellType : unsigned char { C_ABSENT = 0, C_FLUID = 1, C_CGHOST = 2, C_FGHOST = 3, C_BC = 4, C_SOLID = 5 };
+
+enum LatticeId { L_D2Q9 = 9, L_D2Q21 = 21, L_D2Q37 = 37, L_D3Q27 = 27 };
+
+// membership of (x, y) in the 2D sets (|x|, |y| <= 3)
+LBM_HD constexpr bool in_d2q21(int x, int y) {
+    int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+    if (ax > 3 || ay > 3) return false;
+    if (ax == 0 || ay == 0) return true;               // (0,0) (1,0) (2,0) (3,0)
+    return ax == ay && ax <= 2;                         // (1,1) (2,2)
+}
+LBM_HD constexpr bool in_d2q37(int x, int y) {
+    int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+    if (ax > 3 || ay > 3) return false;
+    if (ax == 3 && ay >= 2) return false;
+    if (ay == 3 && ax >= 2) return false;
+    return true;                                        // groups (a,b) with a,b <= 2 or (3,0),(3,1)
+}
+
+// component (x if want_y == 0, else y) of velocity q of a 2D set enumerated row-major over (y, x)
+LBM_HD constexpr int enum21(int q, int want_y) {
+    int k = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x)
+            if (in_d2q21(x, y)) {
+                if (k == q) return want_y ? y : x;
+                ++k;
+            }
+    return 0;
+}
+LBM_HD constexpr int enum37(int q, int want_y) {
+    int k = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x)
+            if (in_d2q37(x, y)) {
+                if (k == q) return want_y ? y : x;
+                ++k;
+            }
+    return 0;
+}
+
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+    static constexpr int Q = 9, D = 2, R = 1;
+    LBM_HD static constexpr int cx(int q) { return q % 3 - 1; }
+    LBM_HD static constexpr int cy(int q) { return q / 3 - 1; }
+    LBM_HD static constexpr int cz(int) { return 0; }
+};
+
+template <> struct Lat<27> {
+    static constexpr int Q = 27, D = 3, R = 1;
+    LBM_HD static constexpr int cx(int q) { return q % 3 - 1; }
+    LBM_HD static constexpr int cy(int q) { return (q / 3) % 3 - 1; }
+    LBM_HD static constexpr int cz(int q) { return q / 9 - 1; }
+};
+
+template <> struct Lat<21> {
+    static constexpr int Q = 21, D = 2, R = 3;
+    LBM_HD static constexpr int cx(int q) { return enum21(q, 0); }
+    LBM_HD static constexpr int cy(int q) { return enum21(q, 1); }
+    LBM_HD static constexpr int cz(int) { return 0; }
+};
+
+template <> struct Lat<37> {
+    static constexpr int Q = 37, D = 2, R = 3;
+    LBM_HD static constexpr int cx(int q) { return enum37(q, 0); }
+    LBM_HD static constexpr int cy(int q) { return enum37(q, 1); }
+    LBM_HD static constexpr int cz(int) { return 0; }
+};
+
+// runtime view (host builder)
+struct LatticeDesc {
+    int Q, D, R;
+    int xi[37][3];
+};
+
+template <class L>
+inline void fill_desc(LatticeDesc& d) {
+    d.Q = L::Q; d.D = L::D; d.R = L::R;
+    for (int q = 0; q < L::Q; ++q) { d.xi[q][0] = L::cx(q); d.xi[q][1] = L::cy(q); d.xi[q][2] = L::cz(q); }
+}
+
+inline LatticeDesc lattice_desc(int id) {
+    LatticeDesc d{};
+    switch (id) {
+        case L_D2Q9: fill_desc<Lat<9>>(d); break;
+        case L_D2Q21: fill_desc<Lat<21>>(d); break;
+        case L_D2Q37: fill_desc<Lat<37>>(d); break;
+        case L_D3Q27: fill_desc<Lat<27>>(d); break;
+        default: d.Q = 0;
+    }
+    return d;
+}
+
+}  // namespace lbm

@@ -1,0 +1,164 @@
+// Compressible double-distribution building blocks of the CUDA path (Appendix A of
+// arXiv 2504.04465): thermal Hermite moments, the kinetic shock sensor and the FP64 Newton
+// solver of the numerical (max-entropy) equilibrium.
+//
+// T from Eq. polyTemp, g_eq from Eq. gEq, sensor of Eqs. DeltaAvg/shock_function (alpha = 1
+// below 0.01), BGK on f and g with the same tau.  The thermal expansion about theta adds, for
+// every set of disjoint index pairs, a factor (T - theta) delta per pair.  Numerical equilibrium:
+// Eq. exponential with the 8 constraints G0..G3yaa, solved with rho = 1 by Newton-Raphson in
+// FP64 (step d = (sum e M M^T)^-1 G by Cholesky, backtracking halving of the step until ||G||_2
+// decreases, at most 30 halvings, stop when max |G| < tol).
+#pragma once
+#include "device_common.cuh"
+
+namespace lbm {
+
+// thermal Hermite moments a_k, components ordered (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (3,0) (2,1)
+// (1,2) (0,3) (4,0) (3,1) (2,2) (1,3) (0,4); dT = T - theta
+template <typename T>
+__device__ __forceinline__ void thermal_moments(T rho, T ux, T uy, T dT, int order, T* a) {
+    const T ux2 = ux * ux, uy2 = uy * uy;
+    a[0] = rho;
+    a[1] = rho * ux;
+    a[2] = rho * uy;
+    a[3] = rho * (ux2 + dT);
+    a[4] = rho * ux * uy;
+    a[5] = rho * (uy2 + dT);
+    a[6] = rho * ux * (ux2 + T(3) * dT);
+    a[7] = rho * uy * (ux2 + dT);
+    a[8] = rho * ux * (uy2 + dT);
+    a[9] = rho * uy * (uy2 + T(3) * dT);
+    if (order >= 4) {
+        a[10] = rho * (ux2 * ux2 + T(6) * ux2 * dT + T(3) * dT * dT);
+        a[11] = rho * ux * uy * (ux2 + T(3) * dT);
+        a[12] = rho * (ux2 * uy2 + (ux2 + uy2) * dT + dT * dT);
+        a[13] = rho * ux * uy * (uy2 + T(3) * dT);
+        a[14] = rho * (uy2 * uy2 + T(6) * uy2 * dT + T(3) * dT * dT);
+    }
+}
+
+// Eq. shock_function with alpha = 1 below 0.01
+template <typename T>
+__device__ __forceinline__ T sensor_alpha(T eps, T tau, T A) {
+    if (eps < T(0.01)) return T(1);
+    if (eps < T(0.10)) return T(1.05);
+    if (eps < T(1.00)) return A;
+    return T(1) / tau;
+}
+
+// ------------------------------------------------------------------ Newton (FP64)
+template <int Q> struct MB {
+    // raw monomials 1, x, y, xx, xy, yy, x r2, y r2 of velocity q
+    __host__ __device__ static constexpr double m(int q, int a) {
+        const double x = Lat<Q>::cx(q), y = Lat<Q>::cy(q), r2 = x * x + y * y;
+        return a == 0 ? 1.0 : a == 1 ? x : a == 2 ? y : a == 3 ? x * x : a == 4 ? x * y : a == 5 ? y * y : a == 6 ? x * r2 : y * r2;
+    }
+};
+
+template <int Q>
+__device__ __forceinline__ void newton_eval(const double* lam, const double* tgt, double* e, double* G) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) G[a] = -tgt[a];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        double s = 1.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) s += lam[a] * MB<Q>::m(q, a);
+        e[q] = exp(-s);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) G[a] += e[q] * MB<Q>::m(q, a);
+    }
+}
+
+// Cholesky solve of the packed SPD system A d = G (A lower triangle, row-major packed)
+__device__ __forceinline__ void chol8_solve(double* A, const double* G, double* d) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        double s = A[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+        const double djj = sqrt(s);
+        A[j * (j + 1) / 2 + j] = djj;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i) {
+            double t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+            A[i * (i + 1) / 2 + j] = t / djj;
+        }
+    }
+    double y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double t = G[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * y[k];
+        y[i] = t / A[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        double t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 8; ++k) t -= A[k * (k + 1) / 2 + i] * d[k];
+        d[i] = t / A[i * (i + 1) / 2 + i];
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void newton_dir(const double* e, const double* G, double* d) {
+    double A[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) A[k++] += e[q] * (MB<Q>::m(q, a) * MB<Q>::m(q, b));
+    }
+    chol8_solve(A, G, d);
+}
+
+// Solve for lambda (in/out) at (u, T); e[] receives exp(-(1 + lambda.M)) (rho = 1).
+// Returns the number of Newton steps; *conv = 1 if max |G| < tol.
+template <int Q>
+__device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double* lam, double* e, double tol,
+                                         int max_iter, int* conv) {
+    const double u2 = ux * ux + uy * uy, t2 = u2 + 4.0 * Tt;
+    const double tgt[8] = {1.0, ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
+    double G[8];
+    newton_eval<Q>(lam, tgt, e, G);
+    *conv = 0;
+    int it = 0;
+    for (;; ++it) {
+        double gmax = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) gmax = fmax(gmax, fabs(G[a]));
+        if (gmax < tol) { *conv = 1; break; }
+        if (it == max_iter) break;
+        double d[8];
+        newton_dir<Q>(e, G, d);
+        double g0 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
+        double t = 1.0;
+        double trial[8], Gt[8];
+#pragma unroll 1
+        for (int h = 0; h <= 30; ++h) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a) trial[a] = lam[a] + t * d[a];
+            newton_eval<Q>(trial, tgt, e, Gt);
+            double g1 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
+            if (g1 < g0 || h == 30) break;
+            t *= 0.5;
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) { lam[a] = trial[a]; G[a] = Gt[a]; }
+    }
+    return it;
+}
+
+}  // namespace lbm
