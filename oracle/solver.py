@@ -152,6 +152,10 @@ class Solver:
             self.g_[lev] = (2.0 * self.Cv - self.lat.D) * T[None, :] * feq
             if lam is not None:
                 self.lam[lev] = lam
+        # the boundary layers hold their boundary values from the start (Appendix A.3: the
+        # conditions are applied over the reach layers; here also to the initial state)
+        for lev in range(self.g.n_levels):
+            self._boundaries(lev)
 
     # ------------------------------------------------------------------ phases
     def _coalesced(self, lev: int):

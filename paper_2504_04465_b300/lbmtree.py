@@ -1,0 +1,257 @@
+"""Thin Python binding of liblbmtree.so (the C ABI declared in include/lbmtree.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.  The
+library must have been built (``python -m paper_2504_04465_b300.build``); importing this module
+without it raises ImportError -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbmtree.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2504_04465_b300.build`")
+
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ constants (include/lbmtree.h)
+OK = 0
+ERR = {-1: "ARG", -2: "STATE", -3: "CUDA", -4: "OOM", -5: "GRID", -6: "NEWTON", -7: "NONFINITE",
+       -10: "UNSUPPORTED"}
+LATTICE = {"D2Q9": 9, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
+MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4}
+STORAGE = {"f64": 1, "f32": 2, "f16dev": 3}
+FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}
+GUESS = {"warm": 0, "zero": 1, "poly": 2}
+FACES = ["x-", "x+", "y-", "y+", "z-", "z+"]
+CELL_FLUID, CELL_CGHOST, CELL_FGHOST, CELL_BC, CELL_SOLID = 1, 2, 3, 4, 5
+
+
+class CollisionParams(C.Structure):
+    _fields_ = [("nu0", C.c_double), ("T0", C.c_double), ("gamma", C.c_double), ("sensor_on", C.c_int),
+                ("sensor_A", C.c_double), ("newton_tol", C.c_double), ("newton_max_iter", C.c_int),
+                ("guess", C.c_int), ("rho_ref", C.c_double)]
+
+
+class Box(C.Structure):
+    _fields_ = [("level", C.c_int), ("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
+
+
+class Shape(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_cells", C.c_int64 * 8), ("n_blocks", C.c_int64 * 8), ("n_eq", C.c_double),
+                ("n_levels", C.c_int), ("block", C.c_int * 3), ("newton_iter_sum", C.c_int64),
+                ("newton_updates", C.c_int64), ("newton_nonconverged", C.c_int64),
+                ("newton_hist", C.c_int64 * 16), ("fine_iterations", C.c_int64),
+                ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64), ("cell_updates", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_sig = {
+    "lbm_create": [C.POINTER(_P), C.c_int, C.c_int, _P],
+    "lbm_destroy": [_P],
+    "lbm_set_lattice": [_P, C.c_int],
+    "lbm_set_collision": [_P, C.c_int, C.POINTER(CollisionParams)],
+    "lbm_set_precision": [_P, C.c_int],
+    "lbm_set_boundary": [_P, C.c_int, C.c_int, _D],
+    "lbm_set_block": [_P, C.c_int, C.c_int, C.c_int],
+    "lbm_build_grid": [_P, C.POINTER(C.c_int64), C.c_int, C.POINTER(Box), C.c_int, C.POINTER(Shape), C.c_int],
+    "lbm_cells": [_P, C.POINTER(C.c_int64), C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.POINTER(C.c_int32)),
+                  C.POINTER(C.POINTER(C.c_uint8))],
+    "lbm_velocities": [_P, C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_int32))],
+    "lbm_init_fields": [_P, _D, _D, _D],
+    "lbm_step": [_P, C.c_int64],
+    "lbm_step_fine": [_P, C.c_int64],
+    "lbm_use_graph": [_P, C.c_int],
+    "lbm_sync": [_P],
+    "lbm_read_moments": [_P, _D, _D, _D],
+    "lbm_read_populations": [_P, C.c_int, _D],
+    "lbm_conserved": [_P, _D],
+    "lbm_stats": [_P, C.POINTER(Stats)],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.lbm_last_error.argtypes = []
+_lib.lbm_last_error.restype = C.c_char_p
+
+EXPORTED = sorted(list(_sig) + ["lbm_last_error"])
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.lbm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {ERR.get(code, code)} ({msg})")
+
+
+def _check(code: int, where: str) -> None:
+    if code != OK:
+        raise LbmError(code, where)
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+class Context:
+    """One simulation: a grid, its populations and its stream (see include/lbmtree.h)."""
+
+    def __init__(self, dim: int, device: int = 0, stream: int | None = None):
+        h = _P()
+        _check(_lib.lbm_create(C.byref(h), dim, device, _P(stream) if stream else None), "lbm_create")
+        self._h = h
+        self.dim = dim
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- configuration
+    def set_lattice(self, name: str) -> None:
+        _check(_lib.lbm_set_lattice(self._h, LATTICE[name]), "lbm_set_lattice")
+
+    def set_collision(self, model: str, nu0: float = 0.0, T0: float = 0.0, gamma: float = 1.4,
+                      sensor_A: float | None = None, newton_tol: float = 1e-12, newton_max_iter: int = 50,
+                      guess: str = "warm", rho_ref: float = 1.0) -> None:
+        p = CollisionParams(nu0, T0, gamma, int(sensor_A is not None), sensor_A or 0.0, newton_tol,
+                            newton_max_iter, GUESS[guess], rho_ref)
+        _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
+
+    def set_precision(self, storage: str) -> None:
+        _check(_lib.lbm_set_precision(self._h, STORAGE[storage]), "lbm_set_precision")
+
+    def set_boundary(self, face: str, kind: str, rho: float = 1.0, u=(0.0, 0.0, 0.0), T: float = 0.0) -> None:
+        v = np.array([rho, *(list(u) + [0.0] * 3)[:3], T], dtype=np.float64)
+        _check(_lib.lbm_set_boundary(self._h, FACES.index(face), FACE_KIND[kind], _dptr(v)), "lbm_set_boundary")
+
+    def set_block(self, bx: int, by: int, bz: int = 1) -> None:
+        _check(_lib.lbm_set_block(self._h, bx, by, bz), "lbm_set_block")
+
+    def build_grid(self, extent, n_levels: int, boxes=(), solids=()) -> None:
+        ext = (C.c_int64 * 3)(*(list(extent) + [1, 1, 1])[:3])
+        bx = (Box * max(1, len(boxes)))()
+        for k, (lv, lo, hi) in enumerate(boxes):
+            bx[k].level = lv
+            bx[k].lo[:] = (list(lo) + [0, 0, 0])[:3]
+            bx[k].hi[:] = (list(hi) + [1, 1, 1])[:3]
+        sh = (Shape * max(1, len(solids)))()
+        for k, s in enumerate(solids):
+            if s["kind"] == "sphere":
+                sh[k].kind = 1
+                p = list(s["center"]) + [0.0] * (3 - len(s["center"])) + [s["radius"]]
+            elif s["kind"] == "naca":
+                sh[k].kind = 2
+                p = [s["chord"], s["x0"], s["y0"], s.get("t", 0.12)]
+            else:
+                raise ValueError(s["kind"])
+            sh[k].p[: len(p)] = p
+        _check(_lib.lbm_build_grid(self._h, ext, n_levels, bx, len(boxes), sh, len(solids)), "lbm_build_grid")
+
+    def configure(self, spec, lattice: str, model: str, storage: str = "f64", block=None, **coll) -> None:
+        """Apply a grid specification (see paper_2504_04465_b300.inputs.GridSpec) and build."""
+        self.set_lattice(lattice)
+        self.set_collision(model, **coll)
+        self.set_precision(storage)
+        for ax in range(spec.dim):
+            for side in "-+":
+                f = "xyz"[ax] + side
+                if spec.periodic[ax]:
+                    self.set_boundary(f, "periodic")
+                else:
+                    fs = spec.faces[f]
+                    kind = fs[0]
+                    rho = fs[1] if len(fs) > 1 else 1.0
+                    u = fs[2] if len(fs) > 2 else (0.0, 0.0, 0.0)
+                    T = fs[3] if len(fs) > 3 and fs[3] is not None else 0.0
+                    self.set_boundary(f, kind, rho, u, T)
+        if block is not None:
+            self.set_block(*block)
+        self.build_grid(spec.extent, spec.n_levels, spec.boxes, spec.solids)
+
+    # -------------------------------------------------------------- cells
+    def cells(self):
+        """(level (n,), xyz (n, 3), type (n,)) in the library's cell order (copies)."""
+        n = C.c_int64()
+        lv = C.POINTER(C.c_int32)()
+        xyz = C.POINTER(C.c_int32)()
+        ty = C.POINTER(C.c_uint8)()
+        _check(_lib.lbm_cells(self._h, C.byref(n), C.byref(lv), C.byref(xyz), C.byref(ty)), "lbm_cells")
+        N = n.value
+        return (np.ctypeslib.as_array(lv, (N,)).copy() if N else np.zeros(0, np.int32),
+                np.ctypeslib.as_array(xyz, (N, 3)).copy() if N else np.zeros((0, 3), np.int32),
+                np.ctypeslib.as_array(ty, (N,)).copy() if N else np.zeros(0, np.uint8))
+
+    def velocities(self) -> np.ndarray:
+        q = C.c_int()
+        xi = C.POINTER(C.c_int32)()
+        _check(_lib.lbm_velocities(self._h, C.byref(q), C.byref(xi)), "lbm_velocities")
+        return np.ctypeslib.as_array(xi, (q.value, 3)).copy()
+
+    # -------------------------------------------------------------- fields and stepping
+    def init_fields(self, rho, u, T=None) -> None:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        T = None if T is None else np.ascontiguousarray(T, dtype=np.float64)
+        _check(_lib.lbm_init_fields(self._h, _dptr(rho), _dptr(u), _dptr(T)), "lbm_init_fields")
+
+    def step(self, n_coarse: int) -> None:
+        _check(_lib.lbm_step(self._h, n_coarse), "lbm_step")
+
+    def step_fine(self, n_fine: int) -> None:
+        _check(_lib.lbm_step_fine(self._h, n_fine), "lbm_step_fine")
+
+    def use_graph(self, on: bool = True) -> None:
+        _check(_lib.lbm_use_graph(self._h, int(on)), "lbm_use_graph")
+
+    def sync(self) -> None:
+        _check(_lib.lbm_sync(self._h), "lbm_sync")
+
+    # -------------------------------------------------------------- outputs
+    def moments(self):
+        n = self.cells()[0].size
+        rho = np.empty(n)
+        u = np.empty(self.dim * n)
+        T = np.empty(n)
+        _check(_lib.lbm_read_moments(self._h, _dptr(rho), _dptr(u), _dptr(T)), "lbm_read_moments")
+        return rho, u.reshape(self.dim, n), T
+
+    def populations(self, which: str = "f") -> np.ndarray:
+        n = self.cells()[0].size
+        k = {"f": 0, "g": 1, "lambda": 2}[which]
+        m = 8 if which == "lambda" else self.velocities().shape[0]
+        out = np.empty(m * n)
+        _check(_lib.lbm_read_populations(self._h, k, _dptr(out)), "lbm_read_populations")
+        return out.reshape(m, n)
+
+    def conserved(self) -> np.ndarray:
+        out = np.empty(5)
+        _check(_lib.lbm_conserved(self._h, _dptr(out)), "lbm_conserved")
+        return out
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(_lib.lbm_stats(self._h, C.byref(s)), "lbm_stats")
+        return s
