@@ -1,0 +1,122 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared entry point, rejects
+bad calls with the documented codes, and its host grid builder reproduces the oracle's cell sets
+(host-only contexts, device < 0, run no kernel)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import grid as G
+from oracle import lattices as L
+from paper_2504_04465_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbmtree.h")
+
+
+@pytest.fixture(scope="module")
+def lt():
+    from paper_2504_04465_b300.build import build
+    build()
+    from paper_2504_04465_b300 import lbmtree
+    return lbmtree
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(lbm_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lt):
+    names = declared_functions()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", lt.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(lbm_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert set(names) <= set(lt.EXPORTED)
+
+
+def test_build_targets_sm103a():
+    from paper_2504_04465_b300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_bad_arguments(lt):
+    with pytest.raises(lt.LbmError) as e:
+        lt.Context(4, device=-1)
+    assert e.value.code == -1
+    c = lt.Context(2, device=-1)
+    with pytest.raises(lt.LbmError):
+        c.set_lattice("D3Q27")                       # dimension mismatch
+    c.set_lattice("D2Q9")
+    with pytest.raises(lt.LbmError) as e:
+        c.build_grid((64, 64), 1)                    # collision model not set
+    assert e.value.code == -2
+    c.set_collision("rr", nu0=0.01)
+    with pytest.raises(lt.LbmError) as e:
+        c.step(1)                                    # nothing built
+    assert e.value.code == -2
+    with pytest.raises(lt.LbmError) as e:            # misaligned box
+        c.build_grid((64, 64), 2, [(0, (15, 16), (48, 48))])
+    assert e.value.code == -5
+    c2 = lt.Context(2, device=-1)
+    c2.set_lattice("D2Q9")
+    c2.set_collision("poly_ddf")
+    with pytest.raises(lt.LbmError) as e:
+        c2.build_grid((64, 64), 1)
+    assert e.value.code == -10
+
+
+def _compare(lt, spec, latname, model, block=None):
+    g = G.build(spec, L.LATTICES[latname])
+    c = lt.Context(spec.dim, device=-1)
+    c.configure(spec, latname, model, block=block)
+    lv, xyz, ty = c.cells()
+    for i, olv in enumerate(g.levels):
+        m = lv == i
+        got = {tuple(int(a) for a in x[: spec.dim]): int(t) for x, t in zip(xyz[m], ty[m])}
+        exp = {tuple(int(v) for v in x): int(t) for x, t in zip(olv.coords, olv.ctype)}
+        assert got == exp, i
+    assert c.stats().n_eq == pytest.approx(g.n_eq())
+    return c
+
+
+SPECS = [
+    ("tg2", lambda: I.taylor_green_spec(64, 16, 48, 2), "D2Q9", "rr", None),
+    ("tg2_32x8", lambda: I.taylor_green_spec(64, 16, 48, 2), "D2Q9", "bgk", (32, 8, 1)),
+    ("three_levels", lambda: I.GridSpec(2, (128, 128), 3, [(1, (32, 32), (96, 96)), (0, (48, 48), (80, 80))], (True, True)), "D2Q9", "bgk", None),
+    ("reach3_q37", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q37", "poly_ddf", None),
+    ("reach3_q21", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q21", "num_ddf", None),
+    ("sod_band", lambda: I.sod_spec(256, 32, 2, (64, 192)), "D2Q37", "poly_ddf", None),
+    ("solid", lambda: I.GridSpec(2, (64, 64), 2, [(0, (16, 16), (48, 48))], (True, True),
+                                 solids=[{"kind": "sphere", "center": (32.0, 32.0), "radius": 5.0}]), "D2Q9", "rr", None),
+    ("channel_ragged", lambda: I.GridSpec(2, (200, 128), 3, [(1, (40, 32), (160, 96)), (0, (64, 48), (128, 80))], (False, True),
+                                          {"x-": ("dirichlet_rho", 1.0, (0.05, 0.0, 0.0)), "x+": ("neumann",)},
+                                          [{"kind": "sphere", "center": (88.0, 64.0), "radius": 6.0}]), "D2Q9", "rr", None),
+    ("naca", lambda: I.GridSpec(2, (256, 128), 2, [(0, (64, 32), (192, 96))], (False, False),
+                                {f: ("neumann",) for f in ("x-", "x+", "y-", "y+")},
+                                [{"kind": "naca", "chord": 80.0, "x0": 88.0, "y0": 64.0}]), "D2Q21", "num_ddf", None),
+    ("d3q27_sphere", lambda: I.GridSpec(3, (64, 32, 32), 2, [(0, (16, 8, 8), (48, 24, 24))], (False, True, True),
+                                        {"x-": ("dirichlet_rho", 1.0, (0.04, 0.0, 0.0)), "x+": ("neumann",)},
+                                        [{"kind": "sphere", "center": (32.0, 16.0, 16.0), "radius": 4.0}]), "D3Q27", "rr", None),
+]
+
+
+@pytest.mark.parametrize("name,mk,latname,model,block", SPECS, ids=[s[0] for s in SPECS])
+def test_host_builder_matches_oracle(lt, name, mk, latname, model, block):
+    _compare(lt, mk(), latname, model, block)
+
+
+def test_velocity_sets_match_oracle(lt):
+    for latname, dim, model in (("D2Q9", 2, "rr"), ("D2Q21", 2, "num_ddf"), ("D2Q37", 2, "poly_ddf"), ("D3Q27", 3, "rr")):
+        c = lt.Context(dim, device=-1)
+        c.set_lattice(latname)
+        c.set_collision(model)
+        ext = (32, 32) if dim == 2 else (8, 8, 8)
+        c.build_grid(ext, 1)
+        xi = c.velocities()[:, :dim]
+        assert {tuple(int(a) for a in v) for v in xi} == {tuple(int(a) for a in v) for v in L.LATTICES[latname].xi}
+        assert np.array_equal(xi[::-1], -xi)          # opposite of q is Q-1-q

@@ -1,0 +1,206 @@
+"""Parity of the CUDA path with the FP64 oracle on the same seeded inputs (GPU required).
+
+Tolerances: FP64 storage, relative L2 of rho, u, T <= 1e-12; FP32 storage <= 1e-5 (Taylor-Green
+after 1000 fine iterations); FP16 deviations: error stated by the test (binary16 rounding of the
+deviation, unit roundoff 4.9e-4 relative to w_i rho_ref, accumulated over the run).
+"""
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+from oracle import lattices as L
+from paper_2504_04465_b300 import inputs as I
+
+from . import harness as H
+
+pytestmark = pytest.mark.gpu
+
+TG_SPEC = I.taylor_green_spec(64, 16, 48, 2)          # 64x64 coarse periodic, 32x32-coarse patch
+TG_FINE = 1000                                         # 500 coarse steps
+
+
+@lru_cache(maxsize=None)
+def tg_oracle(model):
+    return H.run_oracle(TG_SPEC, "D2Q9", model, H.tg_fields(64, 2), TG_FINE, nu0=0.02)
+
+
+def tg_gpu(model, storage, graph=False):
+    ctx = H.make_gpu(TG_SPEC, "D2Q9", model, storage, H.tg_fields(64, 2), nu0=0.02)
+    if graph:
+        ctx.use_graph(True)
+    ctx.step(TG_FINE // 2)
+    ctx.sync()
+    return ctx
+
+
+@pytest.mark.parametrize("model", ["bgk", "rr"])
+def test_taylor_green_two_level_f64(model):
+    sol = tg_oracle(model)
+    ctx = tg_gpu(model, "f64")
+    err = H.compare_moments(sol, ctx)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12, err
+    assert H.compare_populations(sol, ctx) < 1e-12
+
+
+@pytest.mark.parametrize("model", ["bgk", "rr"])
+def test_taylor_green_two_level_f32(model):
+    sol = tg_oracle(model)
+    err = H.compare_moments(sol, tg_gpu(model, "f32"))
+    print("f32 error", model, err)
+    assert err["rho"] < 1e-5 and err["u"] < 1e-5, err
+
+
+@pytest.mark.parametrize("model", ["bgk", "rr"])
+def test_taylor_green_two_level_f16dev(model):
+    sol = tg_oracle(model)
+    err = H.compare_moments(sol, tg_gpu(model, "f16dev"))
+    print("f16dev error", model, err)
+    assert err["rho"] < 1e-3 and err["u"] < 5e-2, err
+
+
+def test_graph_matches_plain_launches_bitwise():
+    a = tg_gpu("rr", "f64", graph=False)
+    b = tg_gpu("rr", "f64", graph=True)
+    assert np.array_equal(a.populations("f"), b.populations("f"))
+    assert b.stats().kernel_launches == a.stats().kernel_launches
+
+
+def test_ledger_matches_oracle_and_is_conserved():
+    fn = H.tg_fields(64, 2, seed=7, amp=0.01)
+    sol = H.run_oracle(TG_SPEC, "D2Q9", "rr", fn, 0, nu0=0.02)
+    ctx = H.make_gpu(TG_SPEC, "D2Q9", "rr", "f64", fn, nu0=0.02)
+    l0_o, l0_g = sol.ledger(), ctx.conserved()
+    assert abs(l0_g[0] - l0_o[0]) < 1e-12 * l0_o[0]
+    assert np.abs(l0_g[1:3] - l0_o[1:3]).max() < 1e-12 * l0_o[0]
+    sol.step_coarse(50)
+    ctx.step(50)
+    l1_o, l1_g = sol.ledger(), ctx.conserved()
+    assert abs(l1_g[0] - l1_o[0]) < 1e-12 * l0_o[0]
+    ctx.step(50)
+    l2_g = ctx.conserved()
+    assert abs(l2_g[0] - l0_g[0]) < 1e-13 * l0_g[0]
+    assert np.abs(l2_g[1:3] - l0_g[1:3]).max() < 1e-13 * l0_g[0]
+
+
+def test_empty_fine_patch_equals_uniform_coarse_bitwise():
+    fn = H.tg_fields(32, 1)
+    two = I.GridSpec(2, (64, 64), 2, [], (True, True))
+    one = I.GridSpec(2, (32, 32), 1, [], (True, True))
+    a = H.make_gpu(two, "D2Q9", "bgk", "f64", lambda lv, c, x: fn(lv, c, x / 2.0), nu0=0.02)
+    b = H.make_gpu(one, "D2Q9", "bgk", "f64", fn, nu0=0.01)
+    a.step_fine(20)
+    b.step_fine(10)
+    assert np.array_equal(a.populations("f"), b.populations("f"))
+
+
+# ------------------------------------------------------------------ channel with a cylinder, 3 levels
+CH_SPEC = I.GridSpec(2, (200, 128), 3, [(1, (40, 32), (160, 96)), (0, (64, 48), (128, 80))], (False, True),
+                     {"x-": ("dirichlet_rho", 1.0, (0.05, 0.0, 0.0)), "x+": ("neumann",)},
+                     [{"kind": "sphere", "center": (88.0, 64.0), "radius": 6.0}])
+
+
+def ch_fields(level, coords, c):
+    n = coords.shape[0]
+    u = np.stack([np.full(n, 0.05), np.zeros(n)]) + 0.005 * np.stack([I.uniform_at(11, level, coords, k) for k in range(2)])
+    return np.ones(n), u
+
+
+def test_channel_three_levels_cylinder_f64():
+    sol = H.run_oracle(CH_SPEC, "D2Q9", "rr", ch_fields, 4 * 40, nu0=0.02)
+    ctx = H.make_gpu(CH_SPEC, "D2Q9", "rr", "f64", ch_fields, nu0=0.02)
+    ctx.step(40)
+    err = H.compare_moments(sol, ctx)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12, err
+
+
+# ------------------------------------------------------------------ D3Q27 two levels with a sphere
+D3_SPEC = I.GridSpec(3, (64, 32, 32), 2, [(0, (16, 8, 8), (48, 24, 24))], (False, True, True),
+                     {"x-": ("dirichlet_rho", 1.0, (0.04, 0.0, 0.0)), "x+": ("neumann",)},
+                     [{"kind": "sphere", "center": (32.0, 16.0, 16.0), "radius": 4.0}])
+
+
+def d3_fields(level, coords, c):
+    n = coords.shape[0]
+    u = np.stack([np.full(n, 0.04), np.zeros(n), np.zeros(n)])
+    u = u + 0.004 * np.stack([I.uniform_at(3900, level, coords, k) for k in range(3)])
+    return np.ones(n), u
+
+
+@lru_cache(maxsize=None)
+def d3_oracle():
+    return H.run_oracle(D3_SPEC, "D3Q27", "rr", d3_fields, 2 * 10, nu0=0.01)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16dev", 3e-2)])
+def test_d3q27_two_level_sphere(storage, tol):
+    sol = d3_oracle()
+    ctx = H.make_gpu(D3_SPEC, "D3Q27", "rr", storage, d3_fields, nu0=0.01)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    print("d3q27", storage, err)
+    assert err["rho"] < tol and err["u"] < tol, err
+
+
+# ------------------------------------------------------------------ D2Q37 polynomial DDF, Sod band
+SOD_SPEC = I.sod_spec(256, 32, 2, (64, 192))
+
+
+@lru_cache(maxsize=None)
+def sod37_oracle():
+    return H.run_oracle(SOD_SPEC, "D2Q37", "poly_ddf", H.sod_fields(256, L.D2Q37.cs2), 40, nu0=0.0, sensor_A=1.5)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-4)])
+def test_d2q37_sod_band(storage, tol):
+    sol = sod37_oracle()
+    ctx = H.make_gpu(SOD_SPEC, "D2Q37", "poly_ddf", storage, H.sod_fields(256, L.D2Q37.cs2), nu0=0.0, sensor_A=1.5)
+    ctx.step_fine(40)
+    err = H.compare_moments(sol, ctx)
+    print("d2q37", storage, err)
+    assert err["rho"] < tol and err["u"] < tol and err["T"] < tol, err
+
+
+# ------------------------------------------------------------------ D2Q21 numerical DDF
+N21_SPEC = I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True))
+
+
+def test_d2q21_numerical_two_level_f64():
+    fn = H.smooth_comp_fields((96, 64), 0.9)
+    sol = H.run_oracle(N21_SPEC, "D2Q21", "num_ddf", fn, 20, nu0=0.01, T0=0.9, sensor_A=1.35)
+    ctx = H.make_gpu(N21_SPEC, "D2Q21", "num_ddf", "f64", fn, nu0=0.01, T0=0.9, sensor_A=1.35)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    s = ctx.stats()
+    assert s.newton_updates > 0 and s.newton_nonconverged == 0
+    assert s.newton_iter_sum / s.newton_updates < 4
+
+
+SUP_SPEC = I.GridSpec(2, (128, 32), 1, [], (False, True),
+                      {"x-": ("dirichlet", 1.0, (0.6, 0.0, 0.0), 0.9), "x+": ("neumann",)})
+
+
+def sup_fields(level, coords, c):
+    n = coords.shape[0]
+    rho = 1 + 0.2 * np.exp(-((c[:, 0] - 64) ** 2) / 50)
+    return rho, np.stack([np.full(n, 0.6), np.zeros(n)]), np.full(n, 0.9)
+
+
+@pytest.mark.parametrize("guess", ["warm", "poly", "zero"])
+def test_d2q21_supersonic_inlet_f64(guess):
+    sol = H.run_oracle(SUP_SPEC, "D2Q21", "num_ddf", sup_fields, 30, nu0=0.01, T0=0.9, sensor_A=1.35, guess=guess)
+    ctx = H.make_gpu(SUP_SPEC, "D2Q21", "num_ddf", "f64", sup_fields, nu0=0.01, T0=0.9, sensor_A=1.35, guess=guess)
+    ctx.step_fine(30)
+    err = H.compare_moments(sol, ctx)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+
+
+def test_d2q21_f32_populations_fp64_newton():
+    fn = H.smooth_comp_fields((96, 64), 0.9)
+    sol = H.run_oracle(N21_SPEC, "D2Q21", "num_ddf", fn, 20, nu0=0.01, T0=0.9, sensor_A=1.35)
+    ctx = H.make_gpu(N21_SPEC, "D2Q21", "num_ddf", "f32", fn, nu0=0.01, T0=0.9, sensor_A=1.35)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    print("d2q21 f32", err)
+    assert err["rho"] < 1e-5 and err["u"] < 1e-4 and err["T"] < 1e-5, err
