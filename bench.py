@@ -1,0 +1,297 @@
+"""Benchmark of the multi-level collide-and-stream path (one JSON line on rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--storage f32|f16dev|f64] [--no-graph]
+
+Workload: D3Q27 recursive-regularized flow past a sphere (diameter 64 finest cells) in a
+1024x512x512 finest-unit box with 4 levels (about 45 M cells, 38.9 M fine-equivalent), inflow
+Mach 0.1, Re 3900, seeded 1e-3 velocity perturbation.  A step is one coarse step (8 fine
+iterations, every level advanced on its schedule).  Metric: fine-equivalent MLUPS = cell updates
+per second (sum over levels of cells x updates per coarse step), aggregated over ranks.
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the path has no
+exchange step); the time is the max over ranks and the value the sum of their updates.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload (the
+reduced copy at 1/4 extents, sphere diameter 16, same level structure), one fine iteration per
+step, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_04465_b300 import inputs as I  # noqa: E402
+
+BYTES_PER_UPDATE = {"f64": 432, "f32": 216, "f16dev": 108}   # 27 populations read + written
+WORKLOAD = ("D3Q27 recursive-regularized, flow past a sphere (D = 64 finest cells), 4 levels, "
+            "1024x512x512 finest-unit box, Ma 0.1, Re 3900")
+# dram bytes per cell update of the step kernel from the ncu capture summarised in
+# profiles/k_step_d3q27_sphere.md (None until a capture of the current kernel exists)
+NCU_TRAFFIC_PER_UPDATE = {"f32": None, "f16dev": None, "f64": None}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_context(spec, storage, device, stream, graph, scale=1):
+    from paper_2504_04465_b300 import lbmtree as lt
+    ctx = lt.Context(3, device=device, stream=stream)
+    ctx.configure(spec, "D3Q27", "rr", storage, nu0=I.sphere_nu0(scale))
+    if graph:
+        ctx.use_graph(True)
+    return ctx
+
+
+def host_fields(ctx):
+    lv, xyz, _ = ctx.cells()
+    n = lv.size
+    rho = np.ones(n)
+    u = np.zeros((3, n))
+    for level in np.unique(lv):
+        m = lv == level
+        r, uu = I.sphere_fields(int(level), xyz[m])
+        rho[m] = r
+        u[:, m] = uu
+    return rho, u
+
+
+def cpu_sample(n_fine: int):
+    """Oracle on the reduced sphere workload: (MLUPS, seconds, cell updates)."""
+    from oracle import grid as G
+    from oracle import lattices as L
+    from oracle import solver as S
+    g = G.build(I.sphere_spec(4), L.D3Q27)
+    s = S.Solver(g, "rr", nu0=I.sphere_nu0(4))
+    s.init_fields([(*I.sphere_fields(lv.level, lv.coords), None) for lv in g.levels])
+    counts = [int((lv.ctype != G.SOLID).sum()) for lv in g.levels]
+    return s, counts
+
+
+def oracle_updates(counts, t0, n):
+    """Cell updates of fine iterations t0 .. t0+n-1 (level i updates when t % 2^i == 0)."""
+    return sum(c for t in range(t0, t0 + n) for i, c in enumerate(counts) if t % (1 << i) == 0)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    s, counts = cpu_sample(0)
+    for _ in range(args.warmup):
+        s.fine_iteration()
+    t0 = s.t
+    start = time.perf_counter()
+    for _ in range(args.steps):
+        s.fine_iteration()
+    dt = time.perf_counter() - start
+    upd = oracle_updates(counts, t0, args.steps)
+    v = upd / dt / 1e6
+    sample = (f"FP64 numpy oracle, reduced sphere workload (256x128x128, sphere D=16, 4 levels, "
+              f"{sum(counts)} cells), {args.steps} fine iterations after {args.warmup} warm-up")
+    line = {"impl": "reference", "metric": "fine-equivalent MLUPS", "value": v, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "reduced copy at 1/4 extents", "step": "one fine iteration"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    spec = I.sphere_spec(args.scale)
+    graph = not args.no_graph
+    ctx = make_context(spec, args.storage, local, stream.cuda_stream, graph, args.scale)
+    rho, u = host_fields(ctx)
+    ctx.init_fields(rho, u)
+    st = ctx.stats()
+    updates_per_step = st.cell_updates              # one coarse step
+    for _ in range(args.warmup):
+        ctx.step(1)
+    ctx.sync()
+    l0 = ctx.stats().kernel_launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            ctx.step(args.steps)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        if dist:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.stats().kernel_launches - l0
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    total_updates = updates_per_step * args.steps * world
+    value = total_updates / (t_max * 1e-3) / 1e6
+    # roofline of the step kernel: it is the only kernel of the timed region
+    bpu = BYTES_PER_UPDATE[args.storage]
+    achieved = bpu * updates_per_step * args.steps / (ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = NCU_TRAFFIC_PER_UPDATE.get(args.storage)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "bytes_per_update": bpu,
+            "traffic": None if traffic is None else traffic * updates_per_step * args.steps / max(launches, 1)}
+    # end to end through the public API with host buffers: upload the fields, step, read the
+    # conserved totals every step and the moments at the end
+    e2e = None
+    if not args.no_e2e:
+        n = rho.size
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.init_fields(rho, u)
+        for _ in range(args.steps):
+            ctx.step(1)
+            ctx.conserved()
+        m = ctx.moments()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = (rho.nbytes + u.nbytes) / args.steps
+        d2h = 5 * 8 + sum(a.nbytes for a in m) / args.steps
+        e2e = {"value": updates_per_step * args.steps * world / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "note": "init_fields from host arrays once, step + conserved() per step, read_moments once; "
+                       "bytes per step are the totals / steps"}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu:
+        s, counts = cpu_sample(0)
+        t0 = time.perf_counter()
+        nf = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            s.fine_iteration()
+            nf += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": oracle_updates(counts, 0, nf) / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, reduced sphere workload (256x128x128, D=16, 4 levels), {nf} fine "
+                         f"iterations in {dt:.1f} s"}
+    line = {"metric": "fine-equivalent MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.scale == 1 else f"{WORKLOAD}, extents / {args.scale}",
+                       "storage": args.storage, "cells": int(sum(st.n_cells[:4])),
+                       "n_eq": st.n_eq, "cell_updates_per_step": int(updates_per_step),
+                       "step": "one coarse step = 8 fine iterations", "cuda_graph": graph,
+                       "l2": "inputs larger than L2 (9.7 GB of populations at f32)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "f64"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--scale", type=int, default=1, choices=[1, 2, 4],
+                    help="1: the full workload; 2, 4: copies with extents divided by 2, 4 (profiling, tests)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -16,8 +16,8 @@
  *     (non-converged Newton solve) record it in a device status word that lbm_sync() returns.
  *   - The library owns every device array.  Host input arrays are copied during the call and may
  *     be freed afterwards.  Host views returned by the library stay valid until lbm_destroy().
- *   - All device work is issued on the stream given to lbm_create() (NULL = the legacy default
- *     stream).  lbm_step() is asynchronous; calls that return host data synchronise the stream.
+ *   - All device work is issued on the stream given to lbm_create() (NULL = a non-blocking
+ *     stream created and owned by the context).  lbm_step() is asynchronous; calls that return host data synchronise the stream.
  *   - Levels: level 0 is the finest; a level-i cell has edge 2^i in finest units.  Coordinates
  *     are integer cell indices at the cell's own level.
  */
@@ -126,7 +126,8 @@ typedef struct {
 } lbm_stats_t;
 
 /* ---------------------------------------------------------------- lifecycle */
-/* Create a context bound to `device` and `stream` (cudaStream_t or NULL).  dim = 2 or 3.
+/* Create a context bound to `device` and `stream` (cudaStream_t, or NULL for a stream owned by
+ * the context).  dim = 2 or 3.
  * device < 0 makes a host-only context: grids can be built and inspected, nothing runs. */
 int lbm_create(lbm_ctx** out, int dim, int device, void* stream);
 /* Release every device and host resource of the context.  NULL is accepted. */

@@ -72,6 +72,7 @@ struct lbm_ctx {
     int dim = 2, device = 0;
     bool host_only = false;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;        // created by the context (caller passed NULL)
     int lattice = 0, model = 0, storage = LBM_F64;
     bool params_set = false;
     lbm_collision_params params{};
@@ -254,8 +255,17 @@ int build_graph(lbm_ctx* c) {
         const int64_t nb = iteration_args(c, k, a);
         if (nb) c->ks.step(a, nb, c->stream);
     }
+    if (cudaGetLastError() != cudaSuccess) {       // end the capture so the stream stays usable
+        cudaGraph_t g2 = nullptr;
+        cudaStreamEndCapture(c->stream, &g2);
+        if (g2) cudaGraphDestroy(g2);
+        return fail(LBM_ERR_CUDA, "launch during graph capture failed");
+    }
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
     e = cudaGraphInstantiate(&c->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -298,6 +308,15 @@ int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
             delete c;
             return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
         }
+        if (!c->stream) {
+            // a stream of our own: the legacy default stream cannot be captured into a graph
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                delete c;
+                return fail(LBM_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+            }
+            c->own_stream = true;
+        }
         std::lock_guard<std::mutex> lk(g_upload_mu);
         if (device < 256 && !g_uploaded[device]) {
             const Constants& k = constants();
@@ -318,6 +337,7 @@ int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
     if (!c->host_only) cudaSetDevice(c->device);
     c->release();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
 }

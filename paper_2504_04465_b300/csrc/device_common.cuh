@@ -5,7 +5,9 @@
 // f[q * ncell + cell] with cell = block * BS + local.  Two buffers per level (A/B, the
 // "two-population" storage of Sec. 4.1).  The stored state of a cell is its post-collision
 // populations; a step gathers f_i(x) = f*_i(x - xi_i) from the other buffer (pull form of
-// Eqs. CollisionStep/StreamingStep), collides and writes its own slot.
+// Eqs. CollisionStep/StreamingStep), collides and writes its own slot.  The weakly compressible
+// models store and compute deviations f_i - w_i rho_ref (FP64/FP32 plain, binary16 relative), so
+// that FP32 rounding acts on small numbers.
 #pragma once
 #include <cuda_fp16.h>
 #include <cstdint>
@@ -20,28 +22,29 @@ template <int ST> struct Store;
 template <> struct Store<ST_F64> {
     using T = double;     // arithmetic type
     using S = double;     // stored type
-    static __device__ __forceinline__ T load(const void* p, long long i, T) { return __ldg((const double*)p + i); }
-    static __device__ __forceinline__ void store(void* p, long long i, T v, T) { ((double*)p)[i] = v; }
+    template <bool DEV> static __device__ __forceinline__ T load(const void* p, long long i, T) { return __ldg((const double*)p + i); }
+    template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T) { ((double*)p)[i] = v; }
 };
 
 template <> struct Store<ST_F32> {
     using T = float;
     using S = float;
-    static __device__ __forceinline__ T load(const void* p, long long i, T) { return __ldg((const float*)p + i); }
-    static __device__ __forceinline__ void store(void* p, long long i, T v, T) { ((float*)p)[i] = v; }
+    template <bool DEV> static __device__ __forceinline__ T load(const void* p, long long i, T) { return __ldg((const float*)p + i); }
+    template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T) { ((float*)p)[i] = v; }
 };
 
-// binary16 deviation from the reference value ref = w_i rho_ref (or the g reference):
-// stored d = v / ref - 1 (round to nearest even), loaded v = ref (1 + d); arithmetic in FP32.
+// binary16 deviation relative to the reference value ref = w_i rho_ref (or the g reference):
+// stored d = v / ref - 1 (round to nearest even); arithmetic in FP32.  With DEV the arithmetic
+// value is itself the deviation v - ref (weakly compressible models), else the population v.
 template <> struct Store<ST_F16DEV> {
     using T = float;
     using S = __half;
-    static __device__ __forceinline__ T load(const void* p, long long i, T ref) {
-        const __half h = ((const __half*)p)[i];
-        return ref * (1.0f + __half2float(h));
+    template <bool DEV> static __device__ __forceinline__ T load(const void* p, long long i, T ref) {
+        const float h = __half2float(((const __half*)p)[i]);
+        return DEV ? ref * h : ref * (1.0f + h);
     }
-    static __device__ __forceinline__ void store(void* p, long long i, T v, T ref) {
-        ((__half*)p)[i] = __float2half_rn(v / ref - 1.0f);
+    template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T ref) {
+        ((__half*)p)[i] = __float2half_rn(DEV ? v / ref : v / ref - 1.0f);
     }
 };
 

@@ -42,6 +42,7 @@ __device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, do
 
 struct D2Q21M {
     static constexpr int D = 2, Q = 21;
+    static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<21>::cx(q); }
     __host__ __device__ static constexpr int cy(int q) { return Lat<21>::cy(q); }

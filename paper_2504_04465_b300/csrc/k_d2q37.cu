@@ -13,6 +13,7 @@ static __constant__ double ccs2_37;
 
 struct D2Q37M {
     static constexpr int D = 2, Q = 37;
+    static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = false, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }
     __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }

@@ -6,6 +6,7 @@ namespace lbm {
 
 template <bool RR_> struct D2Q9M {
     static constexpr int D = 2, Q = 9;
+    static constexpr bool DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
     __host__ __device__ static constexpr int cx(int q) { return TP<2>::cx(q); }
     __host__ __device__ static constexpr int cy(int q) { return TP<2>::cy(q); }

@@ -6,6 +6,7 @@ namespace lbm {
 
 template <bool RR_> struct D3Q27M {
     static constexpr int D = 3, Q = 27;
+    static constexpr bool DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
     __host__ __device__ static constexpr int cx(int q) { return TP<3>::cx(q); }
     __host__ __device__ static constexpr int cy(int q) { return TP<3>::cy(q); }

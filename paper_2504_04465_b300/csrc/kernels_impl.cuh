@@ -10,7 +10,8 @@
 // level i's coarse-ghost cells, which read level i-1's buffer rd_{i-1} (coalescence) and write the
 // fine-ghost slots of rd_{i-1} ^ 1 (explosion); level i-1 skips its fine ghosts at that iteration.
 //
-// Model policy M: D, Q, HAS_G, HAS_LAM, RR, cx/cy/cz(q), w(q); compressible models also
+// Model policy M: D, Q, DEV (values are deviations f - w rho_ref), HAS_G, HAS_LAM, RR,
+// cx/cy/cz(q), w(q); compressible models also
 //   template <int ST> static void feq(m, rho, ux, uy, T, lam, feq, iters, conv)
 //   static void init_guess(ux, uy, T, lam)
 #pragma once
@@ -46,21 +47,21 @@ template <class M, int ST>
 __device__ __forceinline__ void load_pop(const LevelDev& L, int buf, long long src, int q, const ModelDev& m,
                                          typename Store<ST>::T& fo, typename Store<ST>::T& go) {
     using T = typename Store<ST>::T;
-    if (src < 0) {
-        fo = T(0);
+    if (src < 0) {                                       // no source: a zero population
+        fo = M::DEV ? -ref_f<M, ST>(m, q) : T(0);
         go = T(0);
         return;
     }
-    fo = Store<ST>::load(L.f[buf], (long long)q * L.ncell + src, ref_f<M, ST>(m, q));
-    if constexpr (M::HAS_G) go = Store<ST>::load(L.g[buf], (long long)q * L.ncell + src, ref_g<M, ST>(m, q));
+    fo = Store<ST>::template load<M::DEV>(L.f[buf], (long long)q * L.ncell + src, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) go = Store<ST>::template load<false>(L.g[buf], (long long)q * L.ncell + src, ref_g<M, ST>(m, q));
     else go = T(0);
 }
 
 template <class M, int ST>
 __device__ __forceinline__ void store_pop(const LevelDev& L, int buf, long long cell, int q, const ModelDev& m,
                                           typename Store<ST>::T fv, typename Store<ST>::T gv) {
-    Store<ST>::store(L.f[buf], (long long)q * L.ncell + cell, fv, ref_f<M, ST>(m, q));
-    if constexpr (M::HAS_G) Store<ST>::store(L.g[buf], (long long)q * L.ncell + cell, gv, ref_g<M, ST>(m, q));
+    Store<ST>::template store<M::DEV>(L.f[buf], (long long)q * L.ncell + cell, fv, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[buf], (long long)q * L.ncell + cell, gv, ref_g<M, ST>(m, q));
 }
 
 // macroscopic moments (rho, u, T) of f, g (T from Eq. polyTemp)
@@ -68,7 +69,7 @@ template <class M, int ST>
 __device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c, typename Store<ST>::T& rho,
                                         typename Store<ST>::T* u, typename Store<ST>::T& Tt) {
     using T = typename Store<ST>::T;
-    T r = 0, jx = 0, jy = 0, jz = 0, e2 = 0, gs = 0;
+    T r = M::DEV ? T(m.rho_ref) : T(0), jx = 0, jy = 0, jz = 0, e2 = 0, gs = 0;
 #pragma unroll
     for (int q = 0; q < M::Q; ++q) {
         const T v = c.f[q];
@@ -194,10 +195,10 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
         T r = 0;
 #pragma unroll
         for (int q = 0; q < M::Q; ++q) r += c.f[q];
-        rho = r;
+        rho = M::DEV ? r + T(a.m.rho_ref) : r;
     }
     if constexpr (!M::HAS_G) {
-        weak_feq<M::D, T>(rho, T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), c.f);
+        weak_feq_dev<M::D, T>(rho, T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), T(a.m.rho_ref), c.f);
     } else {
         int it = 0, conv = 1;
         M::template feq<ST>(a.m, rho, T(fd.u[0]), T(fd.u[1]), T(fd.T), c.lam, c.f, &it, &conv);
@@ -214,7 +215,7 @@ __device__ __forceinline__ int collide(const ModelDev& m, double tau, Cell<M, ST
     using T = typename Store<ST>::T;
     *conv = 1;
     if constexpr (!M::HAS_G) {
-        weak_collide<M::D, M::RR, T>(c.f, T(1.0 / tau));
+        weak_collide<M::D, M::RR, T>(c.f, T(1.0 / tau), T(m.rho_ref));
         return 0;
     } else {
         T rho, u[3], Tt;
@@ -349,7 +350,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
         out[4 * L.ncell + cell] = Tt;
     } else if (which == 1) {
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) out[(long long)q * L.ncell + cell] = c.f[q];
+        for (int q = 0; q < M::Q; ++q)
+            out[(long long)q * L.ncell + cell] = M::DEV ? (double)c.f[q] + (double)ref_f<M, ST>(a.m, q) : (double)c.f[q];
     } else if (which == 2) {
         if constexpr (M::HAS_G) {
 #pragma unroll
@@ -388,7 +390,7 @@ __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, d
         const double V = double(1ll << (lev * M::D));
 #pragma unroll
         for (int q = 0; q < M::Q; ++q) {
-            const double fq = (double)c.f[q];
+            const double fq = M::DEV ? (double)c.f[q] + M::w(q) * a.m.rho_ref : (double)c.f[q];
             v[0] += fq;
             v[1] += M::cx(q) * fq;
             v[2] += M::cy(q) * fq;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
     const T ux = T(u_in[cell]), uy = T(u_in[n + cell]), uz = T(M::D == 3 ? u_in[2 * n + cell] : 0.0);
     T feq[M::Q];
     if constexpr (!M::HAS_G) {
-        weak_feq<M::D, T>(rho, ux, uy, uz, feq);
+        weak_feq_dev<M::D, T>(rho, ux, uy, uz, T(a.m.rho_ref), feq);
 #pragma unroll
         for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, 1, cell, q, a.m, feq[q], T(0));
     } else {
@@ -526,9 +528,9 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
             vf = Ef[(long long)qs * L.ncell + src];
             if constexpr (M::HAS_G) vg = Eg[(long long)qs * L.ncell + src];
         } else {
-            // zero population (a deviation of -1 in the binary16 format)
-            vf = S(ST == ST_F16DEV ? -1.0f : 0.0f);
-            vg = vf;
+            // zero population: -1 in the binary16 format, -ref for the other deviation formats
+            vf = S(ST == ST_F16DEV ? -1.0f : (M::DEV ? -float(M::w(q) * a.m.rho_ref) : 0.0f));
+            vg = S(ST == ST_F16DEV ? -1.0f : 0.0f);
         }
         Of[(long long)q * L.ncell + cell] = vf;
         if constexpr (M::HAS_G) Og[(long long)q * L.ncell + cell] = vg;

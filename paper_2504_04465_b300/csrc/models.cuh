@@ -75,18 +75,21 @@ __device__ __forceinline__ void tp_reconstruct(const T* A, T* f) {
     }
 }
 
-// Weakly compressible collision in place.  RR = true: recursive regularization, else BGK.
+// Weakly compressible collision in place, on deviations d_i = f_i - w_i rho_ref.
+// RR = true: recursive regularization, else BGK.  rho = rho_ref + sum d, j = sum xi d,
+// sum xi_a xi_b f = rho_ref c_s^2 delta_ab + sum xi_a xi_b d; the reconstruction with
+// A_000 = rho - rho_ref returns the post-collision deviations.
 template <int D, bool RR, typename T>
-__device__ __forceinline__ void weak_collide(T* f, T omega) {
+__device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
     constexpr int Q = TP<D>::Q;
     constexpr int NZ = TP<D>::NZ;
     const T cs2 = T(1.0 / 3.0);
-    T rho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+    T drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int x = TP<D>::cx(q), y = TP<D>::cy(q), z = TP<D>::cz(q);
         const T v = f[q];
-        rho += v;
+        drho += v;
         if (x) { jx += x > 0 ? v : -v; mxx += v; }
         if (y) { jy += y > 0 ? v : -v; myy += v; }
         if (z) { jz += z > 0 ? v : -v; mzz += v; }
@@ -94,16 +97,17 @@ __device__ __forceinline__ void weak_collide(T* f, T omega) {
         if (x * z) mxz += x * z > 0 ? v : -v;
         if (y * z) myz += y * z > 0 ? v : -v;
     }
+    const T rho = rho_ref + drho;
     const T ir = T(1) / rho;
     const T ux = jx * ir, uy = jy * ir, uz = jz * ir;
     const T px[3] = {T(1), ux, ux * ux}, py[3] = {T(1), uy, uy * uy}, pz[3] = {T(1), uz, uz * uz};
     T Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
     if constexpr (RR) {
-        Pxx = mxx - rho * (ux * ux + cs2);
-        Pyy = myy - rho * (uy * uy + cs2);
+        Pxx = mxx - drho * cs2 - rho * ux * ux;
+        Pyy = myy - drho * cs2 - rho * uy * uy;
         Pxy = mxy - rho * ux * uy;
         if constexpr (D == 3) {
-            Pzz = mzz - rho * (uz * uz + cs2);
+            Pzz = mzz - drho * cs2 - rho * uz * uz;
             Pxz = mxz - rho * ux * uz;
             Pyz = myz - rho * uy * uz;
         }
@@ -116,7 +120,7 @@ __device__ __forceinline__ void weak_collide(T* f, T omega) {
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const T eq = rho * px[a] * py[b] * pz[c];
+                const T eq = (a + b + c == 0) ? drho : rho * px[a] * py[b] * pz[c];
                 T ne = 0;
                 if (RR && a + b + c >= 2) {
                     if (a == 2) ne += Pxx * py[b] * pz[c];
@@ -139,9 +143,10 @@ __device__ __forceinline__ void weak_collide(T* f, T omega) {
     }
 }
 
-// Weakly compressible equilibrium (boundary cells, initialisation)
+// Weakly compressible equilibrium as deviations f_eq,i - w_i rho_ref (boundary cells,
+// initialisation)
 template <int D, typename T>
-__device__ __forceinline__ void weak_feq(T rho, T ux, T uy, T uz, T* f) {
+__device__ __forceinline__ void weak_feq_dev(T rho, T ux, T uy, T uz, T rho_ref, T* f) {
     constexpr int NZ = TP<D>::NZ;
     const T px[3] = {T(1), ux, ux * ux}, py[3] = {T(1), uy, uy * uy}, pz[3] = {T(1), uz, uz * uz};
     T A[27];
@@ -151,7 +156,7 @@ __device__ __forceinline__ void weak_feq(T rho, T ux, T uy, T uz, T* f) {
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                A[a + 3 * b + 9 * c] = rho * px[a] * py[b] * pz[c] *
+                A[a + 3 * b + 9 * c] = ((a + b + c == 0) ? rho - rho_ref : rho * px[a] * py[b] * pz[c]) *
                                        T(inv_fact(a) * inv_fact(b) * inv_fact(c) * pow3(a + b + c));
     tp_reconstruct<D, T>(A, f);
 }

@@ -117,3 +117,60 @@ def sod_fields(centres: np.ndarray, nx: int, T0: float):
     rho = np.where(left, SOD_LEFT[0], SOD_RIGHT[0])
     p = np.where(left, SOD_LEFT[1], SOD_RIGHT[1])
     return rho, np.zeros((2, rho.size)), T0 * p / rho
+
+
+# ------------------------------------------------------------------ 3D flow past a sphere
+def sphere_spec(scale: int = 1) -> GridSpec:
+    """Four-level box around a sphere: 1024x512x512 finest units at scale 1, sphere diameter 64
+    centred at (256, 256, 256); uniform inflow at x-, Neumann on the other faces.
+
+    Level boxes (finest units, scale 1): L0 x[160,672) y,z[128,384); L1 x[96,864) y,z[64,448);
+    L2 x[32,992) y,z[32,480); L3 the rest.  scale = 2 halves every extent (the profiling case);
+    scale = 4 gives the reduced copy (256x128x128,
+    sphere diameter 16) whose boxes keep every ghost layer at least the lattice reach away from
+    the next one: L0 x[48,176) y,z[40,88); L1 x[32,224) y,z[32,96); L2 x[16,240) y,z[16,112).
+    """
+    if scale == 1:
+        ext = (1024, 512, 512)
+        boxes = [(2, (32, 32, 32), (992, 480, 480)), (1, (96, 64, 64), (864, 448, 448)),
+                 (0, (160, 128, 128), (672, 384, 384))]
+        centre, radius = (256.0, 256.0, 256.0), 32.0
+    elif scale == 2:
+        ext = (512, 256, 256)
+        boxes = [(2, (16, 16, 16), (496, 240, 240)), (1, (48, 32, 32), (432, 224, 224)),
+                 (0, (80, 64, 64), (336, 192, 192))]
+        centre, radius = (128.0, 128.0, 128.0), 16.0
+    elif scale == 4:
+        ext = (256, 128, 128)
+        boxes = [(2, (16, 16, 16), (240, 112, 112)), (1, (32, 32, 32), (224, 96, 96)),
+                 (0, (48, 40, 40), (176, 88, 88))]
+        centre, radius = (64.0, 64.0, 64.0), 8.0
+    else:
+        raise ValueError("scale must be 1, 2 or 4")
+    u_in = SPHERE_MACH / np.sqrt(3.0)
+    faces = {"x-": ("dirichlet_rho", 1.0, (u_in, 0.0, 0.0)), "x+": ("neumann",),
+             "y-": ("neumann",), "y+": ("neumann",), "z-": ("neumann",), "z+": ("neumann",)}
+    return GridSpec(3, ext, 4, boxes, (False, False, False), faces,
+                    [{"kind": "sphere", "center": centre, "radius": radius}])
+
+
+SPHERE_MACH = 0.1
+SPHERE_RE = 3900.0
+SPHERE_SEED = 3900
+
+
+def sphere_nu0(scale: int = 1) -> float:
+    """Level-0 viscosity u D / Re with D the sphere diameter in finest cells."""
+    return SPHERE_MACH / np.sqrt(3.0) * (64.0 / scale) / SPHERE_RE
+
+
+def sphere_fields(level, coords: np.ndarray):
+    """rho = 1, u = u_inf (1, 0, 0) + 1e-3 u_inf U(-1, 1)^3 per cell (splitmix64, seed 3900)."""
+    coords = np.asarray(coords)
+    n = coords.shape[0]
+    u_in = SPHERE_MACH / np.sqrt(3.0)
+    u = np.zeros((3, n))
+    u[0] = u_in
+    for k in range(3):
+        u[k] += 1e-3 * u_in * uniform_at(SPHERE_SEED, level, coords, k)
+    return np.ones(n), u
