@@ -106,10 +106,18 @@ def dist_setup():
     return world, rank, local
 
 
-def make_context(spec, storage, device, stream, graph, scale=1):
+# block shape and step-kernel variant picked by paper_2504_04465_b300.autotune on a B300 for this
+# workload (overridable with --block / --variant, or re-tuned with --autotune)
+DEFAULT_BLOCK = {"f32": (8, 4, 4), "f16dev": (8, 4, 4), "f64": (8, 4, 4)}
+DEFAULT_VARIANT = {"f32": 0, "f16dev": 0, "f64": 0}
+
+
+def make_context(spec, storage, device, stream, graph, scale=1, block=None, variant=0):
     from paper_2504_04465_b300 import lbmtree as lt
     ctx = lt.Context(3, device=device, stream=stream)
-    ctx.configure(spec, "D3Q27", "rr", storage, nu0=I.sphere_nu0(scale))
+    ctx.configure(spec, "D3Q27", "rr", storage, block=block, nu0=I.sphere_nu0(scale))
+    if variant:
+        ctx.set_variant(variant)
     if graph:
         ctx.use_graph(True)
     return ctx
@@ -179,7 +187,17 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
     spec = I.sphere_spec(args.scale)
     graph = not args.no_graph
-    ctx = make_context(spec, args.storage, local, stream.cuda_stream, graph, args.scale)
+    block = tuple(args.block) if args.block else DEFAULT_BLOCK[args.storage]
+    variant = args.variant if args.variant is not None else DEFAULT_VARIANT[args.storage]
+    tuned = None
+    if args.autotune:
+        from paper_2504_04465_b300 import autotune as AT
+        log = (lambda s: print(s, file=sys.stderr, flush=True)) if rank == 0 else None
+        block, variant, table = AT.tune(
+            lambda shp, strm: make_context(spec, args.storage, local, strm, False, args.scale, shp),
+            lambda c: c.init_fields(*host_fields(c)), AT.CANDIDATES_3D, device=local, log=log)
+        tuned = {f"{k[0]}:{k[1]}": round(v, 4) for k, v in table.items()}
+    ctx = make_context(spec, args.storage, local, stream.cuda_stream, graph, args.scale, block, variant)
     rho, u = host_fields(ctx)
     ctx.init_fields(rho, u)
     st = ctx.stats()
@@ -262,6 +280,8 @@ def run_ours(args, world, rank, local):
                        "storage": args.storage, "cells": int(sum(st.n_cells[:4])),
                        "n_eq": st.n_eq, "cell_updates_per_step": int(updates_per_step),
                        "step": "one coarse step = 8 fine iterations", "cuda_graph": graph,
+                       "block": list(block), "variant_min_blocks": ctx.variants()[variant],
+                       "autotune_ms_per_step": tuned,
                        "l2": "inputs larger than L2 (9.7 GB of populations at f32)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -282,6 +302,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--block", type=int, nargs=3, default=None)
+    ap.add_argument("--variant", type=int, default=None)
+    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--scale", type=int, default=1, choices=[1, 2, 4],
                     help="1: the full workload; 2, 4: copies with extents divided by 2, 4 (profiling, tests)")
     args = ap.parse_args()

@@ -144,6 +144,13 @@ int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);
  * Each extent must be even and at least the lattice reach.  Must precede lbm_build_grid(). */
 int lbm_set_block(lbm_ctx* ctx, int bx, int by, int bz);
 
+/* Compiled variants of the step kernels (occupancy targets of the kernel that runs the interior
+ * blocks): *n variants, minb[k] = resident 128-thread blocks per SM variant k is compiled for
+ * (0 = the model's default; minb may be NULL, else holds 4 ints).  The variants compute the same
+ * result; lbm_set_variant() picks one (an autotuner times them).  Both need a built grid. */
+int lbm_variants(lbm_ctx* ctx, int* n, int* minb);
+int lbm_set_variant(lbm_ctx* ctx, int variant);
+
 /* ---------------------------------------------------------------- grid (Secs. 3.2, 4.3-4.4) */
 /* Build the levels, neighbour tables, ghost layers and boundary layers, and allocate the
  * device arrays.  extent: finest-level extent per axis (divisible by 2^(n_levels-1)).

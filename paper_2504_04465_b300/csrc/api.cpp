@@ -43,6 +43,8 @@ struct DevLevel {
     void* f[2] = {nullptr, nullptr};
     void* g[2] = {nullptr, nullptr};
     double* lam = nullptr;
+    int* blist[2] = {nullptr, nullptr};
+    int64_t nlist[2] = {0, 0};
 };
 
 struct Constants {
@@ -159,6 +161,10 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
         d.f[0] = c->dl[i].f[0]; d.f[1] = c->dl[i].f[1];
         d.g[0] = c->dl[i].g[0]; d.g[1] = c->dl[i].g[1];
         d.lam = c->dl[i].lam;
+        for (int k = 0; k < 2; ++k) {
+            d.blist[k] = c->dl[i].blist[k];
+            d.nlist[k] = c->dl[i].nlist[k];
+        }
         const double nu = c->params.nu0 / double(int64_t(1) << i);
         d.tau = nu / theta + 0.5;
     }
@@ -198,6 +204,14 @@ int64_t iteration_args(const lbm_ctx* c, int64_t t, StepArgs& a) {
     }
     a.block_off[n] = off;
     a.n_active = n;
+    for (int k = 0; k < 2; ++k) {
+        int64_t o = 0;
+        for (int j = 0; j < n; ++j) {
+            a.list_off[k][j] = o;
+            o += c->dl[a.active[j]].nlist[k];
+        }
+        a.list_off[k][n] = o;
+    }
     for (int i = 0; i < L; ++i) {
         a.rd[i] = int((t >> i) & 1);
         a.sync_fg[i] = (i + 1 < L) && (t % (int64_t(2) << i) == 0);
@@ -236,8 +250,9 @@ int launch_iterations(lbm_ctx* c, int64_t n) {
         StepArgs a;
         const int64_t nb = iteration_args(c, c->t, a);
         if (nb) {
-            c->ks.step(a, nb, c->stream);
-            c->launches++;
+            const int64_t nf = a.list_off[0][a.n_active], ng = a.list_off[1][a.n_active];
+            c->ks.step(a, nf, ng, c->stream);
+            c->launches += (nf > 0) + (ng > 0);
         }
         c->t++;
     }
@@ -253,7 +268,7 @@ int build_graph(lbm_ctx* c) {
     for (int64_t k = 0; k < span; ++k) {
         StepArgs a;
         const int64_t nb = iteration_args(c, k, a);
-        if (nb) c->ks.step(a, nb, c->stream);
+        if (nb) c->ks.step(a, a.list_off[0][a.n_active], a.list_off[1][a.n_active], c->stream);
     }
     if (cudaGetLastError() != cudaSuccess) {       // end the capture so the stream stays usable
         cudaGraph_t g2 = nullptr;
@@ -274,9 +289,10 @@ int build_graph(lbm_ctx* c) {
 
 int launches_per_span(const lbm_ctx* c) {
     int n = 0;
-    for (int64_t k = 0; k < 2 * c->period(); ++k)
-        for (int i = c->L() - 1; i >= 0; --i)
-            if (k % (int64_t(1) << i) == 0 && c->grid.levels[i].nb) { ++n; break; }
+    for (int64_t k = 0; k < 2 * c->period(); ++k) {
+        StepArgs a;
+        if (iteration_args(c, k, a)) n += (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
+    }
     return n;
 }
 
@@ -494,6 +510,18 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         CU(cudaMemcpy(d.type, lv.type.data(), lv.type.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.bflag, lv.bflag.data(), lv.bflag.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.rec_id, lv.rec_id.data(), lv.rec_id.size() * 4, cudaMemcpyHostToDevice));
+        std::vector<int32_t> lists[2];
+        for (int64_t b = 0; b < lv.nb; ++b) lists[lv.bflag[b] ? 0 : 1].push_back((int32_t)b);
+        for (int k = 0; k < 2; ++k) {
+            d.nlist[k] = (int64_t)lists[k].size();
+            d.blist[k] = (int*)c->dalloc(lists[k].size() * 4);
+            if (!d.blist[k]) {
+                c->release();
+                c->built = false;
+                return fail(LBM_ERR_OOM, "device allocation of the block lists");
+            }
+            if (!lists[k].empty()) CU(cudaMemcpy(d.blist[k], lists[k].data(), lists[k].size() * 4, cudaMemcpyHostToDevice));
+        }
         if (!lv.recs.empty())
             CU(cudaMemcpy(d.recs, lv.recs.data(), lv.recs.size() * sizeof(CellRecDev), cudaMemcpyHostToDevice));
     }
@@ -586,6 +614,24 @@ int lbm_step_fine(lbm_ctx* c, int64_t n) {
     if (int r = ready(c)) return r;
     if (n < 0) return fail(LBM_ERR_ARG, "negative step count");
     return launch_iterations(c, n);
+}
+
+int lbm_variants(lbm_ctx* c, int* n, int* minb) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (n) *n = c->ks.n_variants;
+    if (minb)
+        for (int k = 0; k < c->ks.n_variants; ++k) minb[k] = c->ks.variant_minb[k];
+    return LBM_OK;
+}
+
+int lbm_set_variant(lbm_ctx* c, int v) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
+    if (v < 0 || v >= c->ks.n_variants) return fail(LBM_ERR_ARG, "variant out of range");
+    c->ks.step = c->ks.variant[v];
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
 }
 
 int lbm_use_graph(lbm_ctx* c, int on) {

@@ -1,8 +1,9 @@
 // Device-side storage formats and the block-table gather of the CUDA path.
 //
 // Layout (Sec. 4.4 of arXiv 2504.04465, adapted to blocks): every level stores its cells in
-// fixed-size blocks (BX x BY x BZ, x fastest), blocks in Morton order; populations are SoA,
-// f[q * ncell + cell] with cell = block * BS + local.  Two buffers per level (A/B, the
+// fixed-size blocks (BX x BY x BZ, x fastest), blocks in Morton order; populations are SoA inside
+// a block, f[(block * Q + q) * BS + local] (cell = block * BS + local), so one block's Q arrays
+// are contiguous and population q of a gathered cell is an immediate offset q * BS.  Two buffers per level (A/B, the
 // "two-population" storage of Sec. 4.1).  The stored state of a cell is its post-collision
 // populations; a step gathers f_i(x) = f*_i(x - xi_i) from the other buffer (pull form of
 // Eqs. CollisionStep/StreamingStep), collides and writes its own slot.  The weakly compressible
@@ -47,6 +48,13 @@ template <> struct Store<ST_F16DEV> {
         ((__half*)p)[i] = __float2half_rn(DEV ? v / ref : v / ref - 1.0f);
     }
 };
+
+// storage index of population q of cell (= block * BS + local)
+template <int BS, int Q>
+__device__ __forceinline__ long long pidx(long long cell, int q) {
+    const long long b = cell / BS;
+    return (b * Q + q) * BS + (cell - b * BS);
+}
 
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);

@@ -25,6 +25,8 @@ struct LevelDev {
     void* g[2];
     double* lam;             // 2 buffers x 8 x ncell (numerical equilibrium)
     double tau;
+    const int* blist[2];     // [0] simple blocks (every cell fluid, every source live), [1] the others
+    long long nlist[2];
 };
 
 struct FaceDev {
@@ -50,7 +52,8 @@ struct StepArgs {
     int n_levels;
     int n_active;
     int active[MAX_LEVELS];           // active levels, coarsest first
-    long long block_off[MAX_LEVELS + 1];
+    long long block_off[MAX_LEVELS + 1];      // over all blocks of the active levels
+    long long list_off[2][MAX_LEVELS + 1];    // over the simple / other block lists
     int rd[MAX_LEVELS];               // buffer index read by each level this iteration
     int sync_fg[MAX_LEVELS];          // 1: the level's fine ghosts receive an explosion now
     ModelDev m;

@@ -42,6 +42,9 @@ __device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, do
 
 struct D2Q21M {
     static constexpr int D = 2, Q = 21;
+    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
+    static constexpr int MINB_FAST = 2, MINB_GEN = 2;
+    static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<21>::cx(q); }

@@ -13,6 +13,9 @@ static __constant__ double ccs2_37;
 
 struct D2Q37M {
     static constexpr int D = 2, Q = 37;
+    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
+    static constexpr int MINB_FAST = 2, MINB_GEN = 2;
+    static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = false, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }

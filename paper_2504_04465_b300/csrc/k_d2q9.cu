@@ -6,6 +6,9 @@ namespace lbm {
 
 template <bool RR_> struct D2Q9M {
     static constexpr int D = 2, Q = 9;
+    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
+    static constexpr int MINB_FAST = 12, MINB_GEN = 6;
+    static constexpr bool TUNE = true;      // compile occupancy variants for the autotuner
     static constexpr bool DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
     __host__ __device__ static constexpr int cx(int q) { return TP<2>::cx(q); }

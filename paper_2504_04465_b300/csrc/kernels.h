@@ -7,12 +7,16 @@
 namespace lbm {
 
 struct KernelSet {
-    void (*step)(const StepArgs&, long long nblocks, cudaStream_t) = nullptr;
+    void (*step)(const StepArgs&, long long n_fast, long long n_gen, cudaStream_t) = nullptr;
     void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
     void (*ledger)(const StepArgs&, long long nblocks, double* partial, double* out, cudaStream_t) = nullptr;
     void (*init)(const StepArgs&, int lev, const double* rho, const double* u, const double* T, cudaStream_t) = nullptr;
     const void* step_kernel = nullptr;
     int block_threads = 0;
+    // compiled variants of the step launch (occupancy targets of the simple-block kernel)
+    void (*variant[4])(const StepArgs&, long long, long long, cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
+    int variant_minb[4] = {0, 0, 0, 0};
+    int n_variants = 1;
 };
 
 // Kernels for (model, storage, block shape) of each lattice; false if that combination is not built.

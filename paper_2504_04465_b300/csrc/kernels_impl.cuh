@@ -43,7 +43,7 @@ __device__ __forceinline__ typename Store<ST>::T ref_g(const ModelDev& m, int q)
     return typename Store<ST>::T(M::w(q) * m.rho_ref * (2.0 * m.Cv - M::D) * m.T0);
 }
 
-template <class M, int ST>
+template <class M, int ST, int BS>
 __device__ __forceinline__ void load_pop(const LevelDev& L, int buf, long long src, int q, const ModelDev& m,
                                          typename Store<ST>::T& fo, typename Store<ST>::T& go) {
     using T = typename Store<ST>::T;
@@ -52,16 +52,18 @@ __device__ __forceinline__ void load_pop(const LevelDev& L, int buf, long long s
         go = T(0);
         return;
     }
-    fo = Store<ST>::template load<M::DEV>(L.f[buf], (long long)q * L.ncell + src, ref_f<M, ST>(m, q));
-    if constexpr (M::HAS_G) go = Store<ST>::template load<false>(L.g[buf], (long long)q * L.ncell + src, ref_g<M, ST>(m, q));
+    const long long i = pidx<BS, M::Q>(src, q);
+    fo = Store<ST>::template load<M::DEV>(L.f[buf], i, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) go = Store<ST>::template load<false>(L.g[buf], i, ref_g<M, ST>(m, q));
     else go = T(0);
 }
 
-template <class M, int ST>
+template <class M, int ST, int BS>
 __device__ __forceinline__ void store_pop(const LevelDev& L, int buf, long long cell, int q, const ModelDev& m,
                                           typename Store<ST>::T fv, typename Store<ST>::T gv) {
-    Store<ST>::template store<M::DEV>(L.f[buf], (long long)q * L.ncell + cell, fv, ref_f<M, ST>(m, q));
-    if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[buf], (long long)q * L.ncell + cell, gv, ref_g<M, ST>(m, q));
+    const long long i = pidx<BS, M::Q>(cell, q);
+    Store<ST>::template store<M::DEV>(L.f[buf], i, fv, ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[buf], i, gv, ref_g<M, ST>(m, q));
 }
 
 // macroscopic moments (rho, u, T) of f, g (T from Eq. polyTemp)
@@ -128,7 +130,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
         for (int q = 0; q < M::Q; ++q) {
             T gv = T(0);
             if (bmask & (1ull << q)) {
-                load_pop<M, ST>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
+                load_pop<M, ST, BX * BY * BZ>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
             } else if (coal && (umask & (1ull << q))) {
                 const LevelDev& F = a.lv[lev - 1];
                 const int rdf = a.rd[lev - 1];
@@ -139,7 +141,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
                     const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
                     const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, M::cx(q), M::cy(q), M::cz(q));
                     T vf, vg;
-                    load_pop<M, ST>(F, rdf, s, q, a.m, vf, vg);
+                    load_pop<M, ST, BX * BY * BZ>(F, rdf, s, q, a.m, vf, vg);
                     sf += vf;
                     sg += vg;
                 }
@@ -147,7 +149,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
                 gv = sg / T(NK);
             } else {
                 const long long s = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(q), M::cy(q), M::cz(q));
-                load_pop<M, ST>(L, rd, s, q, a.m, c.f[q], gv);
+                load_pop<M, ST, BX * BY * BZ>(L, rd, s, q, a.m, c.f[q], gv);
             }
             if constexpr (M::HAS_G) c.g[q] = gv;
         }
@@ -180,7 +182,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
     for (int q = 0; q < M::Q; ++q) {
         const long long s = src_cell_g<BX, BY, BZ>(L.nbr, P, M::cx(q), M::cy(q), M::cz(q));
         T gv;
-        load_pop<M, ST>(L, rd, s, q, a.m, c.f[q], gv);
+        load_pop<M, ST, BX * BY * BZ>(L, rd, s, q, a.m, c.f[q], gv);
         if constexpr (M::HAS_G) c.g[q] = gv;
     }
     if constexpr (M::HAS_LAM) {
@@ -251,30 +253,65 @@ __device__ __forceinline__ int find_level(const StepArgs& a, long long bid, long
     return a.active[k];
 }
 
-// ------------------------------------------------------------------ step kernel
-template <class M, int ST, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX * BY * BZ) k_step(const StepArgs a) {
+// ------------------------------------------------------------------ step kernels
+// FAST = true runs the simple blocks (branch-free gather, no records), FAST = false the others
+// (coarse and fine ghosts, boundary layers, cells next to solids).  Both read buffer rd and write
+// rd ^ 1 of disjoint cells, so the two launches of an iteration are independent.
+__device__ __forceinline__ int find_level_list(const StepArgs& a, int list, long long bid, long long* i) {
+    int k = 0;
+    while (k + 1 < a.n_active && bid >= a.list_off[list][k + 1]) ++k;
+    *i = bid - a.list_off[list][k];
+    return a.active[k];
+}
+
+// MINB > 0 overrides the model's occupancy target (resident 128-thread blocks per SM)
+template <class M, int ST, int BX, int BY, int BZ, bool FAST, int MINB>
+__global__ void __launch_bounds__(BX * BY * BZ,
+                                  (MINB > 0 ? MINB : ((FAST ? M::MINB_FAST : M::MINB_GEN) / (ST == ST_F64 ? 2 : 1))) * 128 /
+                                      (BX * BY * BZ))
+k_step(const StepArgs a) {
     using T = typename Store<ST>::T;
     constexpr int BS = BX * BY * BZ;
     __shared__ int nbr_s[27];
     __shared__ unsigned long long s_nstat[19];
-    long long b;
-    const int lev = find_level(a, blockIdx.x, &b);
+    long long i;
+    const int lev = find_level_list(a, FAST ? 0 : 1, blockIdx.x, &i);
     const LevelDev& L = a.lv[lev];
+    const long long b = L.blist[FAST ? 0 : 1][i];
     const int l = threadIdx.x;
     if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
     if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
     __syncthreads();
     const long long cell = b * BS + l;
     const int rd = a.rd[lev], wr = rd ^ 1;
-    const bool simple = L.bflag[b] != 0;
-    const int type = simple ? (int)C_FLUID : (int)L.type[cell];
+    const int type = FAST ? (int)C_FLUID : (int)L.type[cell];
     const bool work = !(type == C_ABSENT || type == C_SOLID || (type == C_FGHOST && a.sync_fg[lev]));
     int iters = -1;
     if (work) {
         Cell<M, ST> c;
         int conv = 1, conv2 = 1;
-        assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+        if constexpr (FAST) {
+            const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) {
+                int sx = lx - M::cx(q), sy = ly - M::cy(q), sz = lz - M::cz(q);
+                const int ox = sx < 0 ? -1 : (sx >= BX ? 1 : 0);
+                const int oy = sy < 0 ? -1 : (sy >= BY ? 1 : 0);
+                const int oz = sz < 0 ? -1 : (sz >= BZ ? 1 : 0);
+                sx -= ox * BX; sy -= oy * BY; sz -= oz * BZ;
+                const int kk = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+                const int nb = (kk == 13) ? (int)b : nbr_s[kk];
+                const long long i = (long long)nb * (M::Q * BS) + q * BS + (sz * BY + sy) * BX + sx;
+                c.f[q] = Store<ST>::template load<M::DEV>(L.f[rd], i, ref_f<M, ST>(a.m, q));
+                if constexpr (M::HAS_G) c.g[q] = Store<ST>::template load<false>(L.g[rd], i, ref_g<M, ST>(a.m, q));
+            }
+            if constexpr (M::HAS_LAM) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + cell];
+            }
+        } else {
+            assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv);
+        }
         if (type != C_FGHOST) {
             const int it = collide<M, ST>(a.m, L.tau, c, &conv2);
             if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
@@ -282,26 +319,28 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_step(const StepArgs a) {
         }
         // fine ghosts stream purely: stored as gathered (post-collision = pre-collision)
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, wr, cell, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, wr, cell, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
         if constexpr (M::HAS_LAM) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) L.lam[((long long)wr * 8 + i) * L.ncell + cell] = c.lam[i];
+            for (int j = 0; j < 8; ++j) L.lam[((long long)wr * 8 + j) * L.ncell + cell] = c.lam[j];
         }
-        if (type == C_CGHOST) {
-            // uniform explosion (Eq. explosion_uniform) into every child's slot of the buffer the
-            // finer level writes at this iteration
-            const LevelDev& F = a.lv[lev - 1];
-            const int wrf = a.rd[lev - 1] ^ 1;
-            const long long child = L.recs[L.rec_id[cell]].a;
-            constexpr int NK = (M::D == 3) ? 8 : 4;
+        if constexpr (!FAST) {
+            if (type == C_CGHOST) {
+                // uniform explosion (Eq. explosion_uniform) into every child's slot of the buffer
+                // the finer level writes at this iteration
+                const LevelDev& F = a.lv[lev - 1];
+                const int wrf = a.rd[lev - 1] ^ 1;
+                const long long child = L.recs[L.rec_id[cell]].a;
+                constexpr int NK = (M::D == 3) ? 8 : 4;
 #pragma unroll
-            for (int kk = 0; kk < NK; ++kk) {
-                const long long ch = child + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
+                for (int kk = 0; kk < NK; ++kk) {
+                    const long long ch = child + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
 #pragma unroll
-                for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(F, wrf, ch, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
-                if constexpr (M::HAS_LAM) {
+                    for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(F, wrf, ch, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+                    if constexpr (M::HAS_LAM) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) F.lam[((long long)wrf * 8 + i) * F.ncell + ch] = c.lam[i];
+                        for (int j = 0; j < 8; ++j) F.lam[((long long)wrf * 8 + j) * F.ncell + ch] = c.lam[j];
+                    }
                 }
             }
         }
@@ -459,7 +498,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
     if constexpr (!M::HAS_G) {
         weak_feq_dev<M::D, T>(rho, ux, uy, uz, T(a.m.rho_ref), feq);
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, 1, cell, q, a.m, feq[q], T(0));
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, feq[q], T(0));
     } else {
         const T Tt = T(T_in[cell]);
         double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -471,7 +510,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
         if (!conv) set_status(a.status, -6);
         const T gfac = T((2.0 * a.m.Cv - M::D) * (double)Tt);
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST>(L, 1, cell, q, a.m, feq[q], gfac * feq[q]);
+        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, feq[q], gfac * feq[q]);
         if constexpr (M::HAS_LAM) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -525,23 +564,25 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
         }
         S vf, vg;
         if (src >= 0) {
-            vf = Ef[(long long)qs * L.ncell + src];
-            if constexpr (M::HAS_G) vg = Eg[(long long)qs * L.ncell + src];
+            vf = Ef[pidx<BS, M::Q>(src, qs)];
+            if constexpr (M::HAS_G) vg = Eg[pidx<BS, M::Q>(src, qs)];
         } else {
             // zero population: -1 in the binary16 format, -ref for the other deviation formats
             vf = S(ST == ST_F16DEV ? -1.0f : (M::DEV ? -float(M::w(q) * a.m.rho_ref) : 0.0f));
             vg = S(ST == ST_F16DEV ? -1.0f : 0.0f);
         }
-        Of[(long long)q * L.ncell + cell] = vf;
-        if constexpr (M::HAS_G) Og[(long long)q * L.ncell + cell] = vg;
+        Of[pidx<BS, M::Q>(cell, q)] = vf;
+        if constexpr (M::HAS_G) Og[pidx<BS, M::Q>(cell, q)] = vg;
     }
 }
 
 // ------------------------------------------------------------------ host launchers
 template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
-    static void step(const StepArgs& a, long long nblocks, cudaStream_t s) {
-        k_step<M, ST, BX, BY, BZ><<<(unsigned)nblocks, BX * BY * BZ, 0, s>>>(a);
+    template <int MINB>
+    static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s) {
+        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(a);
+        if (n_gen) k_step<M, ST, BX, BY, BZ, false, 0><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(a);
     }
     static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
         if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);
@@ -560,11 +601,24 @@ struct Launch {
 template <class M, int ST, int BX, int BY, int BZ>
 KernelSet make_set() {
     KernelSet k;
-    k.step = &Launch<M, ST, BX, BY, BZ>::step;
+    using LS = Launch<M, ST, BX, BY, BZ>;
+    k.step = &LS::template step<0>;
+    k.variant[0] = &LS::template step<0>;
+    k.variant_minb[0] = 0;
+    k.n_variants = 1;
+    if constexpr (M::TUNE && ST != ST_F64) {       // occupancy targets tried by the autotuner
+        k.variant[1] = &LS::template step<4>;
+        k.variant[2] = &LS::template step<6>;
+        k.variant[3] = &LS::template step<8>;
+        k.variant_minb[1] = 4;
+        k.variant_minb[2] = 6;
+        k.variant_minb[3] = 8;
+        k.n_variants = 4;
+    }
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
     k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;
     k.init = &Launch<M, ST, BX, BY, BZ>::init;
-    k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ>;
+    k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ, true, 0>;
     k.block_threads = BX * BY * BZ;
     return k;
 }

@@ -41,7 +41,18 @@ template <int D> __host__ __device__ constexpr double tp_w(int q) {
     return w1d(TP<D>::cx(q)) * w1d(TP<D>::cy(q)) * (D == 3 ? w1d(TP<D>::cz(q)) : 1.0);
 }
 
-// f_i = w_i sum_abc h_a h_b h_c A[a + 3b + 9c]   (separable)
+// f_i = w_i sum_abc h_a h_b h_c A[a + 3b + 9c], evaluated separably.  Per axis,
+//     18 w(xi) (A_0 + xi A_1 + (xi^2 - 1/3) A_2) = 4 (3 A_0 - A_2) at xi = 0,
+//                                                 3 A_0 +- 3 A_1 + 2 A_2 at xi = +-1,
+// so every coefficient is an exact integer and the only inexact constant is the final IEEE
+// division by 18^D.  Rounded constants such as fl(1/6) would scale the reconstructed mass and
+// momentum by the same factor at every step (a bias that grows linearly in FP32); the division
+// only adds unbiased rounding.
+template <typename T>
+__device__ __forceinline__ T r1(int x, T a0, T a1, T a2) {
+    return x == 0 ? T(4) * (T(3) * a0 - a2) : (T(3) * a0 + T(x) * T(3) * a1 + T(2) * a2);
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void tp_reconstruct(const T* A, T* f) {
     constexpr int NZ = TP<D>::NZ;
@@ -51,27 +62,22 @@ __device__ __forceinline__ void tp_reconstruct(const T* A, T* f) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < NZ; ++c)
-                X[x][b][c] = A[3 * b + 9 * c] + T(h1d(1, x - 1)) * A[1 + 3 * b + 9 * c] +
-                             T(h1d(2, x - 1)) * A[2 + 3 * b + 9 * c];
+            for (int c = 0; c < NZ; ++c) X[x][b][c] = r1<T>(x - 1, A[3 * b + 9 * c], A[1 + 3 * b + 9 * c], A[2 + 3 * b + 9 * c]);
     T Y[3][3][NZ];
 #pragma unroll
     for (int x = 0; x < 3; ++x)
 #pragma unroll
         for (int y = 0; y < 3; ++y)
 #pragma unroll
-            for (int c = 0; c < NZ; ++c)
-                Y[x][y][c] = X[x][0][c] + T(h1d(1, y - 1)) * X[x][1][c] + T(h1d(2, y - 1)) * X[x][2][c];
+            for (int c = 0; c < NZ; ++c) Y[x][y][c] = r1<T>(y - 1, X[x][0][c], X[x][1][c], X[x][2][c]);
+    const T den = T(D == 2 ? 324.0 : 5832.0);
 #pragma unroll
     for (int q = 0; q < TP<D>::Q; ++q) {
-        const int x = TP<D>::cx(q) + 1, y = TP<D>::cy(q) + 1, z = TP<D>::cz(q) + 1;
+        const int x = TP<D>::cx(q) + 1, y = TP<D>::cy(q) + 1, z = TP<D>::cz(q);
         T s;
-        if constexpr (D == 2) {
-            s = Y[x][y][0];
-        } else {
-            s = Y[x][y][0] + T(h1d(1, z - 1)) * Y[x][y][NZ > 1 ? 1 : 0] + T(h1d(2, z - 1)) * Y[x][y][NZ > 2 ? 2 : 0];
-        }
-        f[q] = T(tp_w<D>(q)) * s;
+        if constexpr (D == 2) s = Y[x][y][0];
+        else s = r1<T>(z, Y[x][y][0], Y[x][y][NZ > 1 ? 1 : 0], Y[x][y][NZ > 2 ? 2 : 0]);
+        f[q] = s / den;
     }
 }
 
@@ -83,7 +89,6 @@ template <int D, bool RR, typename T>
 __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
     constexpr int Q = TP<D>::Q;
     constexpr int NZ = TP<D>::NZ;
-    const T cs2 = T(1.0 / 3.0);
     T drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -103,11 +108,11 @@ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
     const T px[3] = {T(1), ux, ux * ux}, py[3] = {T(1), uy, uy * uy}, pz[3] = {T(1), uz, uz * uz};
     T Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
     if constexpr (RR) {
-        Pxx = mxx - drho * cs2 - rho * ux * ux;
-        Pyy = myy - drho * cs2 - rho * uy * uy;
+        Pxx = mxx - drho / T(3) - rho * ux * ux;
+        Pyy = myy - drho / T(3) - rho * uy * uy;
         Pxy = mxy - rho * ux * uy;
         if constexpr (D == 3) {
-            Pzz = mzz - drho * cs2 - rho * uz * uz;
+            Pzz = mzz - drho / T(3) - rho * uz * uz;
             Pxz = mxz - rho * ux * uz;
             Pyz = myz - rho * uy * uz;
         }

@@ -77,6 +77,8 @@ _sig = {
     "lbm_read_populations": [_P, C.c_int, _D],
     "lbm_conserved": [_P, _D],
     "lbm_stats": [_P, C.POINTER(Stats)],
+    "lbm_variants": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "lbm_set_variant": [_P, C.c_int],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -222,6 +224,16 @@ class Context:
 
     def step_fine(self, n_fine: int) -> None:
         _check(_lib.lbm_step_fine(self._h, n_fine), "lbm_step_fine")
+
+    def variants(self) -> list[int]:
+        """Occupancy targets of the compiled step-kernel variants (0 = model default)."""
+        n = C.c_int()
+        mb = (C.c_int * 4)()
+        _check(_lib.lbm_variants(self._h, C.byref(n), mb), "lbm_variants")
+        return list(mb[: n.value])
+
+    def set_variant(self, v: int) -> None:
+        _check(_lib.lbm_set_variant(self._h, v), "lbm_set_variant")
 
     def use_graph(self, on: bool = True) -> None:
         _check(_lib.lbm_use_graph(self._h, int(on)), "lbm_use_graph")
