@@ -44,10 +44,11 @@ template <int D> __host__ __device__ constexpr double tp_w(int q) {
 // f_i = w_i sum_abc h_a h_b h_c A[a + 3b + 9c], evaluated separably.  Per axis,
 //     18 w(xi) (A_0 + xi A_1 + (xi^2 - 1/3) A_2) = 4 (3 A_0 - A_2) at xi = 0,
 //                                                 3 A_0 +- 3 A_1 + 2 A_2 at xi = +-1,
-// so every coefficient is an exact integer and the only inexact constant is the final IEEE
-// division by 18^D.  Rounded constants such as fl(1/6) would scale the reconstructed mass and
-// momentum by the same factor at every step (a bias that grows linearly in FP32); the division
-// only adds unbiased rounding.
+// so every coefficient is an exact integer and the only inexact constant is the final division
+// by 18^D.  Rounded constants such as fl(1/6) would scale the reconstructed mass and momentum by
+// the same factor at every step (a bias that grows linearly in FP32).  The division is a
+// multiplication by fl(1/18^D) followed by one residual correction q += (x - q d) r computed with
+// FMAs, which leaves an error of order (rounding of 1/d)^2 instead of a systematic one.
 template <typename T>
 __device__ __forceinline__ T r1(int x, T a0, T a1, T a2) {
     return x == 0 ? T(4) * (T(3) * a0 - a2) : (T(3) * a0 + T(x) * T(3) * a1 + T(2) * a2);
@@ -71,13 +72,15 @@ __device__ __forceinline__ void tp_reconstruct(const T* A, T* f) {
 #pragma unroll
             for (int c = 0; c < NZ; ++c) Y[x][y][c] = r1<T>(y - 1, X[x][0][c], X[x][1][c], X[x][2][c]);
     const T den = T(D == 2 ? 324.0 : 5832.0);
+    const T rden = T(1) / den;                        // folded at compile time
 #pragma unroll
     for (int q = 0; q < TP<D>::Q; ++q) {
         const int x = TP<D>::cx(q) + 1, y = TP<D>::cy(q) + 1, z = TP<D>::cz(q);
         T s;
         if constexpr (D == 2) s = Y[x][y][0];
         else s = r1<T>(z, Y[x][y][0], Y[x][y][NZ > 1 ? 1 : 0], Y[x][y][NZ > 2 ? 2 : 0]);
-        f[q] = s / den;
+        const T qt = s * rden;
+        f[q] = fma(fma(-qt, den, s), rden, qt);
     }
 }
 
