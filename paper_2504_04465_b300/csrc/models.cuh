@@ -4,8 +4,7 @@
 // {1, xi, xi^2 - c_s^2} (Tab. lattices_hermite for D2Q9; every axis at most twice for D3Q27).
 // Contracting Eq. GenEq over all index tuples gives, per component (a, b, c) in {0, 1, 2}^3,
 //     f_i = w_i sum_{abc} h_a(xi_x) h_b(xi_y) h_c(xi_z) A_abc,   A_abc = a_abc / (a! b! c! c_s^2n)
-// so the reconstruction is three separable 3-point transforms (x, then y, then z) instead of a
-// Q x Q contraction.  Equilibrium moments: a_eq = rho u_x^a u_y^b u_z^c (Eq. RecursivityEquilibrium);
+// so the reconstruction factorises per axis (below) instead of a Q x Q contraction.  Equilibrium moments: a_eq = rho u_x^a u_y^b u_z^c (Eq. RecursivityEquilibrium);
 // RR non-equilibrium moments by the pair sum of the recursion of Eq. a1Rec,
 //     a_neq = [a=2] Pi_xx u^(a-2,b,c) + ... + a b Pi_xy u^(a-1,b-1,c) + ...,
 // with Pi_ab = sum_i xi_a xi_b f_i - rho u_a u_b - c_s^2 rho delta_ab (Appendix A, after Eq. a1Rec).
@@ -17,11 +16,6 @@
 namespace lbm {
 
 __host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
-__host__ __device__ constexpr double h1d(int a, int c) {
-    return a == 0 ? 1.0 : (a == 1 ? double(c) : double(c * c) - 1.0 / 3.0);
-}
-__host__ __device__ constexpr double inv_fact(int a) { return a == 2 ? 0.5 : 1.0; }
-__host__ __device__ constexpr double pow3(int n) { return n == 0 ? 1.0 : 3.0 * pow3(n - 1); }
 
 template <int D> struct TP;     // tensor-product lattices, same order as Lat<9> / Lat<27>
 template <> struct TP<2> {
@@ -41,132 +35,174 @@ template <int D> __host__ __device__ constexpr double tp_w(int q) {
     return w1d(TP<D>::cx(q)) * w1d(TP<D>::cy(q)) * (D == 3 ? w1d(TP<D>::cz(q)) : 1.0);
 }
 
-// f_i = w_i sum_abc h_a h_b h_c A[a + 3b + 9c], evaluated separably.  Per axis,
-//     18 w(xi) (A_0 + xi A_1 + (xi^2 - 1/3) A_2) = 4 (3 A_0 - A_2) at xi = 0,
-//                                                 3 A_0 +- 3 A_1 + 2 A_2 at xi = +-1,
-// so every coefficient is an exact integer and the only inexact constant is the final division
-// by 18^D.  Rounded constants such as fl(1/6) would scale the reconstructed mass and momentum by
-// the same factor at every step (a bias that grows linearly in FP32).  The division is a
-// multiplication by fl(1/18^D) followed by one residual correction q += (x - q d) r computed with
-// FMAs, which leaves an error of order (rounding of 1/d)^2 instead of a systematic one.
+// ------------------------------------------------------------------ factorised form
+// The D1Q3 tensor-product structure makes every term of Eq. GenRegCollision separable:
+//   18^D f*_i = rho E_x E_y E_z + (1 - 1/tau) [Pi_xx X2_x E_y E_z + Pi_yy E_x X2_y E_z
+//              + Pi_zz E_x E_y X2_z + Pi_xy X1_x X1_y E_z + Pi_xz X1_x E_y X1_z + Pi_yz E_x X1_y X1_z]
+// with, per axis and velocity component c in {-1, 0, 1} (18 w(c) times the 1D Hermite sums):
+//   E(c)  = 12 - 18 u^2 (c = 0),   3 + 9 c u + 9 u^2 (c = +-1)      equilibrium factor
+//   X1(c) = -36 u       (c = 0),   9 c + 18 u       (c = +-1)        sum_a a h_a u^(a-1) 3^a/a!
+//   X2(c) = -18         (c = 0),   9                (c = +-1)        h_2 3^2/2!
+// (the a_eq = rho u u u and pair-sum a_neq of models.cuh's tensor-product basis, regrouped per
+// axis).  Deviations from w rho_ref use E = W + e with W(c) = 18 w(c) = {12, 3, 3} and
+// e = E - W, so E_x E_y E_z - W_x W_y W_z = (e_x E_y + W_x e_y) E_z + W_x W_y e_z stays small.
 template <typename T>
-__device__ __forceinline__ T r1(int x, T a0, T a1, T a2) {
-    return x == 0 ? T(4) * (T(3) * a0 - a2) : (T(3) * a0 + T(x) * T(3) * a1 + T(2) * a2);
+struct Axis {
+    T E[3], e[3], X1[3];
+    __host__ __device__ __forceinline__ explicit Axis(T u) {
+        const T u2 = u * u;
+        e[1] = T(-18) * u2;
+        e[0] = T(9) * u2 - T(9) * u;
+        e[2] = T(9) * u2 + T(9) * u;
+        E[1] = T(12) + e[1];
+        E[0] = T(3) + e[0];
+        E[2] = T(3) + e[2];
+        X1[1] = T(-36) * u;
+        X1[0] = T(18) * u - T(9);
+        X1[2] = T(18) * u + T(9);
+    }
+};
+__host__ __device__ constexpr double Wc(int i) { return i == 1 ? 12.0 : 3.0; }     // i = c + 1
+__host__ __device__ constexpr double X2c(int i) { return i == 1 ? -18.0 : 9.0; }
+
+// x / (18^D), correctly rounded up to a residual of order fl(1/d) error squared
+template <typename T>
+__host__ __device__ __forceinline__ T div_den(T x, T den, T rden) {
+    const T qt = x * rden;
+    return fma(fma(-qt, den, x), rden, qt);
 }
 
+// moments of deviations d (sum d, sum xi d, sum xi xi d) by a separable transform
 template <int D, typename T>
-__device__ __forceinline__ void tp_reconstruct(const T* A, T* f) {
+__host__ __device__ __forceinline__ void tp_moments(const T* d, T& drho, T* j, T* m2 /* xx yy zz xy xz yz */) {
     constexpr int NZ = TP<D>::NZ;
-    T X[3][3][NZ];
+    T s0[3][NZ], s1[3][NZ], s2[3][NZ];     // per (y, z): x-sums of d, x d, x^2 d
 #pragma unroll
-    for (int x = 0; x < 3; ++x)
+    for (int z = 0; z < NZ; ++z)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
+        for (int y = 0; y < 3; ++y) {
+            const int b = 3 * y + 9 * z;
+            const T dm = d[b], d0 = d[b + 1], dp = d[b + 2];
+            s2[y][z] = dp + dm;
+            s1[y][z] = dp - dm;
+            s0[y][z] = s2[y][z] + d0;
+        }
+    T t00[NZ], t01[NZ], t02[NZ], t10[NZ], t11[NZ], t20[NZ];
 #pragma unroll
-            for (int c = 0; c < NZ; ++c) X[x][b][c] = r1<T>(x - 1, A[3 * b + 9 * c], A[1 + 3 * b + 9 * c], A[2 + 3 * b + 9 * c]);
-    T Y[3][3][NZ];
-#pragma unroll
-    for (int x = 0; x < 3; ++x)
-#pragma unroll
-        for (int y = 0; y < 3; ++y)
-#pragma unroll
-            for (int c = 0; c < NZ; ++c) Y[x][y][c] = r1<T>(y - 1, X[x][0][c], X[x][1][c], X[x][2][c]);
-    const T den = T(D == 2 ? 324.0 : 5832.0);
-    const T rden = T(1) / den;                        // folded at compile time
-#pragma unroll
-    for (int q = 0; q < TP<D>::Q; ++q) {
-        const int x = TP<D>::cx(q) + 1, y = TP<D>::cy(q) + 1, z = TP<D>::cz(q);
-        T s;
-        if constexpr (D == 2) s = Y[x][y][0];
-        else s = r1<T>(z, Y[x][y][0], Y[x][y][NZ > 1 ? 1 : 0], Y[x][y][NZ > 2 ? 2 : 0]);
-        const T qt = s * rden;
-        f[q] = fma(fma(-qt, den, s), rden, qt);
+    for (int z = 0; z < NZ; ++z) {
+        const T a = s0[2][z] + s0[0][z];
+        t02[z] = a;
+        t00[z] = a + s0[1][z];
+        t01[z] = s0[2][z] - s0[0][z];
+        t10[z] = s1[0][z] + s1[1][z] + s1[2][z];
+        t11[z] = s1[2][z] - s1[0][z];
+        t20[z] = s2[0][z] + s2[1][z] + s2[2][z];
+    }
+    if constexpr (D == 2) {
+        drho = t00[0]; j[0] = t10[0]; j[1] = t01[0]; j[2] = T(0);
+        m2[0] = t20[0]; m2[1] = t02[0]; m2[2] = T(0); m2[3] = t11[0]; m2[4] = T(0); m2[5] = T(0);
+    } else {
+        const T a = t00[2] + t00[0];
+        drho = a + t00[1];
+        j[2] = t00[2] - t00[0];
+        m2[2] = a;
+        j[1] = t01[0] + t01[1] + t01[2];
+        m2[5] = t01[2] - t01[0];
+        m2[1] = t02[0] + t02[1] + t02[2];
+        j[0] = t10[0] + t10[1] + t10[2];
+        m2[4] = t10[2] - t10[0];
+        m2[3] = t11[0] + t11[1] + t11[2];
+        m2[0] = t20[0] + t20[1] + t20[2];
     }
 }
 
 // Weakly compressible collision in place, on deviations d_i = f_i - w_i rho_ref.
-// RR = true: recursive regularization, else BGK.  rho = rho_ref + sum d, j = sum xi d,
-// sum xi_a xi_b f = rho_ref c_s^2 delta_ab + sum xi_a xi_b d; the reconstruction with
-// A_000 = rho - rho_ref returns the post-collision deviations.
+// RR = true: recursive regularization, else BGK (same equilibrium).
 template <int D, bool RR, typename T>
-__device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
-    constexpr int Q = TP<D>::Q;
+__host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
     constexpr int NZ = TP<D>::NZ;
-    T drho = 0, jx = 0, jy = 0, jz = 0, mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int x = TP<D>::cx(q), y = TP<D>::cy(q), z = TP<D>::cz(q);
-        const T v = f[q];
-        drho += v;
-        if (x) { jx += x > 0 ? v : -v; mxx += v; }
-        if (y) { jy += y > 0 ? v : -v; myy += v; }
-        if (z) { jz += z > 0 ? v : -v; mzz += v; }
-        if (x * y) mxy += x * y > 0 ? v : -v;
-        if (x * z) mxz += x * z > 0 ? v : -v;
-        if (y * z) myz += y * z > 0 ? v : -v;
-    }
+    T drho, j[3], m2[6];
+    tp_moments<D, T>(f, drho, j, m2);
     const T rho = rho_ref + drho;
     const T ir = T(1) / rho;
-    const T ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const T px[3] = {T(1), ux, ux * ux}, py[3] = {T(1), uy, uy * uy}, pz[3] = {T(1), uz, uz * uz};
-    T Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
+    const T ux = j[0] * ir, uy = j[1] * ir, uz = j[2] * ir;
+    const Axis<T> ax(ux), ay(uy), az(uz);
+    const T den = T(D == 2 ? 324.0 : 5832.0);
+    const T rden = T(1) / den;
+    T kxx = 0, kyy = 0, kzz = 0, kxy = 0, kxz = 0, kyz = 0;
     if constexpr (RR) {
-        Pxx = mxx - drho / T(3) - rho * ux * ux;
-        Pyy = myy - drho / T(3) - rho * uy * uy;
-        Pxy = mxy - rho * ux * uy;
+        // (1 - 1/tau) Pi_ab, Pi_ab = sum xi_a xi_b f - rho (u_a u_b + c_s^2 delta_ab)
+        const T keep = T(1) - omega;
+        kxx = keep * (m2[0] - drho / T(3) - rho * ux * ux);
+        kyy = keep * (m2[1] - drho / T(3) - rho * uy * uy);
+        kxy = keep * (m2[3] - rho * ux * uy);
         if constexpr (D == 3) {
-            Pzz = mzz - drho / T(3) - rho * uz * uz;
-            Pxz = mxz - rho * ux * uz;
-            Pyz = myz - rho * uy * uz;
+            kzz = keep * (m2[2] - drho / T(3) - rho * uz * uz);
+            kxz = keep * (m2[4] - rho * ux * uz);
+            kyz = keep * (m2[5] - rho * uy * uz);
         }
     }
-    const T keep = T(1) - omega;
-    T A[27];
 #pragma unroll
-    for (int c = 0; c < NZ; ++c)
+    for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const T eq = (a + b + c == 0) ? drho : rho * px[a] * py[b] * pz[c];
-                T ne = 0;
-                if (RR && a + b + c >= 2) {
-                    if (a == 2) ne += Pxx * py[b] * pz[c];
-                    if (b == 2) ne += Pyy * px[a] * pz[c];
-                    if (c == 2) ne += Pzz * px[a] * py[b];
-                    if (a && b) ne += T(a * b) * Pxy * px[a ? a - 1 : 0] * py[b ? b - 1 : 0] * pz[c];
-                    if (a && c) ne += T(a * c) * Pxz * px[a ? a - 1 : 0] * py[b] * pz[c ? c - 1 : 0];
-                    if (b && c) ne += T(b * c) * Pyz * px[a] * py[b ? b - 1 : 0] * pz[c ? c - 1 : 0];
+        for (int iy = 0; iy < 3; ++iy) {
+            const T Exy = ax.E[ix] * ay.E[iy];
+            const T dExy = ax.e[ix] * ay.E[iy] + T(Wc(ix)) * ay.e[iy];
+            const T A0 = drho * Exy + rho_ref * dExy;
+            T N0 = 0, N1 = 0, N2 = 0;
+            if constexpr (RR) {
+                N0 = kxx * T(X2c(ix)) * ay.E[iy] + kyy * ax.E[ix] * T(X2c(iy)) + kxy * ax.X1[ix] * ay.X1[iy];
+                if constexpr (D == 3) {
+                    N1 = kzz * Exy;
+                    N2 = kxz * ax.X1[ix] * ay.E[iy] + kyz * ax.E[ix] * ay.X1[iy];
                 }
-                const T scale = T(inv_fact(a) * inv_fact(b) * inv_fact(c) * pow3(a + b + c));
-                A[a + 3 * b + 9 * c] = (RR ? (eq + keep * ne) : eq) * scale;
             }
-    if constexpr (RR) {
-        tp_reconstruct<D, T>(A, f);
-    } else {
-        T feq[Q];
-        tp_reconstruct<D, T>(A, feq);
+            if constexpr (D == 2) {
+                const int q = ix + 3 * iy;
+                const T num = A0 + N0;
+                if constexpr (RR) f[q] = div_den<T>(num, den, rden);
+                else f[q] += omega * (div_den<T>(A0, den, rden) - f[q]);
+            } else {
+                const T B0 = rho_ref * T(Wc(ix) * Wc(iy));
 #pragma unroll
-        for (int q = 0; q < Q; ++q) f[q] += omega * (feq[q] - f[q]);
-    }
+                for (int iz = 0; iz < 3; ++iz) {
+                    const int q = ix + 3 * iy + 9 * iz;
+                    const T eq = A0 * az.E[iz] + B0 * az.e[iz];
+                    if constexpr (RR) {
+                        const T num = eq + N0 * az.E[iz] + N1 * T(X2c(iz)) + N2 * az.X1[iz];
+                        f[q] = div_den<T>(num, den, rden);
+                    } else {
+                        f[q] += omega * (div_den<T>(eq, den, rden) - f[q]);
+                    }
+                }
+            }
+        }
+    (void)NZ;
 }
 
 // Weakly compressible equilibrium as deviations f_eq,i - w_i rho_ref (boundary cells,
 // initialisation)
 template <int D, typename T>
-__device__ __forceinline__ void weak_feq_dev(T rho, T ux, T uy, T uz, T rho_ref, T* f) {
-    constexpr int NZ = TP<D>::NZ;
-    const T px[3] = {T(1), ux, ux * ux}, py[3] = {T(1), uy, uy * uy}, pz[3] = {T(1), uz, uz * uz};
-    T A[27];
+__host__ __device__ __forceinline__ void weak_feq_dev(T rho, T ux, T uy, T uz, T rho_ref, T* f) {
+    const Axis<T> ax(ux), ay(uy), az(uz);
+    const T den = T(D == 2 ? 324.0 : 5832.0);
+    const T rden = T(1) / den;
+    const T drho = rho - rho_ref;
 #pragma unroll
-    for (int c = 0; c < NZ; ++c)
+    for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
+        for (int iy = 0; iy < 3; ++iy) {
+            const T Exy = ax.E[ix] * ay.E[iy];
+            const T dExy = ax.e[ix] * ay.E[iy] + T(Wc(ix)) * ay.e[iy];
+            const T A0 = drho * Exy + rho_ref * dExy;
+            if constexpr (D == 2) {
+                f[ix + 3 * iy] = div_den<T>(A0, den, rden);
+            } else {
+                const T B0 = rho_ref * T(Wc(ix) * Wc(iy));
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                A[a + 3 * b + 9 * c] = ((a + b + c == 0) ? rho - rho_ref : rho * px[a] * py[b] * pz[c]) *
-                                       T(inv_fact(a) * inv_fact(b) * inv_fact(c) * pow3(a + b + c));
-    tp_reconstruct<D, T>(A, f);
+                for (int iz = 0; iz < 3; ++iz) f[ix + 3 * iy + 9 * iz] = div_den<T>(A0 * az.E[iz] + B0 * az.e[iz], den, rden);
+            }
+        }
 }
 
 }  // namespace lbm
