@@ -202,6 +202,18 @@ int lbm_read_populations(lbm_ctx* ctx, int which, double* out);
 int lbm_conserved(lbm_ctx* ctx, double out[5]);
 int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
 
+/* The same totals as lbm_conserved(), for callers that cannot allocate device memory when they
+ * need them (a host framework that owns all device memory through its own pool and forbids raw
+ * cudaMalloc, a loop that must not trigger the synchronisation an allocation can cause).  No
+ * counterpart in the paper.  The call allocates nothing: d_out is the caller's device buffer of
+ * 5 doubles {mass, momentum_x, momentum_y, momentum_z, energy}, written asynchronously on the
+ * context's stream (read it after lbm_sync()).  The per-block partial sums go to a fixed device
+ * array of the library holding at most 524288 blocks (20 MiB, kept by every GPU that loads the
+ * library until the process exits); larger grids are rejected with LBM_ERR_ARG.  The first call on
+ * a device looks up that array's address, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race.  LBM_ERR_STATE off a synchronisation instant. */
+int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
+
 #ifdef __cplusplus
 }
 #endif

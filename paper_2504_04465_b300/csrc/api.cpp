@@ -298,6 +298,23 @@ int launches_per_span(const lbm_ctx* c) {
 
 }  // namespace
 
+namespace lbm {
+// used by noalloc.cu: the arguments of the ledger launch at the current time, the context's
+// kernels, stream and device (made current)
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+int ledger_launch_args(lbm_ctx* c, StepArgs* a, long long* nblocks, KernelSet* ks, cudaStream_t* s, int* device) {
+    if (int r = ready(c)) return r;
+    if (c->t % c->period()) return fail(LBM_ERR_STATE, "not at a coarse synchronisation instant");
+    CU(cudaSetDevice(c->device));
+    *nblocks = current_args(c, *a);
+    *ks = c->ks;
+    *s = c->stream;
+    *device = c->device;
+    return LBM_OK;
+}
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }

@@ -79,6 +79,7 @@ _sig = {
     "lbm_stats": [_P, C.POINTER(Stats)],
     "lbm_variants": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lbm_set_variant": [_P, C.c_int],
+    "lbm_conserved_noalloc": [_P, C.c_void_p],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -262,6 +263,11 @@ class Context:
         out = np.empty(5)
         _check(_lib.lbm_conserved(self._h, _dptr(out)), "lbm_conserved")
         return out
+
+    def conserved_noalloc(self, d_out: int) -> None:
+        """Conserved totals into the caller's device buffer of 5 doubles (address d_out),
+        without any device allocation in the call; asynchronous on the context's stream."""
+        _check(_lib.lbm_conserved_noalloc(self._h, C.c_void_p(d_out)), "lbm_conserved_noalloc")
 
     def stats(self) -> Stats:
         s = Stats()
