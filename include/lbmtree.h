@@ -123,6 +123,7 @@ typedef struct {
     int64_t kernel_launches;     /* step-kernel launches issued since initialisation          */
     int64_t device_bytes;        /* device memory held by the context                         */
     int64_t cell_updates;        /* cell updates per coarse step (sum_i n_i 2^(L-1-i))          */
+    int64_t n_general_blocks[8]; /* blocks with ghost, boundary or solid-adjacent cells         */
 } lbm_stats_t;
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -144,9 +145,9 @@ int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);
  * Each extent must be even and at least the lattice reach.  Must precede lbm_build_grid(). */
 int lbm_set_block(lbm_ctx* ctx, int bx, int by, int bz);
 
-/* Compiled variants of the step kernels (occupancy targets of the kernel that runs the interior
- * blocks): *n variants, minb[k] = resident 128-thread blocks per SM variant k is compiled for
- * (0 = the model's default; minb may be NULL, else holds 4 ints).  The variants compute the same
+/* Compiled variants of the step kernels (occupancy targets): *n variants; minb[k] encodes the
+ * resident 128-thread blocks per SM variant k is compiled for as 10 * interior + general
+ * (0 = the model's defaults; minb may be NULL, else holds 4 ints).  The variants compute the same
  * result; lbm_set_variant() picks one (an autotuner times them).  Both need a built grid. */
 int lbm_variants(lbm_ctx* ctx, int* n, int* minb);
 int lbm_set_variant(lbm_ctx* ctx, int variant);

@@ -777,6 +777,7 @@ int lbm_stats(lbm_ctx* c, lbm_stats_t* s) {
     for (int i = 0; i < c->L() && i < 8; ++i) {
         const BuiltLevel& lv = c->grid.levels[i];
         s->n_blocks[i] = lv.nb;
+        for (int64_t b = 0; b < lv.nb; ++b) s->n_general_blocks[i] += lv.bflag[b] ? 0 : 1;
         s->n_cells[i] = lv.count[1] + lv.count[2] + lv.count[3] + lv.count[4] + lv.count[5];
         const int64_t live = lv.count[1] + lv.count[2] + lv.count[3] + lv.count[4];
         s->cell_updates += live << (c->L() - 1 - i);

@@ -290,7 +290,9 @@ k_step(const StepArgs a) {
     if (work) {
         Cell<M, ST> c;
         int conv = 1, conv2 = 1;
-        if constexpr (FAST) {
+        // fluid cells without a record (no bounce-back link) have every source live: gather
+        // them branch-free also inside the general blocks
+        if (FAST || (type == C_FLUID && L.rec_id[cell] < 0)) {
             const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
 #pragma unroll
             for (int q = 0; q < M::Q; ++q) {
@@ -309,7 +311,7 @@ k_step(const StepArgs a) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + cell];
             }
-        } else {
+        } else if constexpr (!FAST) {
             assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv);
         }
         if (type != C_FGHOST) {
@@ -579,10 +581,10 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
 // ------------------------------------------------------------------ host launchers
 template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
-    template <int MINB>
+    template <int MINB_F, int MINB_G>
     static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s) {
-        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(a);
-        if (n_gen) k_step<M, ST, BX, BY, BZ, false, 0><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(a);
+        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(a);
+        if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(a);
     }
     static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
         if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);
@@ -602,23 +604,24 @@ template <class M, int ST, int BX, int BY, int BZ>
 KernelSet make_set() {
     KernelSet k;
     using LS = Launch<M, ST, BX, BY, BZ>;
-    k.step = &LS::template step<0>;
-    k.variant[0] = &LS::template step<0>;
+    k.step = &LS::template step<0, 0>;
+    k.variant[0] = &LS::template step<0, 0>;
     k.variant_minb[0] = 0;
     k.n_variants = 1;
     if constexpr (M::TUNE && ST != ST_F64) {       // occupancy targets tried by the autotuner
-        k.variant[1] = &LS::template step<4>;
-        k.variant[2] = &LS::template step<6>;
-        k.variant[3] = &LS::template step<8>;
-        k.variant_minb[1] = 4;
-        k.variant_minb[2] = 6;
-        k.variant_minb[3] = 8;
+        // (interior kernel, general kernel) resident 128-thread blocks; encoded 10 * F + G
+        k.variant[1] = &LS::template step<8, 4>;
+        k.variant[2] = &LS::template step<8, 6>;
+        k.variant[3] = &LS::template step<6, 6>;
+        k.variant_minb[1] = 84;
+        k.variant_minb[2] = 86;
+        k.variant_minb[3] = 66;
         k.n_variants = 4;
     }
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
     k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;
     k.init = &Launch<M, ST, BX, BY, BZ>::init;
-    k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ, true, 0>;
+    k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ, true, 0>;   // for occupancy queries
     k.block_threads = BX * BY * BZ;
     return k;
 }

@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("n_levels", C.c_int), ("block", C.c_int * 3), ("newton_iter_sum", C.c_int64),
                 ("newton_updates", C.c_int64), ("newton_nonconverged", C.c_int64),
                 ("newton_hist", C.c_int64 * 16), ("fine_iterations", C.c_int64),
-                ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64), ("cell_updates", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64), ("cell_updates", C.c_int64),
+                ("n_general_blocks", C.c_int64 * 8)]
 
 
 _P = C.c_void_p
