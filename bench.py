@@ -109,7 +109,7 @@ def dist_setup():
 # block shape and step-kernel variant picked by paper_2504_04465_b300.autotune on a B300 for this
 # workload (overridable with --block / --variant, or re-tuned with --autotune)
 DEFAULT_BLOCK = {"f32": (8, 4, 4), "f16dev": (8, 4, 4), "f64": (8, 4, 4)}
-DEFAULT_VARIANT = {"f32": 1, "f16dev": 1, "f64": 0}
+DEFAULT_VARIANT = {"f32": 2, "f16dev": 2, "f64": 0}
 
 
 def make_context(spec, storage, device, stream, graph, scale=1, block=None, variant=0):
