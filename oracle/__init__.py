@@ -20,7 +20,8 @@ Modules
     grid       multi-level cell-centred grid with Rohde ghost layers (Sections 3.2, 4.3-4.4)
     solver     multi-level time stepping with coalescence/explosion (Section 4.5 and
                Eqs. coalescence/explosion_uniform), boundaries, DDF, shock sensor
-    mlp        small multilayer perceptron forward/backward used for the learned Newton guess
+    mlp        small multilayer perceptron forward/backward/Adam for the learned Newton guess
+               (an extension beyond the paper; see its header)
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than itself
 (printed values, closed forms, invariants, brute force); the one exception is listed in
