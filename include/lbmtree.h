@@ -75,10 +75,13 @@ extern "C" {
 
 /* Initial guess of the Newton solve.  WARM: the multipliers stored in the cell (carried through
  * coalescence/explosion, Sec. 3.2).  ZERO: lambda = 0.  POLY: weighted least-squares fit of
- * -1 - ln f_poly (f_poly the thermal Hermite equilibrium, positive populations only). */
+ * -1 - ln f_poly (f_poly the thermal Hermite equilibrium, positive populations only).
+ * MLP: a small network (below) trained on equilibria the solver produces; Newton still runs to
+ * the same tolerance, so the result does not depend on the guess beyond the tolerance. */
 #define LBM_GUESS_WARM  0
 #define LBM_GUESS_ZERO  1
 #define LBM_GUESS_POLY  2
+#define LBM_GUESS_MLP   3   /* the context's network (lbm_mlp_set) */
 
 /* Analytic solids (cells whose centre lies inside are solid, level 0 only). */
 #define LBM_SOLID_SPHERE 1   /* p = {cx, cy, cz, radius}                (finest units)      */
@@ -214,6 +217,48 @@ int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
  * a device looks up that array's address, so make it before any stream capture.  All calls share
  * the array: calls that overlap on the GPU race.  LBM_ERR_STATE off a synchronisation instant. */
 int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
+
+/* ---------------------------------------------------------------- learned Newton guess */
+/* A beyond-the-paper extension of the numerical equilibrium (Appendix A, Eq. exponential): a
+ * 3 -> 64 -> 64 -> 8 network with tanh hidden layers maps x = (u_x, u_y, T/T0 - 1) to
+ * y, and lambda0 = m + s * y is the Newton starting point.  Parameters: one FP32 vector of
+ * lbm_mlp_nparams() values [W1 (64x3), b1 (64), W2 (64x64), b2 (64), W3 (8x64), b3 (8)],
+ * row-major; weight matrices are used rounded to bfloat16 (nearest even), arithmetic FP32.
+ * The training calls work on caller-owned device buffers and the given stream. */
+int lbm_mlp_nparams(void);
+/* y[n*8] = network(x[n*3]) (x FP64, y FP32). */
+int lbm_mlp_forward(const float* d_params, const double* d_x, int64_t n, float* d_y, void* stream);
+/* d_grad[nparams] = gradient of L = 1/(2n) sum ||y - t||^2 over the batch, d_loss[0] = L
+ * (both overwritten; t[n*8] FP32 targets in normalised units). */
+int lbm_mlp_grad(const float* d_params, const double* d_x, const float* d_t, int64_t n, float* d_grad,
+                 float* d_loss, void* stream);
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8) of d_params with moments d_m, d_v;
+ * step counts from 1. */
+int lbm_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step, float lr, void* stream);
+/* Network used by the context when guess = LBM_GUESS_MLP (host parameters, copied; m, s host). */
+int lbm_mlp_set(lbm_ctx* ctx, const float* params, const double m[8], const double s[8]);
+/* The context's network: FP32 master parameters (trained, before rounding) and m, s (host
+ * buffers of lbm_mlp_nparams(), 8 and 8 values).  LBM_ERR_STATE if no network is set. */
+int lbm_mlp_get(lbm_ctx* ctx, float* params, double m[8], double s[8]);
+
+typedef struct {
+    int steps;              /* Adam steps */
+    int batch;              /* samples per step, drawn with replacement */
+    double lr, lr_final;    /* learning rate, decayed linearly from lr to lr_final */
+    uint64_t seed;          /* initial weights and minibatches (counter-based hash) */
+    float final_loss;       /* out: loss of the trained network over all n samples */
+} lbm_mlp_train_params;
+
+/* Train the context's network on n device samples: uT[n*3] = (u_x, u_y, T) and the converged
+ * multipliers lambda[n*8] (for instance from lbm_newton_batch).  m and s are the per-output
+ * mean and standard deviation of lambda; training minimises the loss of lbm_mlp_grad on
+ * (lambda - m)/s with the project's kernels; the context then uses the network for
+ * LBM_GUESS_MLP.  Allocates temporary device memory; synchronous with the context's stream. */
+int lbm_mlp_train(lbm_ctx* ctx, const double* d_uT, const double* d_lambda, int64_t n, lbm_mlp_train_params* p);
+/* Batched equilibrium solve of the context's model (D2Q21 numerical): samples uT[n*3] =
+ * (u_x, u_y, T) on the device, guess ZERO, POLY or MLP; writes lambda[n*8] and the Newton
+ * iterations per sample (-1 if not converged) on the context's stream. */
+int lbm_newton_batch(lbm_ctx* ctx, const double* d_uT, int64_t n, int guess, double* d_lambda, int* d_iters);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,7 @@
 #include "kernels.h"
 
 using namespace lbm;
+extern "C" int lbm_mlp_nparams(void);
 
 namespace {
 thread_local std::string g_err;
@@ -102,6 +103,9 @@ struct lbm_ctx {
     int64_t launches = 0;
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;
+    float* d_mlp = nullptr;         // Newton-guess network, weights bf16-rounded (own allocation, kept across grid rebuilds)
+    std::vector<float> mlp_master;  // its parameters before rounding
+    double mlp_m[8] = {0}, mlp_s[8] = {0};
     int64_t total_blocks = 0;
 
     void* dalloc(size_t bytes) {
@@ -178,6 +182,8 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     m.newton_tol = c->params.newton_tol > 0 ? c->params.newton_tol : 1e-12;
     m.newton_max_iter = c->params.newton_max_iter > 0 ? c->params.newton_max_iter : 50;
     m.guess = c->params.guess;
+    m.mlp = c->d_mlp;
+    for (int k = 0; k < 8; ++k) { m.mlp_m[k] = c->mlp_m[k]; m.mlp_s[k] = c->mlp_s[k]; }
     for (int f = 0; f < 6; ++f) {
         m.faces[f].kind = c->faces[f].kind;
         m.faces[f].rho = c->faces[f].rho;
@@ -242,7 +248,18 @@ int ready(lbm_ctx* c) {
     if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
     if (c->host_only) return fail(LBM_ERR_STATE, "host-only context (device < 0)");
     if (!c->initialized) return fail(LBM_ERR_STATE, "fields not initialised");
+    if (c->params.guess == LBM_GUESS_MLP && !c->d_mlp) return fail(LBM_ERR_STATE, "network guess selected but no network set");
     return LBM_OK;
+}
+
+// bfloat16 rounding (nearest even) of a float, as the device conversion does
+float bf16_round_host(float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
 }
 
 int launch_iterations(lbm_ctx* c, int64_t n) {
@@ -370,6 +387,7 @@ int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
     if (!c->host_only) cudaSetDevice(c->device);
     c->release();
+    if (c->d_mlp) cudaFree(c->d_mlp);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
@@ -392,7 +410,7 @@ int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
     if (p) {
         if (p->nu0 < 0) return fail(LBM_ERR_ARG, "negative viscosity");
         if (p->gamma <= 1.0 && model >= LBM_COMP_POLY) return fail(LBM_ERR_ARG, "gamma must exceed 1");
-        if (p->guess < 0 || p->guess > LBM_GUESS_POLY) return fail(LBM_ERR_ARG, "unknown Newton guess");
+        if (p->guess < 0 || p->guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "unknown Newton guess");
         c->params = *p;
         if (c->params.gamma <= 1.0) c->params.gamma = 1.4;
         if (c->params.rho_ref <= 0) c->params.rho_ref = 1.0;
@@ -648,6 +666,80 @@ int lbm_set_variant(lbm_ctx* c, int v) {
     if (v < 0 || v >= c->ks.n_variants) return fail(LBM_ERR_ARG, "variant out of range");
     c->ks.step = c->ks.variant[v];
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
+int lbm_mlp_set(lbm_ctx* c, const float* params, const double m[8], const double s[8]) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!params || !m || !s) return fail(LBM_ERR_ARG, "null argument");
+    if (c->host_only) return fail(LBM_ERR_STATE, "host-only context");
+    const int np = lbm_mlp_nparams();
+    std::vector<float> h(params, params + np);
+    // weight matrices rounded once (biases kept): [W1 192, b1 64, W2 4096, b2 64, W3 512, b3 8]
+    const int w_ranges[3][2] = {{0, 192}, {256, 4352}, {4416, 4928}};
+    for (auto& r : w_ranges)
+        for (int k = r[0]; k < r[1]; ++k) h[k] = bf16_round_host(h[k]);
+    CU(cudaSetDevice(c->device));
+    if (!c->d_mlp && cudaMalloc(&c->d_mlp, np * sizeof(float)) != cudaSuccess) {
+        c->d_mlp = nullptr;
+        return fail(LBM_ERR_OOM, "network parameters");
+    }
+    CU(cudaMemcpy(c->d_mlp, h.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+    c->mlp_master.assign(params, params + np);
+    for (int k = 0; k < 8; ++k) { c->mlp_m[k] = m[k]; c->mlp_s[k] = s[k]; }
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
+int lbm_mlp_get(lbm_ctx* c, float* params, double m[8], double s[8]) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!params || !m || !s) return fail(LBM_ERR_ARG, "null argument");
+    if (!c->d_mlp || c->mlp_master.empty()) return fail(LBM_ERR_STATE, "no network set");
+    std::memcpy(params, c->mlp_master.data(), c->mlp_master.size() * sizeof(float));
+    for (int k = 0; k < 8; ++k) { m[k] = c->mlp_m[k]; s[k] = c->mlp_s[k]; }
+    return LBM_OK;
+}
+
+int lbm_mlp_train(lbm_ctx* c, const double* d_uT, const double* d_lambda, int64_t n, lbm_mlp_train_params* p) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!d_uT || !d_lambda || !p || n <= 0) return fail(LBM_ERR_ARG, "bad arguments");
+    if (p->steps < 1 || p->batch < 1 || !(p->lr > 0) || p->lr_final < 0) return fail(LBM_ERR_ARG, "bad training parameters");
+    if (c->host_only) return fail(LBM_ERR_STATE, "host-only context");
+    if (c->model != LBM_COMP_NUMERICAL || c->lattice != LBM_D2Q21) return fail(LBM_ERR_UNSUPPORTED, "needs the D2Q21 numerical model");
+    CU(cudaSetDevice(c->device));
+    const int np = lbm_mlp_nparams();
+    if (!c->d_mlp && cudaMalloc(&c->d_mlp, np * sizeof(float)) != cudaSuccess) {
+        c->d_mlp = nullptr;
+        return fail(LBM_ERR_OOM, "network parameters");
+    }
+    float* master = nullptr;
+    CU(cudaMalloc(&master, np * sizeof(float)));
+    double ms[16];
+    const int r = mlp_train_device(d_uT, d_lambda, n, c->T0(), *p, master, c->d_mlp, ms, &p->final_loss, c->stream);
+    if (r == LBM_OK) {
+        c->mlp_master.resize(np);
+        cudaMemcpy(c->mlp_master.data(), master, np * sizeof(float), cudaMemcpyDeviceToHost);
+        for (int k = 0; k < 8; ++k) { c->mlp_m[k] = ms[k]; c->mlp_s[k] = ms[8 + k]; }
+        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    }
+    cudaFree(master);
+    return r;
+}
+
+int lbm_newton_batch(lbm_ctx* c, const double* d_uT, int64_t n, int guess, double* d_lambda, int* d_iters) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!d_uT || !d_lambda || !d_iters || n < 0) return fail(LBM_ERR_ARG, "bad arguments");
+    if (c->host_only || !c->built) return fail(LBM_ERR_STATE, "grid not built on a device");
+    if (c->model != LBM_COMP_NUMERICAL || c->lattice != LBM_D2Q21) return fail(LBM_ERR_UNSUPPORTED, "needs the D2Q21 numerical model");
+    if (guess < LBM_GUESS_ZERO || guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "guess must be ZERO, POLY or MLP");
+    if (guess == LBM_GUESS_MLP && !c->d_mlp) return fail(LBM_ERR_STATE, "no network set");
+    CU(cudaSetDevice(c->device));
+    StepArgs a;
+    fill_args(c, a);
+    ModelDev m = a.m;
+    m.guess = guess;
+    launch_newton_batch_d2q21(d_uT, n, m, d_lambda, d_iters, c->stream);
+    CU(cudaGetLastError());
     return LBM_OK;
 }
 

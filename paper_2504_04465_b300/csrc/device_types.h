@@ -45,6 +45,8 @@ struct ModelDev {
     int newton_max_iter;
     int guess;
     FaceDev faces[6];
+    const float* mlp;        // Newton-guess network (bf16-rounded weights), guess == 3
+    double mlp_m[8], mlp_s[8];
 };
 
 struct StepArgs {

@@ -5,6 +5,7 @@
 // 3rd-order thermal Hermite equilibrium about theta = 2/3 (positive populations only), onto the
 // eight basis functions by weighted least squares.
 #include "kernels_impl.cuh"
+#include "mlp.cuh"
 
 namespace lbm {
 
@@ -40,6 +41,14 @@ __device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, do
     chol8_solve(A, b, lam);
 }
 
+// network guess lambda0 = m + s * y(u_x, u_y, T/T0 - 1)
+__device__ __forceinline__ void mlp_guess21(const ModelDev& m, double ux, double uy, double Tt, double* lam) {
+    float h1[MLP_H], h2[MLP_H], y[MLP_OUT];
+    mlp_eval(m.mlp, (float)ux, (float)uy, (float)(Tt / m.T0 - 1.0), h1, h2, y);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) lam[a] = m.mlp_m[a] + m.mlp_s[a] * (double)y[a];
+}
+
 struct D2Q21M {
     static constexpr int D = 2, Q = 21;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
@@ -61,6 +70,8 @@ struct D2Q21M {
             for (int a = 0; a < 8; ++a) lam[a] = 0.0;
         } else if (m.guess == 2) {
             poly_guess21((double)ux, (double)uy, (double)Tt, lam);
+        } else if (m.guess == 3) {
+            mlp_guess21(m, (double)ux, (double)uy, (double)Tt, lam);
         }
         double e[21];
         *iters = newton_solve<21>((double)ux, (double)uy, (double)Tt, lam, e, m.newton_tol, m.newton_max_iter, conv);
@@ -69,6 +80,27 @@ struct D2Q21M {
     }
     __device__ static void init_guess(double ux, double uy, double Tt, double* lam) { poly_guess21(ux, uy, Tt, lam); }
 };
+
+// batched equilibrium solve: samples (u_x, u_y, T), guess 1 zero, 2 polynomial, 3 network
+__global__ void __launch_bounds__(128) k_newton_batch(const double* __restrict__ uT, long long n, ModelDev m,
+                                                      double* __restrict__ lam_out, int* __restrict__ iters) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double ux = uT[3 * i], uy = uT[3 * i + 1], Tt = uT[3 * i + 2];
+    double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (m.guess == 2) poly_guess21(ux, uy, Tt, lam);
+    else if (m.guess == 3) mlp_guess21(m, ux, uy, Tt, lam);
+    double e[21];
+    int conv = 0;
+    const int it = newton_solve<21>(ux, uy, Tt, lam, e, m.newton_tol, m.newton_max_iter, &conv);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) lam_out[8 * i + a] = lam[a];
+    iters[i] = conv ? it : -1;
+}
+
+void launch_newton_batch_d2q21(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s) {
+    if (n) k_newton_batch<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(uT, n, m, lam, iters);
+}
 
 bool find_kernels_d2q21(int model, int storage, const int* blk, KernelSet& out) {
     if (model == 4 && blk[0] == 16 && blk[1] == 16 && blk[2] == 1) return pick_storage<D2Q21M, 16, 16, 1>(storage, out);

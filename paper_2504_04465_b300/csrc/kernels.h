@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "device_types.h"
+#include "../../include/lbmtree.h"
 
 namespace lbm {
 
@@ -24,6 +25,10 @@ bool find_kernels_d2q9(int model, int storage, const int* block, KernelSet& out)
 bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d2q37(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d2q21(int model, int storage, const int* block, KernelSet& out);
+
+int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
+                     float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);
+void launch_newton_batch_d2q21(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s);
 
 // Constant tables of the D2Q37 and D2Q21 translation units (current device).
 cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37);

@@ -174,3 +174,45 @@ def sphere_fields(level, coords: np.ndarray):
     for k in range(3):
         u[k] += 1e-3 * u_in * uniform_at(SPHERE_SEED, level, coords, k)
     return np.ones(n), u
+
+
+# ------------------------------------------------------------------ 2D flow past a NACA0012 airfoil
+# Level boxes as multiples of the chord C around the leading edge (x) and the chord line (y),
+# finest level first; the domain is [-15C, 15C]^2 and the coarsest level fills the rest.
+NACA_BOXES = [((-0.1, 1.1), (-0.15, 0.15)), ((-0.5, 2.0), (-0.5, 0.5)), ((-2.0, 5.0), (-2.0, 2.0)),
+              ((-6.0, 12.0), (-6.0, 6.0))]
+NACA_SEED = 1504
+
+
+def naca_spec(chord: int, mach: float, T0: float, gamma: float = 1.4, n_levels: int = 5,
+              supersonic: bool = True) -> GridSpec:
+    """Multi-level box around a NACA0012 at zero incidence, chord ``chord`` finest cells.
+
+    The leading edge sits at the domain centre (15C, 15C).  Inflow at x-: every macroscopic
+    field imposed (supersonic inlet) or density extrapolated (subsonic); Neumann on the other
+    faces.  Box edges are rounded outwards to whole cells of the next coarser level."""
+    ext = 30 * chord
+    cx, cy = 15 * chord, 15 * chord
+    boxes = []
+    for lev, ((x0, x1), (y0, y1)) in enumerate(NACA_BOXES[:n_levels - 1]):
+        a = 2 ** (lev + 1)
+        lo = (int(np.floor((cx + x0 * chord) / a)) * a, int(np.floor((cy + y0 * chord) / a)) * a)
+        hi = (int(np.ceil((cx + x1 * chord) / a)) * a, int(np.ceil((cy + y1 * chord) / a)) * a)
+        boxes.append((lev, lo, hi))
+    u_in = mach * np.sqrt(gamma * T0)
+    inflow = ("dirichlet", 1.0, (u_in, 0.0, 0.0), T0) if supersonic else ("dirichlet_rho", 1.0, (u_in, 0.0, 0.0), T0)
+    faces = {"x-": inflow, "x+": ("neumann",), "y-": ("neumann",), "y+": ("neumann",)}
+    return GridSpec(2, (ext, ext), n_levels, boxes[::-1], (False, False), faces,
+                    [{"kind": "naca", "chord": float(chord), "x0": float(cx), "y0": float(cy), "thickness": 0.12}])
+
+
+def naca_fields(level, coords: np.ndarray, mach: float, T0: float, gamma: float = 1.4):
+    """Uniform free stream rho = 1, u = Ma sqrt(gamma T0) (1, 0) with a 1e-3 relative
+    perturbation per cell (splitmix64, seed 1504), T = T0."""
+    coords = np.asarray(coords)
+    n = coords.shape[0]
+    u_in = mach * np.sqrt(gamma * T0)
+    u = np.zeros((2, n))
+    u[0] = u_in * (1.0 + 1e-3 * uniform_at(NACA_SEED, level, coords, 0))
+    u[1] = 1e-3 * u_in * uniform_at(NACA_SEED, level, coords, 1)
+    return np.ones(n), u, np.full(n, T0)

@@ -27,7 +27,7 @@ LATTICE = {"D2Q9": 9, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
 MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4}
 STORAGE = {"f64": 1, "f32": 2, "f16dev": 3}
 FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}
-GUESS = {"warm": 0, "zero": 1, "poly": 2}
+GUESS = {"warm": 0, "zero": 1, "poly": 2, "mlp": 3}
 FACES = ["x-", "x+", "y-", "y+", "z-", "z+"]
 CELL_FLUID, CELL_CGHOST, CELL_FGHOST, CELL_BC, CELL_SOLID = 1, 2, 3, 4, 5
 
@@ -81,6 +81,14 @@ _sig = {
     "lbm_variants": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "lbm_set_variant": [_P, C.c_int],
     "lbm_conserved_noalloc": [_P, C.c_void_p],
+    "lbm_mlp_forward": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "lbm_mlp_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "lbm_mlp_adam": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p],
+    "lbm_mlp_set": [_P, C.POINTER(C.c_float), _D, _D],
+    "lbm_newton_batch": [_P, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p],
+    "lbm_mlp_nparams": [],
+    "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
+    "lbm_mlp_train": [_P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -90,6 +98,30 @@ _lib.lbm_last_error.argtypes = []
 _lib.lbm_last_error.restype = C.c_char_p
 
 EXPORTED = sorted(list(_sig) + ["lbm_last_error"])
+
+
+class MlpTrainParams(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
+                ("seed", C.c_uint64), ("final_loss", C.c_float)]
+
+
+def mlp_nparams() -> int:
+    return _lib.lbm_mlp_nparams()
+
+
+def mlp_forward(d_params: int, d_x: int, n: int, d_y: int, stream: int = 0) -> None:
+    _check(_lib.lbm_mlp_forward(C.c_void_p(d_params), C.c_void_p(d_x), n, C.c_void_p(d_y), C.c_void_p(stream)),
+           "lbm_mlp_forward")
+
+
+def mlp_grad(d_params: int, d_x: int, d_t: int, n: int, d_grad: int, d_loss: int, stream: int = 0) -> None:
+    _check(_lib.lbm_mlp_grad(C.c_void_p(d_params), C.c_void_p(d_x), C.c_void_p(d_t), n, C.c_void_p(d_grad),
+                             C.c_void_p(d_loss), C.c_void_p(stream)), "lbm_mlp_grad")
+
+
+def mlp_adam(d_params: int, d_grad: int, d_m: int, d_v: int, step: int, lr: float, stream: int = 0) -> None:
+    _check(_lib.lbm_mlp_adam(C.c_void_p(d_params), C.c_void_p(d_grad), C.c_void_p(d_m), C.c_void_p(d_v), step,
+                             C.c_float(lr), C.c_void_p(stream)), "lbm_mlp_adam")
 
 
 class LbmError(RuntimeError):
@@ -269,6 +301,30 @@ class Context:
         """Conserved totals into the caller's device buffer of 5 doubles (address d_out),
         without any device allocation in the call; asynchronous on the context's stream."""
         _check(_lib.lbm_conserved_noalloc(self._h, C.c_void_p(d_out)), "lbm_conserved_noalloc")
+
+    def mlp_set(self, params: np.ndarray, m: np.ndarray, s: np.ndarray) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        _check(_lib.lbm_mlp_set(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), _dptr(m), _dptr(s)), "lbm_mlp_set")
+
+    def mlp_get(self):
+        p = np.zeros(mlp_nparams(), np.float32)
+        m = np.zeros(8)
+        s = np.zeros(8)
+        _check(_lib.lbm_mlp_get(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), _dptr(m), _dptr(s)), "lbm_mlp_get")
+        return p, m, s
+
+    def mlp_train(self, d_uT: int, d_lambda: int, n: int, steps: int = 3000, batch: int = 1024, lr: float = 3e-3,
+                  lr_final: float = 3e-4, seed: int = 1504) -> float:
+        """Train the context's Newton-guess network; returns the final loss over the n samples."""
+        p = MlpTrainParams(steps, batch, lr, lr_final, seed, 0.0)
+        _check(_lib.lbm_mlp_train(self._h, C.c_void_p(d_uT), C.c_void_p(d_lambda), n, C.byref(p)), "lbm_mlp_train")
+        return float(p.final_loss)
+
+    def newton_batch(self, d_uT: int, n: int, guess: str, d_lambda: int, d_iters: int) -> None:
+        _check(_lib.lbm_newton_batch(self._h, C.c_void_p(d_uT), n, GUESS[guess], C.c_void_p(d_lambda),
+                                     C.c_void_p(d_iters)), "lbm_newton_batch")
 
     def stats(self) -> Stats:
         s = Stats()

@@ -26,7 +26,7 @@ def run_oracle(spec, latname, model, fields_fn, n_fine, **params):
     kw = {k: v for k, v in params.items() if k in ORACLE_PARAMS and v is not None}
     if "T0" in kw and not kw["T0"]:
         kw.pop("T0")
-    s = S.Solver(g, model, **kw)
+    s = S.Solver(g, model, mlp=params.get("mlp"), **kw)
     s.init_fields([fields_for(lat, fields_fn, lv.level, lv.coords) for lv in g.levels])
     s.step_fine(n_fine)
     return s
