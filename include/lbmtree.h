@@ -218,6 +218,30 @@ int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
  * the array: calls that overlap on the GPU race.  LBM_ERR_STATE off a synchronisation instant. */
 int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
 
+/* ---------------------------------------------------------------- batched cases */
+/* Several independent cases (contexts built and initialised on one device) advanced together:
+ * each fine iteration launches, per group of cases sharing lattice, model, storage, block
+ * shape and step variant, one kernel over the active simple/streaming blocks of all its cases
+ * and one over their general blocks, instead of two launches per case.  Cases keep their own
+ * state and schedule (a case with L levels advances level i at its own iterations
+ * t % 2^i == 0, Sec. 4.5); results are bitwise those of stepping each case alone.  Supported
+ * for D2Q9 and D2Q37 (LBM_ERR_UNSUPPORTED otherwise).  The batch reads each case's settings
+ * when it is created: a case reconfigured afterwards needs a new batch.  Stepping a case on
+ * its own in between is allowed (the batch rebuilds its tables).  Work goes on `stream` (NULL:
+ * a stream the batch owns); each case's stream waits for it after every lbm_batch_step. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream);
+int lbm_batch_destroy(lbm_batch* batch);
+/* Capture the cases' common schedule period (2^L fine iterations, L the largest level count)
+ * as one CUDA graph and replay it (1) or launch iteration by iteration (0, the default). */
+int lbm_batch_use_graph(lbm_batch* batch, int on);
+/* Advance every case by n_fine fine iterations of its own finest level (asynchronous). */
+int lbm_batch_step(lbm_batch* batch, int64_t n_fine);
+/* Wait for the batch and return the first device status of its cases. */
+int lbm_batch_sync(lbm_batch* batch);
+/* Number of groups, kernel launches issued so far, schedule period in fine iterations. */
+int lbm_batch_info(lbm_batch* batch, int* n_groups, int64_t* launches, int64_t* span);
+
 /* ---------------------------------------------------------------- learned Newton guess */
 /* A beyond-the-paper extension of the numerical equilibrium (Appendix A, Eq. exponential): a
  * 3 -> 64 -> 64 -> 8 network with tanh hidden layers maps x = (u_x, u_y, T/T0 - 1) to

@@ -84,6 +84,7 @@ struct lbm_ctx {
     BuiltGrid grid;
     bool built = false;
     KernelSet ks;
+    int variant = 0;                // compiled step variant in use (lbm_set_variant)
     // host views
     std::vector<int32_t> h_level, h_xyz;
     std::vector<uint8_t> h_type;
@@ -530,9 +531,10 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         d.bflag = (unsigned char*)c->dalloc(lv.bflag.size());
         d.rec_id = (int*)c->dalloc(lv.rec_id.size() * 4);
         d.recs = (CellRecDev*)c->dalloc(lv.recs.size() * sizeof(CellRecDev));
+        // one extra block of zero populations stands in for missing neighbour blocks
         for (int k = 0; k < 2; ++k) {
-            d.f[k] = c->dalloc(size_t(Q) * ncell * es);
-            if (has_g) d.g[k] = c->dalloc(size_t(Q) * ncell * es);
+            d.f[k] = c->dalloc(size_t(Q) * (ncell + BS) * es);
+            if (has_g) d.g[k] = c->dalloc(size_t(Q) * (ncell + BS) * es);
         }
         if (has_lam) d.lam = (double*)c->dalloc(size_t(2) * 8 * ncell * 8);
         if (!d.nbr || !d.type || !d.bflag || !d.rec_id || !d.recs || !d.f[0] || !d.f[1] ||
@@ -545,8 +547,13 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         CU(cudaMemcpy(d.type, lv.type.data(), lv.type.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.bflag, lv.bflag.data(), lv.bflag.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.rec_id, lv.rec_id.data(), lv.rec_id.size() * 4, cudaMemcpyHostToDevice));
+        // list 0 entries: 2 * block + 1 for streaming blocks (cell types read), 2 * block for
+        // simple blocks; list 1: the general blocks
         std::vector<int32_t> lists[2];
-        for (int64_t b = 0; b < lv.nb; ++b) lists[lv.bflag[b] ? 0 : 1].push_back((int32_t)b);
+        for (int64_t b = 0; b < lv.nb; ++b) {
+            if (lv.bflag[b]) lists[0].push_back((int32_t)(2 * b + (lv.bflag[b] == 2 ? 1 : 0)));
+            else lists[1].push_back((int32_t)b);
+        }
         for (int k = 0; k < 2; ++k) {
             d.nlist[k] = (int64_t)lists[k].size();
             d.blist[k] = (int*)c->dalloc(lists[k].size() * 4);
@@ -665,6 +672,7 @@ int lbm_set_variant(lbm_ctx* c, int v) {
     if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
     if (v < 0 || v >= c->ks.n_variants) return fail(LBM_ERR_ARG, "variant out of range");
     c->ks.step = c->ks.variant[v];
+    c->variant = v;
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return LBM_OK;
 }
@@ -887,6 +895,258 @@ int lbm_stats(lbm_ctx* c, lbm_stats_t* s) {
         s->newton_nonconverged = (int64_t)h[2];
         for (int k = 0; k < 16; ++k) s->newton_hist[k] = (int64_t)h[3 + k];
     }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched cases
+// Cases that share lattice, model, storage, block shape and step variant form a group; every
+// fine iteration launches each group's FAST and general kernels once over the active blocks of
+// all its cases.  The per-case iteration arguments of a span of 2^L fine iterations (L the
+// largest level count) sit in a device table; the span is captured as a CUDA graph.
+struct lbm_batch {
+    struct Group {
+        KernelSet ks;
+        int variant = 0;
+        std::vector<int> cases;                 // indices into lbm_batch::cases
+        StepArgs* d_args = nullptr;             // span x n
+        long long* d_off = nullptr;             // span x 2 x (n + 1)
+        std::vector<long long> nf, ng;          // per iteration of the span
+    };
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_ctx*> cases;
+    std::vector<int64_t> t0;                    // case times when the tables were built
+    std::vector<Group> groups;
+    int64_t span = 1, tb = 0;
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+
+    void free_tables() {
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        for (auto& g : groups) {
+            if (g.d_args) cudaFree(g.d_args);
+            if (g.d_off) cudaFree(g.d_off);
+            g.d_args = nullptr;
+            g.d_off = nullptr;
+        }
+    }
+};
+
+namespace {
+
+int batch_tables(lbm_batch* b) {
+    b->free_tables();
+    b->span = 1;
+    for (lbm_ctx* c : b->cases) b->span = std::max(b->span, 2 * c->period());
+    b->t0.resize(b->cases.size());
+    for (size_t k = 0; k < b->cases.size(); ++k) b->t0[k] = b->cases[k]->t;
+    b->tb = 0;
+    for (auto& g : b->groups) {
+        const int n = (int)g.cases.size();
+        std::vector<StepArgs> args(size_t(b->span) * n);
+        std::vector<long long> off(size_t(b->span) * 2 * (n + 1));
+        g.nf.assign(b->span, 0);
+        g.ng.assign(b->span, 0);
+        for (int64_t j = 0; j < b->span; ++j) {
+            long long* of = &off[size_t(j) * 2 * (n + 1)];
+            long long* og = of + (n + 1);
+            of[0] = og[0] = 0;
+            for (int k = 0; k < n; ++k) {
+                lbm_ctx* c = b->cases[g.cases[k]];
+                StepArgs& a = args[size_t(j) * n + k];
+                iteration_args(c, c->t + j, a);
+                of[k + 1] = of[k] + a.list_off[0][a.n_active];
+                og[k + 1] = og[k] + a.list_off[1][a.n_active];
+            }
+            g.nf[j] = of[n];
+            g.ng[j] = og[n];
+        }
+        CU(cudaMalloc(&g.d_args, args.size() * sizeof(StepArgs)));
+        CU(cudaMalloc(&g.d_off, off.size() * sizeof(long long)));
+        CU(cudaMemcpy(g.d_args, args.data(), args.size() * sizeof(StepArgs), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(g.d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    return LBM_OK;
+}
+
+// one fine iteration of every case (table row j)
+void batch_iteration(lbm_batch* b, int64_t j) {
+    for (auto& g : b->groups) {
+        const int n = (int)g.cases.size();
+        const long long* of = g.d_off + size_t(j) * 2 * (n + 1);
+        g.ks.batch[g.variant](g.d_args + size_t(j) * n, of, of + (n + 1), n, g.nf[j], g.ng[j], b->stream);
+        b->launches += (g.nf[j] > 0) + (g.ng[j] > 0);
+    }
+}
+
+int batch_graph(lbm_batch* b) {
+    if (b->gexec) return LBM_OK;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved = b->launches;
+    for (int64_t j = 0; j < b->span; ++j) batch_iteration(b, j);
+    b->launches = saved;
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaGraph_t g2 = nullptr;
+        cudaStreamEndCapture(b->stream, &g2);
+        if (g2) cudaGraphDestroy(g2);
+        return fail(LBM_ERR_CUDA, "launch during graph capture failed");
+    }
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream) {
+    if (!out) return fail(LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!cases || n <= 0) return fail(LBM_ERR_ARG, "no cases");
+    for (int k = 0; k < n; ++k) {
+        if (check_ctx(cases[k])) return LBM_ERR_ARG;
+        if (int r = ready(cases[k])) return r;
+        if (cases[k]->device != cases[0]->device) return fail(LBM_ERR_ARG, "cases on different devices");
+        for (int j = 0; j < k; ++j)
+            if (cases[j] == cases[k]) return fail(LBM_ERR_ARG, "a case is listed twice");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return fail(LBM_ERR_OOM, "batch allocation");
+    b->device = cases[0]->device;
+    b->cases.assign(cases, cases + n);
+    for (int k = 0; k < n; ++k) {
+        lbm_ctx* c = cases[k];
+        if (!c->ks.batch[c->variant]) {
+            delete b;
+            return fail(LBM_ERR_UNSUPPORTED, "no batched kernels for this lattice (D2Q9 and D2Q37 have them)");
+        }
+        bool placed = false;
+        for (auto& g : b->groups) {
+            lbm_ctx* h = b->cases[g.cases[0]];
+            if (h->lattice == c->lattice && h->model == c->model && h->storage == c->storage &&
+                h->block[0] == c->block[0] && h->block[1] == c->block[1] && h->block[2] == c->block[2] &&
+                h->variant == c->variant) {
+                g.cases.push_back(k);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) {
+            lbm_batch::Group g;
+            g.ks = c->ks;
+            g.variant = c->variant;
+            g.cases.push_back(k);
+            b->groups.push_back(std::move(g));
+        }
+    }
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) {
+        b->stream = (cudaStream_t)stream;
+        if (!b->stream) {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(LBM_ERR_CUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+    }
+    // the cases' own streams may hold queued work
+    for (lbm_ctx* c : b->cases) cudaStreamSynchronize(c->stream);
+    if (int r = batch_tables(b)) {
+        b->free_tables();
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return r;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    b->free_tables();
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+int lbm_batch_use_graph(lbm_batch* b, int on) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    b->use_graph = on != 0;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t n_fine) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    if (n_fine < 0) return fail(LBM_ERR_ARG, "negative step count");
+    CU(cudaSetDevice(b->device));
+    // a case stepped on its own since the tables were built: rebuild them at its new time
+    bool moved = false;
+    for (size_t k = 0; k < b->cases.size(); ++k) {
+        lbm_ctx* c = b->cases[k];
+        if (int r = ready(c)) return r;
+        if (c->t != b->t0[k] + b->tb) moved = true;
+    }
+    if (moved) {
+        for (lbm_ctx* c : b->cases) cudaStreamSynchronize(c->stream);
+        if (int r = batch_tables(b)) return r;
+    }
+    int64_t n = n_fine;
+    while (n > 0) {
+        const int64_t j = b->tb % b->span;
+        if (b->use_graph && j == 0 && n >= b->span) {
+            if (int r = batch_graph(b)) return r;
+            CU(cudaGraphLaunch(b->gexec, b->stream));
+            for (auto& g : b->groups)
+                for (int64_t i = 0; i < b->span; ++i) b->launches += (g.nf[i] > 0) + (g.ng[i] > 0);
+            b->tb += b->span;
+            n -= b->span;
+            for (lbm_ctx* c : b->cases) c->t += b->span;
+            continue;
+        }
+        batch_iteration(b, j);
+        b->tb++;
+        n--;
+        for (lbm_ctx* c : b->cases) c->t++;
+    }
+    CU(cudaGetLastError());
+    // later work on a case's own stream runs after the batch
+    cudaEvent_t ev;
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(ev, b->stream));
+    for (lbm_ctx* c : b->cases) cudaStreamWaitEvent(c->stream, ev, 0);
+    cudaEventDestroy(ev);
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    CU(cudaSetDevice(b->device));
+    CU(cudaStreamSynchronize(b->stream));
+    for (lbm_ctx* c : b->cases)
+        if (int r = lbm_sync(c)) return r;
+    return LBM_OK;
+}
+
+int lbm_batch_info(lbm_batch* b, int* n_groups, int64_t* launches, int64_t* span) {
+    if (!b) return fail(LBM_ERR_ARG, "null batch");
+    if (n_groups) *n_groups = (int)b->groups.size();
+    if (launches) *launches = b->launches;
+    if (span) *span = b->span;
     return LBM_OK;
 }
 

@@ -405,10 +405,12 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
             if (lv.bflag[b]) continue;
             int tid = omp_get_thread_num();
             bool simple = true;
+            bool stream = true;     // only record-free fluid cells, fine ghosts and absent slots
             for (int l = 0; l < BS; ++l) {
                 int64_t cell = b * BS + l;
                 uint8_t t = lv.type[cell];
                 if (t != C_FLUID) simple = false;
+                if (!(t == C_FLUID || t == C_FGHOST || t == C_ABSENT)) stream = false;
                 if (t == C_ABSENT || t == C_SOLID) continue;
                 int lx = l % g.B[0], ly = (l / g.B[0]) % g.B[1], lz = l / (g.B[0] * g.B[1]);
                 int64_t c[3] = {int64_t(lv.bxyz[3 * b]) * g.B[0] + lx, int64_t(lv.bxyz[3 * b + 1]) * g.B[1] + ly,
@@ -479,9 +481,12 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                     r.b = in.faces[f].kind | (f << 4);
                     r.mask = 0;
                 }
-                if (need) trec[tid].push_back({cell, r});
+                if (need) {
+                    trec[tid].push_back({cell, r});
+                    stream = false;
+                }
             }
-            lv.bflag[b] = simple ? 1 : 0;
+            lv.bflag[b] = simple ? 1 : (stream ? 2 : 0);
         }
         for (auto& e : errs)
             if (!e.empty()) return e + " (level " + std::to_string(i) + ")";

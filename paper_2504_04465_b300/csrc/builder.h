@@ -61,7 +61,9 @@ struct BuiltLevel {
     std::vector<int32_t> bxyz;        // nb x 3 block coordinates (Morton order)
     std::vector<int32_t> nbr;         // nb x 27 neighbour blocks (offset (dx,dy,dz) -> (dx+1)+3(dy+1)+9(dz+1)), -1 if none
     std::vector<uint8_t> type;        // nb x BS
-    std::vector<uint8_t> bflag;       // nb: 1 = simple (all cells fluid, every source a live non-solid cell)
+    std::vector<uint8_t> bflag;       // nb: 1 = simple (all cells fluid, every source a live non-solid cell),
+                                      // 2 = streaming block (record-free fluid cells, fine ghosts, absent slots),
+                                      // 0 = general
     std::vector<int32_t> rec_id;      // nb x BS: index into recs or -1
     std::vector<CellRec> recs;
     std::vector<int32_t> bindex;      // dense block grid -> block index or -1

@@ -18,14 +18,15 @@ struct LevelDev {
     long long ncell;         // nb * BS: SoA stride
     const int* nbr;          // nb * 27
     const unsigned char* type;
-    const unsigned char* bflag;
+    const unsigned char* bflag;   // 1 simple, 2 streaming, 0 general
     const int* rec_id;
     const CellRecDev* recs;
     void* f[2];
     void* g[2];
     double* lam;             // 2 buffers x 8 x ncell (numerical equilibrium)
     double tau;
-    const int* blist[2];     // [0] simple blocks (every cell fluid, every source live), [1] the others
+    const int* blist[2];     // [0] 2 * block + s: simple (s = 0) and streaming (s = 1) blocks, [1] the others
+                             // (block nb of f/g holds zero populations: the missing-neighbour stand-in)
     long long nlist[2];
 };
 

@@ -54,6 +54,7 @@ struct D2Q21M {
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = 2, MINB_GEN = 2;
     static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
+    static constexpr bool BATCH = false;  // compile the batched multi-case launch
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<21>::cx(q); }

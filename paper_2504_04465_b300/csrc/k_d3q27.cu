@@ -9,6 +9,7 @@ template <bool RR_> struct D3Q27M {
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = 6, MINB_GEN = 4;
     static constexpr bool TUNE = true;      // compile occupancy variants for the autotuner
+    static constexpr bool BATCH = false; // compile the batched multi-case launch
     static constexpr bool DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
     __host__ __device__ static constexpr int cx(int q) { return TP<3>::cx(q); }

@@ -18,6 +18,9 @@ struct KernelSet {
     void (*variant[4])(const StepArgs&, long long, long long, cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
     int variant_minb[4] = {0, 0, 0, 0};
     int n_variants = 1;
+    // batched launches of several cases (per variant; null where the lattice has none)
+    void (*batch[4])(const StepArgs*, const long long*, const long long*, int, long long, long long,
+                     cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Kernels for (model, storage, block shape) of each lattice; false if that combination is not built.

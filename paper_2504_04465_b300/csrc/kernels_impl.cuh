@@ -264,27 +264,31 @@ __device__ __forceinline__ int find_level_list(const StepArgs& a, int list, long
     return a.active[k];
 }
 
-// MINB > 0 overrides the model's occupancy target (resident 128-thread blocks per SM)
-template <class M, int ST, int BX, int BY, int BZ, bool FAST, int MINB>
-__global__ void __launch_bounds__(BX * BY * BZ,
-                                  (MINB > 0 ? MINB : ((FAST ? M::MINB_FAST : M::MINB_GEN) / (ST == ST_F64 ? 2 : 1))) * 128 /
-                                      (BX * BY * BZ))
-k_step(const StepArgs a) {
+// One block of cells of the iteration described by a (bid: the block's index in the
+// iteration's FAST or general list, over all active levels).
+template <class M, int ST, int BX, int BY, int BZ, bool FAST>
+__device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int* nbr_s, unsigned long long* s_nstat) {
     using T = typename Store<ST>::T;
     constexpr int BS = BX * BY * BZ;
-    __shared__ int nbr_s[27];
-    __shared__ unsigned long long s_nstat[19];
     long long i;
-    const int lev = find_level_list(a, FAST ? 0 : 1, blockIdx.x, &i);
+    const int lev = find_level_list(a, FAST ? 0 : 1, bid, &i);
     const LevelDev& L = a.lv[lev];
-    const long long b = L.blist[FAST ? 0 : 1][i];
+    const int entry = L.blist[FAST ? 0 : 1][i];
+    // FAST list entries carry a streaming-block bit: such blocks hold fine ghosts and absent
+    // slots besides record-free fluid cells, so the cell types are read and a missing
+    // neighbour block reads the zero-population block nb
+    const long long b = FAST ? (long long)(entry >> 1) : (long long)entry;
+    const bool streaming = FAST && (entry & 1);
     const int l = threadIdx.x;
-    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    if (l < 27) {
+        const int v = L.nbr[b * 27 + l];
+        nbr_s[l] = (FAST && v < 0) ? (int)L.nb : v;
+    }
     if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
     __syncthreads();
     const long long cell = b * BS + l;
     const int rd = a.rd[lev], wr = rd ^ 1;
-    const int type = FAST ? (int)C_FLUID : (int)L.type[cell];
+    const int type = (FAST && !streaming) ? (int)C_FLUID : (int)L.type[cell];
     const bool work = !(type == C_ABSENT || type == C_SOLID || (type == C_FGHOST && a.sync_fg[lev]));
     int iters = -1;
     if (work) {
@@ -361,6 +365,38 @@ k_step(const StepArgs a) {
     }
 }
 
+// occupancy target (resident 128-thread blocks per SM); MINB > 0 overrides the model's
+template <class M, int ST, bool FAST, int MINB>
+constexpr int step_min_blocks(int threads) {
+    return (MINB > 0 ? MINB : ((FAST ? M::MINB_FAST : M::MINB_GEN) / (ST == ST_F64 ? 2 : 1))) * 128 / threads;
+}
+
+template <class M, int ST, int BX, int BY, int BZ, bool FAST, int MINB>
+__global__ void __launch_bounds__(BX * BY * BZ, step_min_blocks<M, ST, FAST, MINB>(BX * BY * BZ))
+k_step(const StepArgs a) {
+    __shared__ int nbr_s[27];
+    __shared__ unsigned long long s_nstat[19];
+    step_block<M, ST, BX, BY, BZ, FAST>(a, blockIdx.x, nbr_s, s_nstat);
+}
+
+// Batched form: the blocks of several independent cases of one iteration in one launch.
+// args[k] describes case k at this iteration; off[k] .. off[k + 1] are its blocks in the
+// launch (off[n] = grid size).  A block finds its case by binary search.
+template <class M, int ST, int BX, int BY, int BZ, bool FAST, int MINB>
+__global__ void __launch_bounds__(BX * BY * BZ, step_min_blocks<M, ST, FAST, MINB>(BX * BY * BZ))
+k_step_batch(const StepArgs* __restrict__ args, const long long* __restrict__ off, int n) {
+    __shared__ int nbr_s[27];
+    __shared__ unsigned long long s_nstat[19];
+    const long long bid = blockIdx.x;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bid >= off[mid]) lo = mid;
+        else hi = mid;
+    }
+    step_block<M, ST, BX, BY, BZ, FAST>(args[lo], bid - off[lo], nbr_s, s_nstat);
+}
+
 // ------------------------------------------------------------------ readout
 // out (FP64, SoA over the level's slots): which = 0 moments (rho, ux, uy, uz, T),
 // 1 populations f, 2 populations g, 3 lambda
@@ -375,7 +411,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
     if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
     __syncthreads();
     const long long cell = b * BS + l;
-    const bool simple = L.bflag[b] != 0;
+    const bool simple = L.bflag[b] == 1;
     const int type = simple ? (int)C_FLUID : (int)L.type[cell];
     if (type == C_ABSENT || type == C_SOLID) return;
     Cell<M, ST> c;
@@ -421,7 +457,7 @@ __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, d
     if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
     __syncthreads();
     const long long cell = b * BS + l;
-    const bool simple = L.bflag[b] != 0;
+    const bool simple = L.bflag[b] == 1;
     const int type = simple ? (int)C_FLUID : (int)L.type[cell];
     double v[5] = {0, 0, 0, 0, 0};
     if (type == C_FLUID || type == C_BC || type == C_CGHOST) {
@@ -491,8 +527,19 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
     const long long b = blockIdx.x;
     const int l = threadIdx.x;
     const long long cell = b * BS + l;
-    const int type = L.bflag[b] ? (int)C_FLUID : (int)L.type[cell];
-    if (type == C_ABSENT || type == C_SOLID) return;
+    // block nb (one past the last) is the zero-population block; absent and solid slots hold
+    // zero populations in both buffers too, so that a plain gather reads a zero where the
+    // pull has no source
+    const int type = (b == L.nb) ? (int)C_ABSENT : (L.bflag[b] == 1 ? (int)C_FLUID : (int)L.type[cell]);
+    if (type == C_ABSENT || type == C_SOLID) {
+#pragma unroll 1
+        for (int q = 0; q < M::Q; ++q) {
+            const T z = M::DEV ? -ref_f<M, ST>(a.m, q) : T(0);
+            store_pop<M, ST, BX * BY * BZ>(L, 0, cell, q, a.m, z, T(0));
+            store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, z, T(0));
+        }
+        return;
+    }
     const long long n = L.ncell;
     const T rho = T(rho_in[cell]);
     const T ux = T(u_in[cell]), uy = T(u_in[n + cell]), uz = T(M::D == 3 ? u_in[2 * n + cell] : 0.0);
@@ -536,10 +583,10 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
     if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
     __syncthreads();
     const long long cell = b * BS + l;
-    const int type = L.bflag[b] ? (int)C_FLUID : (int)L.type[cell];
+    const int type = L.bflag[b] == 1 ? (int)C_FLUID : (int)L.type[cell];
     if (type == C_ABSENT || type == C_SOLID) return;
     unsigned long long bmask = 0ull;
-    if (!L.bflag[b] && type == C_FLUID) {
+    if (L.bflag[b] != 1 && type == C_FLUID) {
         const int r = L.rec_id[cell];
         if (r >= 0) bmask = L.recs[r].mask;
     }
@@ -586,6 +633,12 @@ struct Launch {
         if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(a);
         if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(a);
     }
+    template <int MINB_F, int MINB_G>
+    static void batch(const StepArgs* args, const long long* off_fast, const long long* off_gen, int n,
+                      long long n_fast, long long n_gen, cudaStream_t s) {
+        if (n_fast) k_step_batch<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(args, off_fast, n);
+        if (n_gen) k_step_batch<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(args, off_gen, n);
+    }
     static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
         if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);
     }
@@ -595,7 +648,7 @@ struct Launch {
     }
     static void init(const StepArgs& a, int lev, const double* r, const double* u, const double* t, cudaStream_t s) {
         if (!a.lv[lev].nb) return;
-        k_init_eq<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, r, u, t);
+        k_init_eq<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb + 1, BX * BY * BZ, 0, s>>>(a, lev, r, u, t);
         k_init_prestream<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
     }
 };
@@ -608,11 +661,17 @@ KernelSet make_set() {
     k.variant[0] = &LS::template step<0, 0>;
     k.variant_minb[0] = 0;
     k.n_variants = 1;
+    if constexpr (M::BATCH) k.batch[0] = &LS::template batch<0, 0>;
     if constexpr (M::TUNE && ST != ST_F64) {       // occupancy targets tried by the autotuner
         // (interior kernel, general kernel) resident 128-thread blocks; encoded 10 * F + G
         k.variant[1] = &LS::template step<8, 4>;
         k.variant[2] = &LS::template step<8, 6>;
         k.variant[3] = &LS::template step<6, 6>;
+        if constexpr (M::BATCH) {
+            k.batch[1] = &LS::template batch<8, 4>;
+            k.batch[2] = &LS::template batch<8, 6>;
+            k.batch[3] = &LS::template batch<6, 6>;
+        }
         k.variant_minb[1] = 84;
         k.variant_minb[2] = 86;
         k.variant_minb[3] = 66;

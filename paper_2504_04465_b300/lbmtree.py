@@ -88,6 +88,12 @@ _sig = {
     "lbm_newton_batch": [_P, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p],
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
+    "lbm_batch_create": [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
+    "lbm_batch_destroy": [C.c_void_p],
+    "lbm_batch_use_graph": [C.c_void_p, C.c_int],
+    "lbm_batch_step": [C.c_void_p, C.c_int64],
+    "lbm_batch_sync": [C.c_void_p],
+    "lbm_batch_info": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "lbm_mlp_train": [_P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
 }
 for _name, _args in _sig.items():
@@ -98,6 +104,42 @@ _lib.lbm_last_error.argtypes = []
 _lib.lbm_last_error.restype = C.c_char_p
 
 EXPORTED = sorted(list(_sig) + ["lbm_last_error"])
+
+
+class Batch:
+    """Several contexts stepped together (lbm_batch_*)."""
+
+    def __init__(self, cases, stream: int = 0):
+        self.cases = list(cases)                 # keeps the contexts alive
+        arr = (C.c_void_p * len(self.cases))(*[c._h.value for c in self.cases])
+        h = C.c_void_p()
+        _check(_lib.lbm_batch_create(C.byref(h), arr, len(self.cases), C.c_void_p(stream)), "lbm_batch_create")
+        self._h = h
+
+    def use_graph(self, on: bool = True) -> None:
+        _check(_lib.lbm_batch_use_graph(self._h, int(on)), "lbm_batch_use_graph")
+
+    def step_fine(self, n: int) -> None:
+        _check(_lib.lbm_batch_step(self._h, n), "lbm_batch_step")
+
+    def sync(self) -> None:
+        _check(_lib.lbm_batch_sync(self._h), "lbm_batch_sync")
+
+    def info(self):
+        g, l, s = C.c_int(), C.c_int64(), C.c_int64()
+        _check(_lib.lbm_batch_info(self._h, C.byref(g), C.byref(l), C.byref(s)), "lbm_batch_info")
+        return {"groups": g.value, "launches": l.value, "span": s.value}
+
+    def close(self) -> None:
+        if self._h:
+            _lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MlpTrainParams(C.Structure):
