@@ -216,3 +216,87 @@ def naca_fields(level, coords: np.ndarray, mach: float, T0: float, gamma: float 
     u[0] = u_in * (1.0 + 1e-3 * uniform_at(NACA_SEED, level, coords, 0))
     u[1] = 1e-3 * u_in * uniform_at(NACA_SEED, level, coords, 1)
     return np.ones(n), u, np.full(n, T0)
+
+
+# ------------------------------------------------------------------ batch of uneven 2D cases
+def _place_boxes(rng, parents, n_boxes, unit, margin, frac=(0.3, 0.55), min_cells=32):
+    """Up to n_boxes disjoint boxes, each inside one of the parent boxes (lo, hi) with
+    ``margin`` parent cells of clearance from the parent's edges and from each other; edges on
+    multiples of ``unit`` finest units (8 parent cells)."""
+    out = []
+    for _ in range(n_boxes):
+        for _attempt in range(20):
+            plo, phi = parents[rng.integers(len(parents))]
+            lo, hi = [], []
+            ok = True
+            for d in range(2):
+                span = phi[d] - plo[d]
+                size = int(rng.uniform(*frac) * span) // unit * unit
+                room = span - size - 2 * margin
+                if size < min_cells * unit // 8 or room < 0:
+                    ok = False
+                    break
+                start = plo[d] + margin + int(rng.integers(0, room // unit + 1)) * unit
+                lo.append(start)
+                hi.append(start + size)
+            if not ok:
+                continue
+            clash = any(all(lo[d] < b_hi[d] + margin and b_lo[d] < hi[d] + margin for d in range(2))
+                        for b_lo, b_hi in out)
+            if not clash:
+                out.append((tuple(lo), tuple(hi)))
+                break
+    return out
+
+
+def batch_cases(seed: int = 48, n: int = 48):
+    """Uneven 2D cases for batched stepping (PCG64 stream ``seed``): coarse sides 2^U{6..10},
+    2-4 levels, 1-3 refined boxes per level nested in the next coarser level's boxes, half
+    D2Q9 recursive-regularized Taylor-Green, half D2Q37 polynomial-DDF Sod tubes along x.
+
+    Returns dicts {name, lattice, model, spec, fields(level, coords) -> (rho, u[, T]), params}."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        L = int(rng.integers(2, 5))
+        s = 2 ** (L - 1)
+        tg = (k % 2 == 0)
+        if tg:
+            cx = cy = 2 ** int(rng.integers(6, 11))
+        else:
+            cx = 2 ** int(rng.integers(7, 11))
+            cy = 2 ** int(rng.integers(6, min(int(np.log2(cx)), 9) + 1))
+        ext = (cx * s, cy * s)
+        boxes = []
+        parents = [((0, 0), ext)]
+        for lev in range(L - 2, -1, -1):
+            unit = 8 * 2 ** (lev + 1)                  # 8 cells of the parent level
+            margin = 16 * 2 ** (lev + 1)
+            placed = _place_boxes(rng, parents, int(rng.integers(1, 4)), unit, margin)
+            if not placed:
+                break
+            boxes += [(lev, lo, hi) for lo, hi in placed]
+            parents = placed
+        levels = L if boxes else 1
+        if levels < L:                                 # drop the empty finer levels
+            shift = L - levels
+            ext = (ext[0] >> shift, ext[1] >> shift)
+            boxes = [(lev - shift, tuple(v >> shift for v in lo), tuple(v >> shift for v in hi)) for lev, lo, hi in boxes]
+        if tg:
+            spec = GridSpec(2, ext, levels, boxes, (True, True))
+            u0, nc = 0.05, cx
+
+            def fields(level, coords, nc=nc, levels=levels, u0=u0):
+                c = cell_centres(coords, level)
+                return taylor_green_fields(c, nc, levels, u0, 1.0 / 3.0)
+            cases.append({"name": f"tg{k}", "lattice": "D2Q9", "model": "rr", "spec": spec, "fields": fields,
+                          "params": {"nu0": 0.01 * 2 ** (levels - 1)}})
+        else:
+            spec = GridSpec(2, ext, levels, boxes, (False, True), {"x-": ("neumann",), "x+": ("neumann",)})
+            T0 = 0.7
+
+            def fields(level, coords, nx=ext[0], T0=T0):
+                return sod_fields(cell_centres(coords, level), nx, T0)
+            cases.append({"name": f"sod{k}", "lattice": "D2Q37", "model": "poly_ddf", "spec": spec, "fields": fields,
+                          "params": {"nu0": 0.0, "T0": T0, "sensor_A": 1.5}})
+    return cases

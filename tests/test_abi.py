@@ -120,3 +120,30 @@ def test_velocity_sets_match_oracle(lt):
         xi = c.velocities()[:, :dim]
         assert {tuple(int(a) for a in v) for v in xi} == {tuple(int(a) for a in v) for v in L.LATTICES[latname].xi}
         assert np.array_equal(xi[::-1], -xi)          # opposite of q is Q-1-q
+
+
+def test_batch_needs_initialised_device_contexts(lt):
+    ctx = lt.Context(2, device=-1)
+    ctx.configure(I.taylor_green_spec(32, 8, 24, 2), "D2Q9", "rr", "f64", nu0=0.02)
+    with pytest.raises(lt.LbmError) as e:
+        lt.Batch([ctx])
+    assert lt.ERR[e.value.code] == "STATE"
+    with pytest.raises(lt.LbmError):
+        lt.Batch([])
+
+
+def test_batch_case_recipe_builds(lt):
+    cases = I.batch_cases()
+    assert len(cases) == 48
+    assert sum(c["lattice"] == "D2Q9" for c in cases) == 24
+    total = 0
+    levels = set()
+    for c in cases:
+        ctx = lt.Context(2, device=-1)
+        ctx.configure(c["spec"], c["lattice"], c["model"], "f32", **c["params"])
+        s = ctx.stats()
+        total += int(sum(s.n_cells[:s.n_levels]))
+        levels.add(s.n_levels)
+        ctx.close()
+    assert 20e6 <= total <= 30e6, total
+    assert levels == {2, 3, 4}

@@ -78,3 +78,63 @@ def test_line_search_never_increases_residual():
         cur = np.linalg.norm(nm.residual(M, lam_k, tgt)[0], axis=0)
         assert np.all(cur <= prev * (1 + 1e-12) + 1e-300)
         prev = cur
+
+
+def test_cholesky_solve_matches_library_and_flags_singular():
+    rng = np.random.default_rng(21)
+    B = rng.standard_normal((40, 8, 8))
+    A = B @ np.transpose(B, (0, 2, 1)) + 0.1 * np.eye(8)
+    b = rng.standard_normal((40, 8))
+    x = nm.cholesky_solve(A, b)
+    ref = np.linalg.solve(A, b[:, :, None])[:, :, 0]
+    assert np.abs(x - ref).max() < 1e-10 * np.abs(ref).max()
+    S = A[:2].copy()
+    S[0, 3, :] = S[0, :, 3] = 0.0            # singular (zero row and column)
+    S[1, 5, 5] = -1.0                        # not positive definite
+    assert np.isnan(nm.cholesky_solve(S, b[:2])).all()
+
+
+def test_polynomial_guess_is_the_weighted_fit_where_it_helps():
+    lat = L.LATTICES["D2Q21"]
+    from oracle import hermite as hm
+    u = np.array([[0.2], [0.1]])
+    T = np.array([0.7])
+    g = nm.poly_guess(lat, u, T, 3)[:, 0]
+    # the same weighted least-squares problem through the library's lstsq
+    fp = hm.feq_thermal(lat, np.ones(1), u, T, 3)[:, 0]
+    pos = fp > 0
+    M = nm.moment_basis(lat)
+    sw = np.sqrt(lat.w[pos])
+    ref = np.linalg.lstsq(M[:, pos].T * sw[:, None], (-1.0 - np.log(fp[pos])) * sw, rcond=None)[0]
+    assert np.abs(g - ref).max() < 1e-10
+
+
+def test_polynomial_guess_falls_back_to_zero_at_high_mach():
+    lat = L.LATTICES["D2Q21"]
+    from oracle import hermite as hm
+    u = np.array([[1.43], [0.0]])            # Mach 1.5 at T = 0.65 (gamma 1.4)
+    T = np.array([0.65])
+    g = nm.poly_guess(lat, u, T, 3)
+    assert np.array_equal(g, np.zeros((8, 1)))
+    # there the fit itself is farther from the root than lambda = 0
+    fp = hm.feq_thermal(lat, np.ones(1), u, T, 3)[:, 0]
+    pos = fp > 0
+    M = nm.moment_basis(lat)
+    sw = np.sqrt(lat.w[pos])
+    fit = np.linalg.lstsq(M[:, pos].T * sw[:, None], (-1.0 - np.log(fp[pos])) * sw, rcond=None)[0]
+    tgt = nm.mb_targets(u, T)
+    Gf, _ = nm.residual(M, fit[:, None], tgt)
+    G0, _ = nm.residual(M, np.zeros((8, 1)), tgt)
+    assert (Gf ** 2).sum() > (G0 ** 2).sum()
+    lam, e, it, conv = nm.newton(lat, u, T, g, 1e-12, 50)
+    assert conv.all()
+
+
+def test_newton_stops_without_error_at_an_unreachable_state():
+    lat = L.LATTICES["D2Q21"]
+    u = np.array([[2.0, 0.1], [0.0, 0.0]])   # |u| = 2: beyond the lattice (exp underflow)
+    T = np.array([0.65, 0.65])
+    lam, e, it, conv = nm.newton(lat, u, T, np.zeros((8, 2)), 1e-12, 50)
+    assert not conv[0] and conv[1]
+    assert it[0] < 50
+    assert np.isfinite(e).all() and np.isfinite(lam).all()
