@@ -177,6 +177,194 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ forms beside the plain FP32 method
+def _event_ms(stream, fn, reps=1):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def _moment_err(a, b, types):
+    """Relative L2 of rho and u of context a against context b over the listed cell types."""
+    ra, ua, _ = a.moments()
+    rb, ub, _ = b.moments()
+    m = np.isin(types, (1, 4))
+    return {"rho": float(np.linalg.norm(ra[m] - rb[m]) / np.linalg.norm(rb[m])),
+            "u": float(np.linalg.norm(ua[:, m] - ub[:, m]) / np.linalg.norm(ub[:, m]))}
+
+
+def form_fp16(args, stream, local, f32_ms):
+    """FP16-deviation storage on the same workload, and its error after 20 coarse steps on the
+    reduced sphere against the FP64 GPU path (itself equal to the oracle within 1e-12)."""
+    ctx = make_context(I.sphere_spec(args.scale), "f16dev", local, stream.cuda_stream, True, args.scale,
+                       DEFAULT_BLOCK["f16dev"], DEFAULT_VARIANT["f16dev"])
+    ctx.init_fields(*host_fields(ctx))
+    ctx.step(args.warmup)
+    upd = ctx.stats().cell_updates
+    ms = _event_ms(stream, lambda: ctx.step(args.steps)) / args.steps
+    ctx.sync()
+    ctx.close()
+    errs = {}
+    ref = make_context(I.sphere_spec(4), "f64", local, stream.cuda_stream, True, 4, (8, 4, 4), 0)
+    ref.init_fields(*host_fields(ref))
+    ref.step(20)
+    types = ref.cells()[2]
+    for st in ("f32", "f16dev"):
+        c = make_context(I.sphere_spec(4), st, local, stream.cuda_stream, True, 4, (8, 4, 4), 0)
+        c.init_fields(*host_fields(c))
+        c.step(20)
+        errs[st] = _moment_err(c, ref, types)
+        c.close()
+    ref.close()
+    bpu = BYTES_PER_UPDATE["f16dev"]
+    peak, kind = peaks()
+    return {"workload": "same as the main line, populations stored as binary16 deviations from w rho_ref",
+            "ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS", "speedup_vs_f32": f32_ms / ms,
+            "roofline": {"bound": "hbm", "bytes_per_update": bpu, "achieved": bpu * upd / ms / 1e6, "peak": peak,
+                         "frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind},
+            "err_vs_f64": errs,
+            "err_case": "reduced sphere (256x128x128, D=16, 4 levels), 20 coarse steps, relative L2 over bulk and "
+                        "boundary cells against the FP64 path"}
+
+
+LEARNED = {"chord": 2304, "mach": 1.5, "T0": 0.65, "Re": 1e4, "gamma": 1.4, "sensor_A": 1.35}
+
+
+def form_learned(args, stream, local):
+    """Numerical-equilibrium D2Q21 flow past a NACA0012 at Mach 1.5 (5 levels, N_eq 7.9 M):
+    Newton from the polynomial guess (the plain method), from the network trained here on the
+    solver's own equilibria, and from the previous multipliers (warm start)."""
+    import torch
+    from paper_2504_04465_b300 import lbmtree as lt
+    P = dict(LEARNED)
+    if args.scale > 1:
+        P["chord"] = 256
+    spec = I.naca_spec(P["chord"], P["mach"], P["T0"], P["gamma"])
+    u_in = P["mach"] * np.sqrt(P["gamma"] * P["T0"])
+    ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
+    ctx.configure(spec, "D2Q21", "num_ddf", "f32", nu0=u_in * P["chord"] / P["Re"], T0=P["T0"], gamma=P["gamma"],
+                  sensor_A=P["sensor_A"], guess="warm")
+    lv, xyz, ty = ctx.cells()
+    n = lv.size
+    rho, u, T = np.ones(n), np.zeros((2, n)), np.full(n, P["T0"])
+    for L in np.unique(lv):
+        m = lv == L
+        r, uu, tt = I.naca_fields(int(L), xyz[m, :2], P["mach"], P["T0"], P["gamma"])
+        rho[m], u[:, m], T[m] = r, uu, tt
+    ctx.init_fields(rho, u, T)
+    ctx.step(3)                                        # leave the impulsive start (warm start)
+    # training samples: (u, T) of the solver's fluid cells, filtered, split 90/10; targets are
+    # the converged multipliers at exactly those states (batched Newton from lambda = 0)
+    rho, u, T = ctx.moments()
+    cs = np.sqrt(P["gamma"] * P["T0"])
+    keep = (ty == 1) & (T > 0.5 * P["T0"]) & (T < 2 * P["T0"]) & (np.sqrt((u ** 2).sum(0)) < 2 * cs)
+    idx = np.random.default_rng(1504).permutation(np.nonzero(keep)[0])[:1_000_000]
+    ntr = int(0.9 * idx.size)
+    d_uT = torch.tensor(np.stack([u[0, idx], u[1, idx], T[idx]], axis=1), device="cuda")
+    d_lam = torch.empty((idx.size, 8), dtype=torch.float64, device="cuda")
+    d_it = torch.empty(idx.size, dtype=torch.int32, device="cuda")
+    ctx.newton_batch(d_uT.data_ptr(), idx.size, "zero", d_lam.data_ptr(), d_it.data_ptr())
+    ctx.sync()
+    lam_ref = d_lam.cpu().numpy()
+    t0 = time.perf_counter()
+    loss = ctx.mlp_train(d_uT.data_ptr(), d_lam.data_ptr(), ntr, steps=3000, batch=4096, lr=3e-3, lr_final=3e-4,
+                         seed=1504)
+    train_s = time.perf_counter() - t0
+    held = {}
+    nte = idx.size - ntr
+    d_te = d_uT[ntr:].contiguous()
+    for g in ("zero", "poly", "mlp"):
+        d_l = torch.empty((nte, 8), dtype=torch.float64, device="cuda")
+        d_i = torch.empty(nte, dtype=torch.int32, device="cuda")
+        ctx.newton_batch(d_te.data_ptr(), nte, g, d_l.data_ptr(), d_i.data_ptr())
+        ctx.sync()
+        it = d_i.cpu().numpy()
+        held[g] = {"mean_iters": float(it[it >= 0].mean()) if (it >= 0).any() else None,
+                   "nonconverged": int((it < 0).sum()),
+                   "max_abs_dlambda_vs_zero_guess": float(np.abs(d_l.cpu().numpy() - lam_ref[ntr:]).max())}
+    runs = {}
+    K = 1
+    for g in ("poly", "mlp", "warm"):
+        ctx.set_guess(g)
+        ctx.step(1)
+        s0 = ctx.stats()
+        ms = _event_ms(stream, lambda: ctx.step(K)) / K
+        ctx.sync()
+        s1 = ctx.stats()
+        runs[g] = {"ms_per_step": ms, "value": s1.cell_updates / ms / 1e3, "unit": "MLUPS",
+                   "mean_newton_iters": (s1.newton_iter_sum - s0.newton_iter_sum) /
+                   max(1, s1.newton_updates - s0.newton_updates),
+                   "nonconverged": s1.newton_nonconverged - s0.newton_nonconverged}
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": f"D2Q21 numerical equilibrium, NACA0012 chord {P['chord']}, Mach {P['mach']}, T0 {P['T0']}, "
+                        f"Re {P['Re']:.0f}, 5 levels, N_eq {st.n_eq:.0f}, FP32 populations, FP64 Newton (tol 1e-12)",
+            "step": "one coarse step = 16 fine iterations", "by_guess": runs,
+            "speedup_mlp_vs_poly": runs["poly"]["ms_per_step"] / runs["mlp"]["ms_per_step"],
+            "iterations_saved_vs_poly": runs["poly"]["mean_newton_iters"] - runs["mlp"]["mean_newton_iters"],
+            "heldout_newton": held,
+            "training": {"samples": int(ntr), "heldout": int(nte), "steps": 3000, "batch": 4096, "final_loss": loss,
+                         "seconds": train_s, "filter": "T in [0.5, 2] T0, |u| < 2 sqrt(gamma T0), fluid cells"},
+            "err": "Newton runs to the same tolerance from every guess: results agree within it"}
+
+
+def form_batched(args, stream, local):
+    """48 uneven 2D cases (D2Q9 Taylor-Green and D2Q37 Sod tubes, 2-4 levels): one batched
+    launch per lattice group per fine iteration (CUDA graph of the schedule period) against
+    stepping the cases one after another, each with its own graph."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    cases = I.batch_cases()
+    out = {"workload": "48 cases from the batch recipe (PCG64 seed 48), 23 M cells",
+           "step": "16 fine iterations of every case (one period of the 4-level schedule)"}
+    for storage in ("f32", "f16dev"):
+        ctxs = []
+        for cs in cases:
+            c = lt.Context(2, device=local, stream=stream.cuda_stream)
+            c.configure(cs["spec"], cs["lattice"], cs["model"], storage, **cs["params"])
+            lvl, xyz, _ = c.cells()
+            n = lvl.size
+            rho, u, T = np.ones(n), np.zeros((2, n)), np.zeros(n)
+            for L in np.unique(lvl):
+                m = lvl == L
+                r = cs["fields"](int(L), xyz[m, :2])
+                rho[m], u[:, m] = r[0], r[1]
+                if len(r) > 2:
+                    T[m] = r[2]
+            c.init_fields(rho, u, T if cs["model"] == "poly_ddf" else None)
+            c.use_graph(True)
+            ctxs.append(c)
+        stats = [c.stats() for c in ctxs]
+        upd = sum(s.cell_updates * 16 // (1 << (s.n_levels - 1)) for s in stats)
+        coarse = [16 >> (s.n_levels - 1) for s in stats]     # 16 fine iterations in coarse steps
+        b = lt.Batch(ctxs, stream.cuda_stream)
+        b.use_graph(True)
+        b.step_fine(32)
+        reps = 4
+        ms_b = _event_ms(stream, lambda: b.step_fine(16), reps)
+        b.sync()
+        l0 = b.info()["launches"]
+        for c, k in zip(ctxs, coarse):
+            c.step(k)
+        ms_s = _event_ms(stream, lambda: [c.step(k) for c, k in zip(ctxs, coarse)], reps)
+        for c in ctxs:
+            c.sync()
+        out[storage] = {"batched_ms": ms_b, "sequential_ms": ms_s, "speedup": ms_s / ms_b,
+                        "value": upd / ms_b / 1e3, "unit": "MLUPS", "sequential_value": upd / ms_s / 1e3,
+                        "groups": b.info()["groups"]}
+        b.close()
+        for c in ctxs:
+            c.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -273,6 +461,16 @@ def run_ours(args, world, rank, local):
         cpu = {"value": oracle_updates(counts, 0, nf) / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"FP64 numpy oracle, reduced sphere workload (256x128x128, D=16, 4 levels), {nf} fine "
                          f"iterations in {dt:.1f} s"}
+    forms = None
+    if not args.no_forms and args.storage == "f32":
+        forms = {}
+        for name, fn in (("fp16_store", lambda: form_fp16(args, stream, local, t_max / args.steps)),
+                         ("learned", lambda: form_learned(args, stream, local)),
+                         ("batched", lambda: form_batched(args, stream, local))):
+            try:
+                forms[name] = fn()
+            except Exception as e:                  # report, keep the main line
+                forms[name] = {"error": f"{type(e).__name__}: {e}"}
     line = {"metric": "fine-equivalent MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
@@ -285,7 +483,7 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs larger than L2 (9.7 GB of populations at f32)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "forms": forms}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -301,6 +499,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block", type=int, nargs=3, default=None)
     ap.add_argument("--variant", type=int, default=None)

@@ -141,6 +141,9 @@ const char* lbm_last_error(void);
 /* ---------------------------------------------------------------- configuration */
 int lbm_set_lattice(lbm_ctx* ctx, int lattice);
 int lbm_set_collision(lbm_ctx* ctx, int model, const lbm_collision_params* params);
+/* Newton starting point of the numerical equilibrium (LBM_GUESS_*), also on a built and running
+ * context (the next step uses it; the captured graph is rebuilt). */
+int lbm_set_guess(lbm_ctx* ctx, int guess);
 int lbm_set_precision(lbm_ctx* ctx, int storage);
 /* face 0..5; kind LBM_*; rho_u_T = {rho, ux, uy, uz, T} (ignored for PERIODIC/NEUMANN). */
 int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);

@@ -421,6 +421,14 @@ int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
     return LBM_OK;
 }
 
+int lbm_set_guess(lbm_ctx* c, int guess) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (guess < LBM_GUESS_WARM || guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "unknown Newton guess");
+    c->params.guess = guess;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
 int lbm_set_precision(lbm_ctx* c, int storage) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16DEV) return fail(LBM_ERR_ARG, "unknown storage");

@@ -38,7 +38,28 @@ __device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, do
             }
         }
     }
-    chol8_solve(A, b, lam);
+    double fit[8];
+    chol8_solve(A, b, fit);
+    // keep the fit where it is finite and closer to the root than lambda = 0 (at large |u| or T
+    // far from the lattice temperature the truncated polynomial is a poor start)
+    const double u2 = ux * ux + uy * uy, t2 = u2 + 4.0 * Tt;
+    const double tgt[8] = {1.0, ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fin = fin && isfinite(fit[a]);
+    double e[21], G[8], gf = 0.0, g0 = 0.0;
+    if (fin) {
+        newton_eval<21>(fit, tgt, e, G);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) gf += G[a] * G[a];
+        const double zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        newton_eval<21>(zero, tgt, e, G);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
+    }
+    const bool keep = fin && (gf < g0);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) lam[a] = keep ? fit[a] : 0.0;
 }
 
 // network guess lambda0 = m + s * y(u_x, u_y, T/T0 - 1)

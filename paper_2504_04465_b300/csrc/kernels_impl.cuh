@@ -136,7 +136,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
                 const int rdf = a.rd[lev - 1];
                 constexpr int NK = (M::D == 3) ? 8 : 4;
                 T sf = 0, sg = 0;
-#pragma unroll
+#pragma unroll 1
                 for (int k = 0; k < NK; ++k) {
                     const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
                     const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, M::cx(q), M::cy(q), M::cz(q));
@@ -338,7 +338,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
                 const int wrf = a.rd[lev - 1] ^ 1;
                 const long long child = L.recs[L.rec_id[cell]].a;
                 constexpr int NK = (M::D == 3) ? 8 : 4;
-#pragma unroll
+#pragma unroll 1
                 for (int kk = 0; kk < NK; ++kk) {
                     const long long ch = child + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
 #pragma unroll

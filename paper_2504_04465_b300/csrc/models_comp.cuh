@@ -121,7 +121,10 @@ __device__ __forceinline__ void newton_dir(const double* e, const double* G, dou
 }
 
 // Solve for lambda (in/out) at (u, T); e[] receives exp(-(1 + lambda.M)) (rho = 1).
-// Returns the number of Newton steps; *conv = 1 if max |G| < tol.
+// Returns the number of Newton steps; *conv = 1 if the residual is finite and max |G| < tol.
+// A cell stops unconverged at its last finite iterate when the Jacobian's Cholesky
+// factorisation meets a non-positive pivot (non-finite direction) or the line search ends on a
+// non-finite trial.
 template <int Q>
 __device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double* lam, double* e, double tol,
                                          int max_iter, int* conv) {
@@ -133,17 +136,26 @@ __device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double
     int it = 0;
     for (;; ++it) {
         double gmax = 0.0;
+        bool fin = true;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) gmax = fmax(gmax, fabs(G[a]));
-        if (gmax < tol) { *conv = 1; break; }
-        if (it == max_iter) break;
+        for (int a = 0; a < 8; ++a) {
+            fin = fin && isfinite(G[a]);
+            gmax = fmax(gmax, fabs(G[a]));
+        }
+        if (fin && gmax < tol) { *conv = 1; break; }
+        if (!fin || it == max_iter) break;
         double d[8];
         newton_dir<Q>(e, G, d);
+        bool dfin = true;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) dfin = dfin && isfinite(d[a]);
+        if (!dfin) break;
         double g0 = 0.0;
 #pragma unroll
         for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
         double t = 1.0;
         double trial[8], Gt[8];
+        bool take = false;
 #pragma unroll 1
         for (int h = 0; h <= 30; ++h) {
 #pragma unroll
@@ -152,8 +164,12 @@ __device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double
             double g1 = 0.0;
 #pragma unroll
             for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
-            if (g1 < g0 || h == 30) break;
+            if (g1 < g0 || (h == 30 && isfinite(g1))) { take = true; break; }
             t *= 0.5;
+        }
+        if (!take) {                        // keep the current iterate (restore its e)
+            newton_eval<Q>(lam, tgt, e, G);
+            break;
         }
 #pragma unroll
         for (int a = 0; a < 8; ++a) { lam[a] = trial[a]; G[a] = Gt[a]; }

@@ -88,6 +88,7 @@ _sig = {
     "lbm_newton_batch": [_P, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p],
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
+    "lbm_set_guess": [_P, C.c_int],
     "lbm_batch_create": [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
     "lbm_batch_destroy": [C.c_void_p],
     "lbm_batch_use_graph": [C.c_void_p, C.c_int],
@@ -217,6 +218,9 @@ class Context:
         p = CollisionParams(nu0, T0, gamma, int(sensor_A is not None), sensor_A or 0.0, newton_tol,
                             newton_max_iter, GUESS[guess], rho_ref)
         _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
+
+    def set_guess(self, guess: str) -> None:
+        _check(_lib.lbm_set_guess(self._h, GUESS[guess]), "lbm_set_guess")
 
     def set_precision(self, storage: str) -> None:
         _check(_lib.lbm_set_precision(self._h, STORAGE[storage]), "lbm_set_precision")

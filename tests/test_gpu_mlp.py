@@ -165,9 +165,12 @@ def test_batched_newton_matches_oracle_and_trained_guess_saves_iterations():
 
 
 def test_solver_with_learned_guess_matches_oracle():
-    ctx, uT, lam = solver_samples(20)
+    ctx, uT, _ = solver_samples(20)
     n = uT.shape[0]
-    d_uT, d_lam = dev(uT, torch.float64), dev(lam, torch.float64)
+    d_uT = dev(uT, torch.float64)
+    d_lam = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    d_it = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.newton_batch(d_uT.data_ptr(), n, "zero", d_lam.data_ptr(), d_it.data_ptr())
     ctx.mlp_train(d_uT.data_ptr(), d_lam.data_ptr(), n, steps=1500, batch=1024)
     params, m, s = ctx.mlp_get()
     ctx.close()
