@@ -103,10 +103,13 @@ typedef struct {
     double gamma;        /* specific heat ratio of the DDF (Cv = 1/(gamma-1))                   */
     int    sensor_on;    /* kinetic shock sensor, Eqs. DeltaAvg / shock_function                */
     double sensor_A;     /* value of alpha on [0.1, 1)                                          */
-    double newton_tol;   /* stop when max |G| < tol (1e-12 in FP64)                             */
+    double newton_tol;   /* stop when max |G| < tol; <= 0: 1e-12 (FP64) or 1e-5 (FP32 solve)      */
     int    newton_max_iter;
     int    guess;        /* LBM_GUESS_*                                                         */
     double rho_ref;      /* reference density of the F16DEV storage (1.0)                       */
+    int    newton_fp32;  /* 1: Newton of the numerical equilibrium in FP32 arithmetic (the
+                            paper's single-precision threshold is 1e-5); multipliers kept in
+                            FP64 between steps.  0 (default): FP64 Newton.                     */
 } lbm_collision_params;
 
 typedef struct { int level; int64_t lo[3]; int64_t hi[3]; } lbm_box;     /* finest units */

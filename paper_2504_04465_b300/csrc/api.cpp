@@ -76,6 +76,8 @@ struct lbm_ctx {
     bool host_only = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;        // created by the context (caller passed NULL)
+    cudaStream_t side = nullptr;    // general-kernel stream, forked from and joined to `stream`
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int lattice = 0, model = 0, storage = LBM_F64;
     bool params_set = false;
     lbm_collision_params params{};
@@ -180,9 +182,10 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     m.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : 1.0;
     m.sensor_on = c->params.sensor_on;
     m.sensor_A = c->params.sensor_A;
-    m.newton_tol = c->params.newton_tol > 0 ? c->params.newton_tol : 1e-12;
+    m.newton_tol = c->params.newton_tol > 0 ? c->params.newton_tol : (c->params.newton_fp32 ? 1e-5 : 1e-12);
     m.newton_max_iter = c->params.newton_max_iter > 0 ? c->params.newton_max_iter : 50;
     m.guess = c->params.guess;
+    m.newton_fp32 = c->params.newton_fp32;
     m.mlp = c->d_mlp;
     for (int k = 0; k < 8; ++k) { m.mlp_m[k] = c->mlp_m[k]; m.mlp_s[k] = c->mlp_s[k]; }
     for (int f = 0; f < 6; ++f) {
@@ -263,14 +266,27 @@ float bf16_round_host(float v) {
     return r;
 }
 
+// one fine iteration: the general kernel on the side stream beside the interior kernel
+void launch_step(lbm_ctx* c, const StepArgs& a) {
+    const int64_t nf = a.list_off[0][a.n_active], ng = a.list_off[1][a.n_active];
+    if (nf && ng) {
+        cudaEventRecord(c->ev_fork, c->stream);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        c->ks.step(a, nf, ng, c->stream, c->side);
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    } else {
+        c->ks.step(a, nf, ng, c->stream, c->stream);
+    }
+}
+
 int launch_iterations(lbm_ctx* c, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
         StepArgs a;
         const int64_t nb = iteration_args(c, c->t, a);
         if (nb) {
-            const int64_t nf = a.list_off[0][a.n_active], ng = a.list_off[1][a.n_active];
-            c->ks.step(a, nf, ng, c->stream);
-            c->launches += (nf > 0) + (ng > 0);
+            launch_step(c, a);
+            c->launches += (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
         }
         c->t++;
     }
@@ -286,7 +302,7 @@ int build_graph(lbm_ctx* c) {
     for (int64_t k = 0; k < span; ++k) {
         StepArgs a;
         const int64_t nb = iteration_args(c, k, a);
-        if (nb) c->ks.step(a, a.list_off[0][a.n_active], a.list_off[1][a.n_active], c->stream);
+        if (nb) launch_step(c, a);
     }
     if (cudaGetLastError() != cudaSuccess) {       // end the capture so the stream stays usable
         cudaGraph_t g2 = nullptr;
@@ -368,6 +384,16 @@ int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
             }
             c->own_stream = true;
         }
+        e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (c->side) cudaStreamDestroy(c->side);
+            if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(LBM_ERR_CUDA, std::string("side stream: ") + cudaGetErrorString(e));
+        }
         std::lock_guard<std::mutex> lk(g_upload_mu);
         if (device < 256 && !g_uploaded[device]) {
             const Constants& k = constants();
@@ -389,6 +415,12 @@ int lbm_destroy(lbm_ctx* c) {
     if (!c->host_only) cudaSetDevice(c->device);
     c->release();
     if (c->d_mlp) cudaFree(c->d_mlp);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return LBM_OK;
@@ -412,6 +444,8 @@ int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
         if (p->nu0 < 0) return fail(LBM_ERR_ARG, "negative viscosity");
         if (p->gamma <= 1.0 && model >= LBM_COMP_POLY) return fail(LBM_ERR_ARG, "gamma must exceed 1");
         if (p->guess < 0 || p->guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "unknown Newton guess");
+        if (p->newton_fp32 && p->newton_tol > 0 && p->newton_tol < 1e-6)
+            return fail(LBM_ERR_ARG, "an FP32 Newton solve cannot reach a tolerance below 1e-6 (use 1e-5)");
         c->params = *p;
         if (c->params.gamma <= 1.0) c->params.gamma = 1.4;
         if (c->params.rho_ref <= 0) c->params.rho_ref = 1.0;
@@ -925,6 +959,8 @@ struct lbm_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;                // general kernels, forked and joined per iteration
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<lbm_ctx*> cases;
     std::vector<int64_t> t0;                    // case times when the tables were built
     std::vector<Group> groups;
@@ -933,6 +969,12 @@ struct lbm_batch {
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
 
+    void release_streams() {
+        if (side) { cudaStreamSynchronize(side); cudaStreamDestroy(side); side = nullptr; }
+        if (ev_fork) { cudaEventDestroy(ev_fork); ev_fork = nullptr; }
+        if (ev_join) { cudaEventDestroy(ev_join); ev_join = nullptr; }
+        if (own_stream && stream) { cudaStreamDestroy(stream); stream = nullptr; }
+    }
     void free_tables() {
         if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
         for (auto& g : groups) {
@@ -981,14 +1023,18 @@ int batch_tables(lbm_batch* b) {
     return LBM_OK;
 }
 
-// one fine iteration of every case (table row j)
+// one fine iteration of every case (table row j); general kernels on the side stream
 void batch_iteration(lbm_batch* b, int64_t j) {
+    cudaEventRecord(b->ev_fork, b->stream);
+    cudaStreamWaitEvent(b->side, b->ev_fork, 0);
     for (auto& g : b->groups) {
         const int n = (int)g.cases.size();
         const long long* of = g.d_off + size_t(j) * 2 * (n + 1);
-        g.ks.batch[g.variant](g.d_args + size_t(j) * n, of, of + (n + 1), n, g.nf[j], g.ng[j], b->stream);
+        g.ks.batch[g.variant](g.d_args + size_t(j) * n, of, of + (n + 1), n, g.nf[j], g.ng[j], b->stream, b->side);
         b->launches += (g.nf[j] > 0) + (g.ng[j] > 0);
     }
+    cudaEventRecord(b->ev_join, b->side);
+    cudaStreamWaitEvent(b->stream, b->ev_join, 0);
 }
 
 int batch_graph(lbm_batch* b) {
@@ -1067,7 +1113,11 @@ int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream
             b->own_stream = e == cudaSuccess;
         }
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        b->release_streams();
         delete b;
         return fail(LBM_ERR_CUDA, std::string("batch stream: ") + cudaGetErrorString(e));
     }
@@ -1075,7 +1125,7 @@ int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream
     for (lbm_ctx* c : b->cases) cudaStreamSynchronize(c->stream);
     if (int r = batch_tables(b)) {
         b->free_tables();
-        if (b->own_stream) cudaStreamDestroy(b->stream);
+        b->release_streams();
         delete b;
         return r;
     }
@@ -1087,7 +1137,7 @@ int lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     cudaSetDevice(b->device);
     b->free_tables();
-    if (b->own_stream) cudaStreamDestroy(b->stream);
+    b->release_streams();
     delete b;
     return LBM_OK;
 }

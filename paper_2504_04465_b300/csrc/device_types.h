@@ -44,6 +44,7 @@ struct ModelDev {
     double sensor_A;
     double newton_tol;
     int newton_max_iter;
+    int newton_fp32;         // Newton arithmetic in FP32
     int guess;
     FaceDev faces[6];
     const float* mlp;        // Newton-guess network (bf16-rounded weights), guess == 3

@@ -95,6 +95,19 @@ struct D2Q21M {
         } else if (m.guess == 3) {
             mlp_guess21(m, (double)ux, (double)uy, (double)Tt, lam);
         }
+        if (m.newton_fp32) {
+            // single-precision solve (FP32 pipe); the multipliers stay FP64 between steps
+            float lf[8], ef[21];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) lf[a] = (float)lam[a];
+            *iters = newton_solve<21, float>((float)ux, (float)uy, (float)Tt, lf, ef, (float)m.newton_tol,
+                                             m.newton_max_iter, conv);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) lam[a] = (double)lf[a];
+#pragma unroll
+            for (int q = 0; q < 21; ++q) f[q] = T((float)rho * ef[q]);
+            return;
+        }
         double e[21];
         *iters = newton_solve<21>((double)ux, (double)uy, (double)Tt, lam, e, m.newton_tol, m.newton_max_iter, conv);
 #pragma unroll

@@ -8,18 +8,21 @@
 namespace lbm {
 
 struct KernelSet {
-    void (*step)(const StepArgs&, long long n_fast, long long n_gen, cudaStream_t) = nullptr;
+    // interior-kernel launch on s_fast, general-kernel launch on s_gen (they touch disjoint cells
+    // and may run concurrently)
+    void (*step)(const StepArgs&, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) = nullptr;
     void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
     void (*ledger)(const StepArgs&, long long nblocks, double* partial, double* out, cudaStream_t) = nullptr;
     void (*init)(const StepArgs&, int lev, const double* rho, const double* u, const double* T, cudaStream_t) = nullptr;
     const void* step_kernel = nullptr;
     int block_threads = 0;
     // compiled variants of the step launch (occupancy targets of the simple-block kernel)
-    void (*variant[4])(const StepArgs&, long long, long long, cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
+    void (*variant[4])(const StepArgs&, long long, long long, cudaStream_t, cudaStream_t) = {nullptr, nullptr, nullptr,
+                                                                                            nullptr};
     int variant_minb[4] = {0, 0, 0, 0};
     int n_variants = 1;
     // batched launches of several cases (per variant; null where the lattice has none)
-    void (*batch[4])(const StepArgs*, const long long*, const long long*, int, long long, long long,
+    void (*batch[4])(const StepArgs*, const long long*, const long long*, int, long long, long long, cudaStream_t,
                      cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
 };
 

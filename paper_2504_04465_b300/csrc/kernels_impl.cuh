@@ -102,7 +102,8 @@ __device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c,
 //           equilibrium of (rho_bc or the partner's rho, u_bc, T_bc)
 template <class M, int ST, int BX, int BY, int BZ, int MODE>
 __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b, int l, int type, bool simple,
-                                         const int* nbr_s, Cell<M, ST>& c, int* conv_out) {
+                                         const int* nbr_s, Cell<M, ST>& c, int* conv_out,
+                                         const typename Store<ST>::T* coal_pre = nullptr) {
     using T = typename Store<ST>::T;
     constexpr int BS = BX * BY * BZ;
     const LevelDev& L = a.lv[lev];
@@ -131,27 +132,55 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
             T gv = T(0);
             if (bmask & (1ull << q)) {
                 load_pop<M, ST, BX * BY * BZ>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
-            } else if (coal && (umask & (1ull << q))) {
-                const LevelDev& F = a.lv[lev - 1];
-                const int rdf = a.rd[lev - 1];
-                constexpr int NK = (M::D == 3) ? 8 : 4;
-                T sf = 0, sg = 0;
-#pragma unroll 1
-                for (int k = 0; k < NK; ++k) {
-                    const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
-                    const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, M::cx(q), M::cy(q), M::cz(q));
-                    T vf, vg;
-                    load_pop<M, ST, BX * BY * BZ>(F, rdf, s, q, a.m, vf, vg);
-                    sf += vf;
-                    sg += vg;
-                }
-                c.f[q] = sf / T(NK);
-                gv = sg / T(NK);
-            } else {
+            } else if (!(coal && (umask & (1ull << q)))) {
                 const long long s = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(q), M::cy(q), M::cz(q));
                 load_pop<M, ST, BX * BY * BZ>(L, rd, s, q, a.m, c.f[q], gv);
             }
             if constexpr (M::HAS_G) c.g[q] = gv;
+        }
+        if (coal && coal_pre) {
+            // coalesced values computed by the whole block beforehand ([q][cell] in shared memory)
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q)
+                if (umask & (1ull << q)) c.f[q] = coal_pre[q * BS + l];
+        } else if (coal) {
+            // coalescence: one population at a time (set bits of the unknown mask), its 2^D
+            // children's streamed values loaded together and summed in child order
+            const LevelDev& F = a.lv[lev - 1];
+            const int rdf = a.rd[lev - 1];
+            constexpr int NK = (M::D == 3) ? 8 : 4;
+            unsigned long long um = umask;
+#pragma unroll 1
+            while (um) {
+                const int q = __ffsll((long long)um) - 1;
+                um &= um - 1;
+                int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+                for (int qq = 0; qq < M::Q; ++qq)
+                    if (qq == q) { cx = M::cx(qq); cy = M::cy(qq); cz = M::cz(qq); }
+                T vf[NK], vg[NK];
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
+                    const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz);
+                    load_pop<M, ST, BX * BY * BZ>(F, rdf, s, q, a.m, vf[k], vg[k]);
+                }
+                T sf = 0, sg = 0;
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    sf += vf[k];
+                    sg += vg[k];
+                }
+                sf = sf / T(NK);
+                sg = sg / T(NK);
+#pragma unroll
+                for (int qq = 0; qq < M::Q; ++qq) {
+                    if (qq == q) {
+                        c.f[qq] = sf;
+                        if constexpr (M::HAS_G) c.g[qq] = sg;
+                    }
+                }
+            }
         }
         if constexpr (M::HAS_LAM) {
             if (coal) {
@@ -264,12 +293,100 @@ __device__ __forceinline__ int find_level_list(const StepArgs& a, int list, long
     return a.active[k];
 }
 
+// Coalescence (Eq. coalescence) of every unknown population of every coarse ghost of the
+// block, shared out over all the block's threads: the (ghost, population) pairs are numbered by
+// a block prefix sum and thread t takes pairs t, t + BS, ...; each pair's 2^D children are
+// loaded together and summed in child order.  Result: out[q * BS + cell].
+template <class M, int ST, int BX, int BY, int BZ>
+__device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l, unsigned long long umask,
+                                               long long child, typename Store<ST>::T* out, int* s_cnt,
+                                               unsigned long long* s_um, int* s_child, int* s_warp) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    constexpr int NW = BS / 32;
+    constexpr int NK = (M::D == 3) ? 8 : 4;
+    s_um[l] = umask;
+    s_child[l] = (int)child;
+    // block exclusive prefix sum of the pair counts
+    const int n = __popcll(umask);
+    const int lane = l & 31, w = l >> 5;
+    int x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int base = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+        if (j < w) base += s_warp[j];
+    s_cnt[l] = base + x - n;
+    if (l == BS - 1) s_cnt[BS] = base + x;
+    __syncthreads();
+    const int P = s_cnt[BS];
+    if (P == 0) return;
+    const LevelDev& F = a.lv[lev - 1];
+    const int rdf = a.rd[lev - 1];
+#pragma unroll 1
+    for (int p = l; p < P; p += BS) {
+        int lo = 0, hi = BS;                    // owner: the largest o with s_cnt[o] <= p
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_cnt[mid] <= p) lo = mid;
+            else hi = mid;
+        }
+        unsigned long long m = s_um[lo];
+        for (int r = p - s_cnt[lo]; r > 0; --r) m &= m - 1;
+        const int q = __ffsll((long long)m) - 1;
+        int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+        for (int qq = 0; qq < M::Q; ++qq)
+            if (qq == q) { cx = M::cx(qq); cy = M::cy(qq); cz = M::cz(qq); }
+        const long long ch0 = s_child[lo];
+        T v[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) {
+            const long long ch = ch0 + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
+            const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz);
+            T vg;
+            load_pop<M, ST, BS>(F, rdf, s, q, a.m, v[kk], vg);
+        }
+        T sf = 0;
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) sf += v[kk];
+        out[q * BS + lo] = sf / T(NK);
+    }
+}
+
+// Staging of a block's coarse-ghost post-collision states for the cooperative explosion:
+// populations [q][cell], the finer level's block under each octant of the block (-1: none)
+// and a coarse-ghost flag per cell.  Empty where the explosion is written per cell.
+template <class T, int Q, int BS, bool ON>
+struct ExplodeStage {
+    T f[Q * BS];
+    int fb[8];
+    unsigned char cg[BS];
+};
+template <class T, int Q, int BS>
+struct ExplodeStage<T, Q, BS, false> {};
+template <class T, int Q, int BS>
+__device__ __forceinline__ const T* stage_ptr(const ExplodeStage<T, Q, BS, true>& s) { return s.f; }
+template <class T, int Q, int BS>
+__device__ __forceinline__ const T* stage_ptr(const ExplodeStage<T, Q, BS, false>&) { return nullptr; }
+
 // One block of cells of the iteration described by a (bid: the block's index in the
 // iteration's FAST or general list, over all active levels).
 template <class M, int ST, int BX, int BY, int BZ, bool FAST>
 __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int* nbr_s, unsigned long long* s_nstat) {
     using T = typename Store<ST>::T;
     constexpr int BS = BX * BY * BZ;
+    // single-distribution models explode through shared memory: each coarse ghost's 2^D
+    // children are written by the threads that own those slots of the finer blocks, in whole
+    // rows, instead of 2^D scattered stores per population from the ghost's own thread
+    constexpr bool COOP = !FAST && !M::HAS_G;
+    __shared__ ExplodeStage<T, M::Q, BS, COOP> sx;
     long long i;
     const int lev = find_level_list(a, FAST ? 0 : 1, bid, &i);
     const LevelDev& L = a.lv[lev];
@@ -285,11 +402,28 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         nbr_s[l] = (FAST && v < 0) ? (int)L.nb : v;
     }
     if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
+    if constexpr (COOP) {
+        if (l < 8) sx.fb[l] = -1;
+        sx.cg[l] = 0;
+    }
     __syncthreads();
     const long long cell = b * BS + l;
     const int rd = a.rd[lev], wr = rd ^ 1;
     const int type = (FAST && !streaming) ? (int)C_FLUID : (int)L.type[cell];
     const bool work = !(type == C_ABSENT || type == C_SOLID || (type == C_FGHOST && a.sync_fg[lev]));
+    if constexpr (COOP) {
+        __shared__ int s_cnt[BS + 1], s_child[BS], s_warp[BS / 32];
+        __shared__ unsigned long long s_um[BS];
+        unsigned long long um = 0ull;
+        long long child = 0;
+        if (type == C_CGHOST) {
+            const CellRecDev rec = L.recs[L.rec_id[cell]];
+            um = rec.mask;
+            child = rec.a;
+        }
+        coalesce_block<M, ST, BX, BY, BZ>(a, lev, l, um, child, sx.f, s_cnt, s_um, s_child, s_warp);
+        __syncthreads();
+    }
     int iters = -1;
     if (work) {
         Cell<M, ST> c;
@@ -316,7 +450,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
                 for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + cell];
             }
         } else if constexpr (!FAST) {
-            assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv);
+            assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv, stage_ptr(sx));
         }
         if (type != C_FGHOST) {
             const int it = collide<M, ST>(a.m, L.tau, c, &conv2);
@@ -330,7 +464,16 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
 #pragma unroll
             for (int j = 0; j < 8; ++j) L.lam[((long long)wr * 8 + j) * L.ncell + cell] = c.lam[j];
         }
-        if constexpr (!FAST) {
+        if constexpr (COOP) {
+            if (type == C_CGHOST) {
+                const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+#pragma unroll
+                for (int q = 0; q < M::Q; ++q) sx.f[q * BS + l] = c.f[q];
+                sx.cg[l] = 1;
+                const long long child = L.recs[L.rec_id[cell]].a;
+                sx.fb[(2 * lx) / BX + 2 * ((2 * ly) / BY) + 4 * ((2 * lz) / BZ)] = (int)(child / BS);
+            }
+        } else if constexpr (!FAST) {
             if (type == C_CGHOST) {
                 // uniform explosion (Eq. explosion_uniform) into every child's slot of the buffer
                 // the finer level writes at this iteration
@@ -348,6 +491,30 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
                         for (int j = 0; j < 8; ++j) F.lam[((long long)wrf * 8 + j) * F.ncell + ch] = c.lam[j];
                     }
                 }
+            }
+        }
+    }
+    if constexpr (COOP) {
+        // uniform explosion (Eq. explosion_uniform): every child of every coarse ghost of this
+        // block receives the ghost's post-collision populations in the buffer the finer level
+        // writes at this iteration
+        if (__syncthreads_or(work && type == C_CGHOST)) {
+            const LevelDev& F = a.lv[lev - 1];
+            const int wrf = a.rd[lev - 1] ^ 1;
+            const int fx = l % BX, fy = (l / BX) % BY, fz = l / (BX * BY);
+            constexpr int NOCT = (M::D == 3) ? 8 : 4;
+#pragma unroll 1
+            for (int oct = 0; oct < NOCT; ++oct) {
+                const int fb = sx.fb[oct];
+                if (fb < 0) continue;
+                const int px = ((oct & 1) * BX + fx) >> 1;
+                const int py = (((oct >> 1) & 1) * BY + fy) >> 1;
+                const int pz = (((oct >> 2) & 1) * BZ + fz) >> 1;
+                const int p = (pz * BY + py) * BX + px;
+                if (!sx.cg[p]) continue;
+                const long long ch = (long long)fb * BS + l;
+#pragma unroll
+                for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BS>(F, wrf, ch, q, a.m, sx.f[q * BS + p], T(0));
             }
         }
     }
@@ -629,15 +796,16 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
 template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
     template <int MINB_F, int MINB_G>
-    static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s) {
-        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(a);
-        if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(a);
+    static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) {
+        // the few, latency-bound general blocks first, so that they start beside the interior sweep
+        if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s_gen>>>(a);
+        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(a);
     }
     template <int MINB_F, int MINB_G>
     static void batch(const StepArgs* args, const long long* off_fast, const long long* off_gen, int n,
-                      long long n_fast, long long n_gen, cudaStream_t s) {
-        if (n_fast) k_step_batch<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s>>>(args, off_fast, n);
-        if (n_gen) k_step_batch<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s>>>(args, off_gen, n);
+                      long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) {
+        if (n_gen) k_step_batch<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s_gen>>>(args, off_gen, n);
+        if (n_fast) k_step_batch<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(args, off_fast, n);
     }
     static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
         if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);

@@ -6,8 +6,8 @@
 // below 0.01), BGK on f and g with the same tau.  The thermal expansion about theta adds, for
 // every set of disjoint index pairs, a factor (T - theta) delta per pair.  Numerical equilibrium:
 // Eq. exponential with the 8 constraints G0..G3yaa, solved with rho = 1 by Newton-Raphson in
-// FP64 (step d = (sum e M M^T)^-1 G by Cholesky, backtracking halving of the step until ||G||_2
-// decreases, at most 30 halvings, stop when max |G| < tol).
+// FP64, or FP32 when selected (step d = (sum e M M^T)^-1 G by Cholesky, backtracking halving of
+// the step until ||G||_2 decreases, at most 30 halvings, stop when max |G| < tol).
 #pragma once
 #include "device_common.cuh"
 
@@ -55,69 +55,71 @@ template <int Q> struct MB {
     }
 };
 
-template <int Q>
-__device__ __forceinline__ void newton_eval(const double* lam, const double* tgt, double* e, double* G) {
+// R: the arithmetic of the solve (double, or float for the single-precision variant)
+template <int Q, typename R = double>
+__device__ __forceinline__ void newton_eval(const R* lam, const R* tgt, R* e, R* G) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) G[a] = -tgt[a];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        double s = 1.0;
+        R s = R(1);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) s += lam[a] * MB<Q>::m(q, a);
+        for (int a = 0; a < 8; ++a) s += lam[a] * R(MB<Q>::m(q, a));
         e[q] = exp(-s);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) G[a] += e[q] * MB<Q>::m(q, a);
+        for (int a = 0; a < 8; ++a) G[a] += e[q] * R(MB<Q>::m(q, a));
     }
 }
 
 // Cholesky solve of the packed SPD system A d = G (A lower triangle, row-major packed)
-__device__ __forceinline__ void chol8_solve(double* A, const double* G, double* d) {
+template <typename R = double>
+__device__ __forceinline__ void chol8_solve(R* A, const R* G, R* d) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        double s = A[j * (j + 1) / 2 + j];
+        R s = A[j * (j + 1) / 2 + j];
 #pragma unroll
         for (int k = 0; k < j; ++k) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-        const double djj = sqrt(s);
+        const R djj = sqrt(s);
         A[j * (j + 1) / 2 + j] = djj;
 #pragma unroll
         for (int i = j + 1; i < 8; ++i) {
-            double t = A[i * (i + 1) / 2 + j];
+            R t = A[i * (i + 1) / 2 + j];
 #pragma unroll
             for (int k = 0; k < j; ++k) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
             A[i * (i + 1) / 2 + j] = t / djj;
         }
     }
-    double y[8];
+    R y[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        double t = G[i];
+        R t = G[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * y[k];
         y[i] = t / A[i * (i + 1) / 2 + i];
     }
 #pragma unroll
     for (int i = 7; i >= 0; --i) {
-        double t = y[i];
+        R t = y[i];
 #pragma unroll
         for (int k = i + 1; k < 8; ++k) t -= A[k * (k + 1) / 2 + i] * d[k];
         d[i] = t / A[i * (i + 1) / 2 + i];
     }
 }
 
-template <int Q>
-__device__ __forceinline__ void newton_dir(const double* e, const double* G, double* d) {
-    double A[36];
+template <int Q, typename R = double>
+__device__ __forceinline__ void newton_dir(const R* e, const R* G, R* d) {
+    R A[36];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) A[k] = 0.0;
+    for (int k = 0; k < 36; ++k) A[k] = R(0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         int k = 0;
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
-            for (int b = 0; b <= a; ++b) A[k++] += e[q] * (MB<Q>::m(q, a) * MB<Q>::m(q, b));
+            for (int b = 0; b <= a; ++b) A[k++] += e[q] * R(MB<Q>::m(q, a) * MB<Q>::m(q, b));
     }
-    chol8_solve(A, G, d);
+    chol8_solve<R>(A, G, d);
 }
 
 // Solve for lambda (in/out) at (u, T); e[] receives exp(-(1 + lambda.M)) (rho = 1).
@@ -125,17 +127,16 @@ __device__ __forceinline__ void newton_dir(const double* e, const double* G, dou
 // A cell stops unconverged at its last finite iterate when the Jacobian's Cholesky
 // factorisation meets a non-positive pivot (non-finite direction) or the line search ends on a
 // non-finite trial.
-template <int Q>
-__device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double* lam, double* e, double tol,
-                                         int max_iter, int* conv) {
-    const double u2 = ux * ux + uy * uy, t2 = u2 + 4.0 * Tt;
-    const double tgt[8] = {1.0, ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
-    double G[8];
-    newton_eval<Q>(lam, tgt, e, G);
+template <int Q, typename R = double>
+__device__ __noinline__ int newton_solve(R ux, R uy, R Tt, R* lam, R* e, R tol, int max_iter, int* conv) {
+    const R u2 = ux * ux + uy * uy, t2 = u2 + R(4) * Tt;
+    const R tgt[8] = {R(1), ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
+    R G[8];
+    newton_eval<Q, R>(lam, tgt, e, G);
     *conv = 0;
     int it = 0;
     for (;; ++it) {
-        double gmax = 0.0;
+        R gmax = R(0);
         bool fin = true;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -144,31 +145,31 @@ __device__ __noinline__ int newton_solve(double ux, double uy, double Tt, double
         }
         if (fin && gmax < tol) { *conv = 1; break; }
         if (!fin || it == max_iter) break;
-        double d[8];
-        newton_dir<Q>(e, G, d);
+        R d[8];
+        newton_dir<Q, R>(e, G, d);
         bool dfin = true;
 #pragma unroll
         for (int a = 0; a < 8; ++a) dfin = dfin && isfinite(d[a]);
         if (!dfin) break;
-        double g0 = 0.0;
+        R g0 = R(0);
 #pragma unroll
         for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
-        double t = 1.0;
-        double trial[8], Gt[8];
+        R t = R(1);
+        R trial[8], Gt[8];
         bool take = false;
 #pragma unroll 1
         for (int h = 0; h <= 30; ++h) {
 #pragma unroll
             for (int a = 0; a < 8; ++a) trial[a] = lam[a] + t * d[a];
-            newton_eval<Q>(trial, tgt, e, Gt);
-            double g1 = 0.0;
+            newton_eval<Q, R>(trial, tgt, e, Gt);
+            R g1 = R(0);
 #pragma unroll
             for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
             if (g1 < g0 || (h == 30 && isfinite(g1))) { take = true; break; }
-            t *= 0.5;
+            t *= R(0.5);
         }
         if (!take) {                        // keep the current iterate (restore its e)
-            newton_eval<Q>(lam, tgt, e, G);
+            newton_eval<Q, R>(lam, tgt, e, G);
             break;
         }
 #pragma unroll

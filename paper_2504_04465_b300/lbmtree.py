@@ -35,7 +35,7 @@ CELL_FLUID, CELL_CGHOST, CELL_FGHOST, CELL_BC, CELL_SOLID = 1, 2, 3, 4, 5
 class CollisionParams(C.Structure):
     _fields_ = [("nu0", C.c_double), ("T0", C.c_double), ("gamma", C.c_double), ("sensor_on", C.c_int),
                 ("sensor_A", C.c_double), ("newton_tol", C.c_double), ("newton_max_iter", C.c_int),
-                ("guess", C.c_int), ("rho_ref", C.c_double)]
+                ("guess", C.c_int), ("rho_ref", C.c_double), ("newton_fp32", C.c_int)]
 
 
 class Box(C.Structure):
@@ -213,10 +213,10 @@ class Context:
         _check(_lib.lbm_set_lattice(self._h, LATTICE[name]), "lbm_set_lattice")
 
     def set_collision(self, model: str, nu0: float = 0.0, T0: float = 0.0, gamma: float = 1.4,
-                      sensor_A: float | None = None, newton_tol: float = 1e-12, newton_max_iter: int = 50,
-                      guess: str = "warm", rho_ref: float = 1.0) -> None:
+                      sensor_A: float | None = None, newton_tol: float = 0.0, newton_max_iter: int = 50,
+                      guess: str = "warm", rho_ref: float = 1.0, newton_fp32: bool = False) -> None:
         p = CollisionParams(nu0, T0, gamma, int(sensor_A is not None), sensor_A or 0.0, newton_tol,
-                            newton_max_iter, GUESS[guess], rho_ref)
+                            newton_max_iter, GUESS[guess], rho_ref, int(newton_fp32))
         _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
 
     def set_guess(self, guess: str) -> None:
