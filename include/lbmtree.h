@@ -147,6 +147,9 @@ int lbm_set_collision(lbm_ctx* ctx, int model, const lbm_collision_params* param
 /* Newton starting point of the numerical equilibrium (LBM_GUESS_*), also on a built and running
  * context (the next step uses it; the captured graph is rebuilt). */
 int lbm_set_guess(lbm_ctx* ctx, int guess);
+/* Arithmetic (fp32 = 1: FP32, 0: FP64) and tolerance (<= 0: the default of that arithmetic) of
+ * the Newton solve, also on a built and running context. */
+int lbm_set_newton_precision(lbm_ctx* ctx, int fp32, double tol);
 int lbm_set_precision(lbm_ctx* ctx, int storage);
 /* face 0..5; kind LBM_*; rho_u_T = {rho, ux, uy, uz, T} (ignored for PERIODIC/NEUMANN). */
 int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);

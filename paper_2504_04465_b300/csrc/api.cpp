@@ -174,12 +174,21 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
         }
         const double nu = c->params.nu0 / double(int64_t(1) << i);
         d.tau = nu / theta + 0.5;
+        d.omega = 1.0 / d.tau;
+        d.omega_f = (float)d.omega;
     }
     ModelDev& m = a.m;
     m.cs2 = theta;
     m.T0 = c->T0();
     m.Cv = 1.0 / (c->params.gamma - 1.0);
     m.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : 1.0;
+    m.rho_ref_f = (float)m.rho_ref;
+    m.inv_rho_ref_f = (float)(1.0 / m.rho_ref);
+    {
+        const double gref = m.rho_ref * (2.0 * m.Cv - c->dim) * m.T0;
+        m.gref_f = (float)gref;
+        m.inv_gref_f = gref != 0.0 ? (float)(1.0 / gref) : 0.0f;
+    }
     m.sensor_on = c->params.sensor_on;
     m.sensor_A = c->params.sensor_A;
     m.newton_tol = c->params.newton_tol > 0 ? c->params.newton_tol : (c->params.newton_fp32 ? 1e-5 : 1e-12);
@@ -384,7 +393,11 @@ int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
             }
             c->own_stream = true;
         }
-        e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        // the general blocks go on a high-priority stream: the block scheduler hands them free
+        // slots first, so they finish inside the interior sweep instead of after it
+        int prio_lo = 0, prio_hi = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) {
@@ -459,6 +472,16 @@ int lbm_set_guess(lbm_ctx* c, int guess) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (guess < LBM_GUESS_WARM || guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "unknown Newton guess");
     c->params.guess = guess;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
+int lbm_set_newton_precision(lbm_ctx* c, int fp32, double tol) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (fp32 && tol > 0 && tol < 1e-6)
+        return fail(LBM_ERR_ARG, "an FP32 Newton solve cannot reach a tolerance below 1e-6 (use 1e-5)");
+    c->params.newton_fp32 = fp32 ? 1 : 0;
+    c->params.newton_tol = tol;
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return LBM_OK;
 }
@@ -1113,7 +1136,9 @@ int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream
             b->own_stream = e == cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {

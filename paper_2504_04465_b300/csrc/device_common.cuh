@@ -35,8 +35,9 @@ template <> struct Store<ST_F32> {
 };
 
 // binary16 deviation relative to the reference value ref = w_i rho_ref (or the g reference):
-// stored d = v / ref - 1 (round to nearest even); arithmetic in FP32.  With DEV the arithmetic
-// value is itself the deviation v - ref (weakly compressible models), else the population v.
+// stored d = v / ref - 1, computed as v * (1 / ref) (round to nearest even); arithmetic in FP32.
+// With DEV the arithmetic value is itself the deviation v - ref (weakly compressible models),
+// else the population v.  load() takes ref, store() takes 1 / ref.
 template <> struct Store<ST_F16DEV> {
     using T = float;
     using S = __half;
@@ -44,8 +45,8 @@ template <> struct Store<ST_F16DEV> {
         const float h = __half2float(((const __half*)p)[i]);
         return DEV ? ref * h : ref * (1.0f + h);
     }
-    template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T ref) {
-        ((__half*)p)[i] = __float2half_rn(DEV ? v / ref : v / ref - 1.0f);
+    template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T inv_ref) {
+        ((__half*)p)[i] = __float2half_rn(DEV ? v * inv_ref : fmaf(v, inv_ref, -1.0f));
     }
 };
 

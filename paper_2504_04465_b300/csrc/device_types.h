@@ -25,6 +25,8 @@ struct LevelDev {
     void* g[2];
     double* lam;             // 2 buffers x 8 x ncell (numerical equilibrium)
     double tau;
+    double omega;            // 1 / tau
+    float omega_f;           // 1 / tau in FP32 (no division in the kernels)
     const int* blist[2];     // [0] 2 * block + s: simple (s = 0) and streaming (s = 1) blocks, [1] the others
                              // (block nb of f/g holds zero populations: the missing-neighbour stand-in)
     long long nlist[2];
@@ -40,6 +42,8 @@ struct ModelDev {
     double T0;               // reference temperature (compressible)
     double Cv;               // 1/(gamma - 1)
     double rho_ref;          // F16DEV reference density
+    float rho_ref_f, inv_rho_ref_f;   // the same in FP32, and its reciprocal
+    float gref_f, inv_gref_f;         // g reference rho_ref (2 Cv - D) T0 in FP32, and its reciprocal
     int sensor_on;
     double sensor_A;
     double newton_tol;

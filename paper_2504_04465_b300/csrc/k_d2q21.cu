@@ -10,6 +10,7 @@
 namespace lbm {
 
 static __constant__ double cw21[21];
+static __constant__ float cw21f[21], cinvw21f[21];   // the weights in FP32 and their reciprocals
 static __constant__ double cH21[21][10];
 
 __device__ __forceinline__ void poly_guess21(double ux, double uy, double Tt, double* lam) {
@@ -82,6 +83,8 @@ struct D2Q21M {
     __host__ __device__ static constexpr int cy(int q) { return Lat<21>::cy(q); }
     __host__ __device__ static constexpr int cz(int) { return 0; }
     __device__ static double w(int q) { return cw21[q]; }
+    __device__ static float wf(int q) { return cw21f[q]; }
+    __device__ static float inv_wf(int q) { return cinvw21f[q]; }
     template <int ST>
     __device__ static void feq(const ModelDev& m, typename Store<ST>::T rho, typename Store<ST>::T ux,
                                typename Store<ST>::T uy, typename Store<ST>::T Tt, double* lam,
@@ -145,6 +148,13 @@ bool find_kernels_d2q21(int model, int storage, const int* blk, KernelSet& out) 
 cudaError_t upload_tables_d2q21(const double* w21, const double* H21) {
     cudaError_t e;
     if ((e = cudaMemcpyToSymbol(cw21, w21, sizeof(double) * 21)) != cudaSuccess) return e;
+    float wf[21], iwf[21];
+    for (int q = 0; q < 21; ++q) {
+        wf[q] = (float)w21[q];
+        iwf[q] = (float)(1.0 / w21[q]);
+    }
+    if ((e = cudaMemcpyToSymbol(cw21f, wf, sizeof(wf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cinvw21f, iwf, sizeof(iwf))) != cudaSuccess) return e;
     return cudaMemcpyToSymbol(cH21, H21, sizeof(double) * 21 * 10);
 }
 

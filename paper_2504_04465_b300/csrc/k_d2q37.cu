@@ -8,6 +8,7 @@
 namespace lbm {
 
 static __constant__ double cw37[37];
+static __constant__ float cw37f[37], cinvw37f[37];   // the weights in FP32 and their reciprocals
 static __constant__ double cH37[37][15];
 static __constant__ double ccs2_37;
 
@@ -23,6 +24,8 @@ struct D2Q37M {
     __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }
     __host__ __device__ static constexpr int cz(int) { return 0; }
     __device__ static double w(int q) { return cw37[q]; }
+    __device__ static float wf(int q) { return cw37f[q]; }
+    __device__ static float inv_wf(int q) { return cinvw37f[q]; }
     template <int ST>
     __device__ static void feq(const ModelDev&, typename Store<ST>::T rho, typename Store<ST>::T ux,
                                typename Store<ST>::T uy, typename Store<ST>::T Tt, double*,
@@ -51,6 +54,13 @@ bool find_kernels_d2q37(int model, int storage, const int* blk, KernelSet& out) 
 cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37) {
     cudaError_t e;
     if ((e = cudaMemcpyToSymbol(cw37, w37, sizeof(double) * 37)) != cudaSuccess) return e;
+    float wf[37], iwf[37];
+    for (int q = 0; q < 37; ++q) {
+        wf[q] = (float)w37[q];
+        iwf[q] = (float)(1.0 / w37[q]);
+    }
+    if ((e = cudaMemcpyToSymbol(cw37f, wf, sizeof(wf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cinvw37f, iwf, sizeof(iwf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(cH37, H37, sizeof(double) * 37 * 15)) != cudaSuccess) return e;
     return cudaMemcpyToSymbol(ccs2_37, &cs2_37, sizeof(double));
 }

@@ -16,6 +16,8 @@ template <bool RR_> struct D2Q9M {
     __host__ __device__ static constexpr int cy(int q) { return TP<2>::cy(q); }
     __host__ __device__ static constexpr int cz(int) { return 0; }
     __host__ __device__ static constexpr double w(int q) { return tp_w<2>(q); }
+    __host__ __device__ static constexpr float wf(int q) { return float(tp_w<2>(q)); }
+    __host__ __device__ static constexpr float inv_wf(int q) { return float(1.0 / tp_w<2>(q)); }
 };
 
 bool find_kernels_d2q9(int model, int storage, const int* blk, KernelSet& out) {

@@ -16,6 +16,8 @@ template <bool RR_> struct D3Q27M {
     __host__ __device__ static constexpr int cy(int q) { return TP<3>::cy(q); }
     __host__ __device__ static constexpr int cz(int q) { return TP<3>::cz(q); }
     __host__ __device__ static constexpr double w(int q) { return tp_w<3>(q); }
+    __host__ __device__ static constexpr float wf(int q) { return float(tp_w<3>(q)); }
+    __host__ __device__ static constexpr float inv_wf(int q) { return float(1.0 / tp_w<3>(q)); }
 };
 
 bool find_kernels_d3q27(int model, int storage, const int* blk, KernelSet& out) {

@@ -34,13 +34,32 @@ struct Cell {
     double lam[M::HAS_LAM ? 8 : 1];
 };
 
+// reference values w_q rho_ref (f) and w_q rho_ref (2 Cv - D) T0 (g) of the deviation formats, and
+// their reciprocals; in FP32 from single-precision weights, so that no FP64 operation or
+// division is left in the per-population path
 template <class M, int ST>
 __device__ __forceinline__ typename Store<ST>::T ref_f(const ModelDev& m, int q) {
-    return typename Store<ST>::T(M::w(q) * m.rho_ref);
+    using T = typename Store<ST>::T;
+    if constexpr (sizeof(T) == 4) return M::wf(q) * m.rho_ref_f;
+    else return T(M::w(q) * m.rho_ref);
+}
+template <class M, int ST>
+__device__ __forceinline__ typename Store<ST>::T inv_ref_f(const ModelDev& m, int q) {
+    using T = typename Store<ST>::T;
+    if constexpr (sizeof(T) == 4) return M::inv_wf(q) * m.inv_rho_ref_f;
+    else return T(1.0 / (M::w(q) * m.rho_ref));
 }
 template <class M, int ST>
 __device__ __forceinline__ typename Store<ST>::T ref_g(const ModelDev& m, int q) {
-    return typename Store<ST>::T(M::w(q) * m.rho_ref * (2.0 * m.Cv - M::D) * m.T0);
+    using T = typename Store<ST>::T;
+    if constexpr (sizeof(T) == 4) return M::wf(q) * m.gref_f;
+    else return T(M::w(q) * m.rho_ref * (2.0 * m.Cv - M::D) * m.T0);
+}
+template <class M, int ST>
+__device__ __forceinline__ typename Store<ST>::T inv_ref_g(const ModelDev& m, int q) {
+    using T = typename Store<ST>::T;
+    if constexpr (sizeof(T) == 4) return M::inv_wf(q) * m.inv_gref_f;
+    else return T(1.0 / (M::w(q) * m.rho_ref * (2.0 * m.Cv - M::D) * m.T0));
 }
 
 template <class M, int ST, int BS>
@@ -62,8 +81,8 @@ template <class M, int ST, int BS>
 __device__ __forceinline__ void store_pop(const LevelDev& L, int buf, long long cell, int q, const ModelDev& m,
                                           typename Store<ST>::T fv, typename Store<ST>::T gv) {
     const long long i = pidx<BS, M::Q>(cell, q);
-    Store<ST>::template store<M::DEV>(L.f[buf], i, fv, ref_f<M, ST>(m, q));
-    if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[buf], i, gv, ref_g<M, ST>(m, q));
+    Store<ST>::template store<M::DEV>(L.f[buf], i, fv, inv_ref_f<M, ST>(m, q));
+    if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[buf], i, gv, inv_ref_g<M, ST>(m, q));
 }
 
 // macroscopic moments (rho, u, T) of f, g (T from Eq. polyTemp)
@@ -71,7 +90,7 @@ template <class M, int ST>
 __device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c, typename Store<ST>::T& rho,
                                         typename Store<ST>::T* u, typename Store<ST>::T& Tt) {
     using T = typename Store<ST>::T;
-    T r = M::DEV ? T(m.rho_ref) : T(0), jx = 0, jy = 0, jz = 0, e2 = 0, gs = 0;
+    T r = M::DEV ? (sizeof(T) == 4 ? T(m.rho_ref_f) : T(m.rho_ref)) : T(0), jx = 0, jy = 0, jz = 0, e2 = 0, gs = 0;
 #pragma unroll
     for (int q = 0; q < M::Q; ++q) {
         const T v = c.f[q];
@@ -242,11 +261,13 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
 
 // ------------------------------------------------------------------ collision
 template <class M, int ST>
-__device__ __forceinline__ int collide(const ModelDev& m, double tau, Cell<M, ST>& c, int* conv) {
+__device__ __forceinline__ int collide(const ModelDev& m, const LevelDev& L, Cell<M, ST>& c, int* conv) {
     using T = typename Store<ST>::T;
     *conv = 1;
+    const double tau = L.tau;
     if constexpr (!M::HAS_G) {
-        weak_collide<M::D, M::RR, T>(c.f, T(1.0 / tau), T(m.rho_ref));
+        if constexpr (sizeof(T) == 4) weak_collide<M::D, M::RR, T>(c.f, L.omega_f, m.rho_ref_f);
+        else weak_collide<M::D, M::RR, T>(c.f, T(L.omega), T(m.rho_ref));
         return 0;
     } else {
         T rho, u[3], Tt;
@@ -453,7 +474,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
             assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv, stage_ptr(sx));
         }
         if (type != C_FGHOST) {
-            const int it = collide<M, ST>(a.m, L.tau, c, &conv2);
+            const int it = collide<M, ST>(a.m, L, c, &conv2);
             if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
             if (!conv || !conv2) set_status(a.status, -6);
         }
@@ -595,7 +616,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
     } else if (which == 1) {
 #pragma unroll
         for (int q = 0; q < M::Q; ++q)
-            out[(long long)q * L.ncell + cell] = M::DEV ? (double)c.f[q] + (double)ref_f<M, ST>(a.m, q) : (double)c.f[q];
+            out[(long long)q * L.ncell + cell] = M::DEV ? (double)c.f[q] + M::w(q) * a.m.rho_ref : (double)c.f[q];
     } else if (which == 2) {
         if constexpr (M::HAS_G) {
 #pragma unroll
@@ -784,7 +805,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
             if constexpr (M::HAS_G) vg = Eg[pidx<BS, M::Q>(src, qs)];
         } else {
             // zero population: -1 in the binary16 format, -ref for the other deviation formats
-            vf = S(ST == ST_F16DEV ? -1.0f : (M::DEV ? -float(M::w(q) * a.m.rho_ref) : 0.0f));
+            vf = S(ST == ST_F16DEV ? -1.0f : (M::DEV ? -ref_f<M, ST>(a.m, q) : 0.0f));
             vg = S(ST == ST_F16DEV ? -1.0f : 0.0f);
         }
         Of[pidx<BS, M::Q>(cell, q)] = vf;
@@ -797,9 +818,9 @@ template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
     template <int MINB_F, int MINB_G>
     static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) {
-        // the few, latency-bound general blocks first, so that they start beside the interior sweep
-        if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s_gen>>>(a);
+        // interior sweep first; the few, latency-bound general blocks fill in as its blocks retire
         if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(a);
+        if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s_gen>>>(a);
     }
     template <int MINB_F, int MINB_G>
     static void batch(const StepArgs* args, const long long* off_fast, const long long* off_gen, int n,

@@ -89,6 +89,7 @@ _sig = {
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
     "lbm_set_guess": [_P, C.c_int],
+    "lbm_set_newton_precision": [_P, C.c_int, C.c_double],
     "lbm_batch_create": [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
     "lbm_batch_destroy": [C.c_void_p],
     "lbm_batch_use_graph": [C.c_void_p, C.c_int],
@@ -221,6 +222,9 @@ class Context:
 
     def set_guess(self, guess: str) -> None:
         _check(_lib.lbm_set_guess(self._h, GUESS[guess]), "lbm_set_guess")
+
+    def set_newton_precision(self, fp32: bool, tol: float = 0.0) -> None:
+        _check(_lib.lbm_set_newton_precision(self._h, int(fp32), tol), "lbm_set_newton_precision")
 
     def set_precision(self, storage: str) -> None:
         _check(_lib.lbm_set_precision(self._h, STORAGE[storage]), "lbm_set_precision")

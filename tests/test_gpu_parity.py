@@ -209,14 +209,16 @@ def test_d2q21_f32_populations_fp64_newton():
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 def test_d2q21_fp32_newton(storage):
     """Single-precision Newton (tolerance 1e-5, the paper's FP32 threshold) against the FP64
-    oracle: the equilibrium moments differ by the solve's tolerance, so the fields agree to
-    about 1e-5 relative after 20 fine iterations (stated bound 1e-4)."""
+    oracle.  The tolerance bounds the residual of the moment constraints in absolute terms, so
+    the equilibrium's momentum is off by up to ~1e-5 against |u| ~ 0.05 here: after 20 fine
+    iterations rho and T agree to ~1e-5 and u to ~1.2e-4 relative (stated bounds 1e-4, 1e-4,
+    5e-4)."""
     fn = H.smooth_comp_fields((96, 64), 0.9)
     sol = H.run_oracle(N21_SPEC, "D2Q21", "num_ddf", fn, 20, nu0=0.01, T0=0.9, sensor_A=1.35)
     ctx = H.make_gpu(N21_SPEC, "D2Q21", "num_ddf", storage, fn, nu0=0.01, T0=0.9, sensor_A=1.35, newton_fp32=True)
     ctx.step(10)
     err = H.compare_moments(sol, ctx)
     print("d2q21 fp32 newton", storage, err)
-    assert err["rho"] < 1e-4 and err["u"] < 1e-4 and err["T"] < 1e-4, err
+    assert err["rho"] < 1e-4 and err["u"] < 5e-4 and err["T"] < 1e-4, err
     s = ctx.stats()
     assert s.newton_nonconverged == 0
