@@ -480,6 +480,8 @@ def run_ours(args, world, rank, local):
         for name, fn in (("fp16_store", lambda: form_fp16(args, stream, local, t_max / args.steps)),
                          ("learned", lambda: form_learned(args, stream, local)),
                          ("batched", lambda: form_batched(args, stream, local))):
+            if name not in args.forms.split(","):
+                continue
             try:
                 forms[name] = fn()
             except Exception as e:                  # report, keep the main line
@@ -513,6 +515,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
+    ap.add_argument("--forms", default="fp16_store,learned,batched", help="which forms to run (comma list)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block", type=int, nargs=3, default=None)
     ap.add_argument("--variant", type=int, default=None)

@@ -60,12 +60,12 @@ const Constants& constants() {
 std::mutex g_upload_mu;
 bool g_uploaded[256] = {false};
 
-bool find_kernels(int lattice, int model, int storage, const int* blk, KernelSet& out) {
+bool find_kernels(int lattice, int model, int storage, const int* blk, bool newton_fp32, KernelSet& out) {
     switch (lattice) {
         case LBM_D2Q9: return find_kernels_d2q9(model, storage, blk, out);
         case LBM_D3Q27: return find_kernels_d3q27(model, storage, blk, out);
         case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, out);
-        case LBM_D2Q21: return find_kernels_d2q21(model, storage, blk, out);
+        case LBM_D2Q21: return find_kernels_d2q21(model, storage, blk, newton_fp32, out);
     }
     return false;
 }
@@ -482,6 +482,14 @@ int lbm_set_newton_precision(lbm_ctx* c, int fp32, double tol) {
         return fail(LBM_ERR_ARG, "an FP32 Newton solve cannot reach a tolerance below 1e-6 (use 1e-5)");
     c->params.newton_fp32 = fp32 ? 1 : 0;
     c->params.newton_tol = tol;
+    if (c->built) {
+        // the two precisions are separate kernel sets (D2Q21); keep the variant in use
+        KernelSet ks;
+        if (find_kernels(c->lattice, c->model, c->storage, c->block, fp32 != 0, ks)) {
+            ks.step = ks.variant[c->variant < ks.n_variants ? c->variant : 0];
+            c->ks = ks;
+        }
+    }
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return LBM_OK;
 }
@@ -526,7 +534,7 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
         (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
-    if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->ks))
+    if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
     GridInput in;
     in.dim = c->dim;
@@ -590,6 +598,11 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         const BuiltLevel& lv = c->grid.levels[i];
         DevLevel& d = c->dl[i];
         const int64_t ncell = lv.nb * BS;
+        if ((ncell + BS) * int64_t(Q) >= (int64_t(1) << 32)) {
+            c->release();
+            c->built = false;
+            return fail(LBM_ERR_GRID, "level " + std::to_string(i) + " too large for 32-bit population offsets");
+        }
         c->total_blocks += lv.nb;
         d.nbr = (int*)c->dalloc(lv.nbr.size() * 4);
         d.type = (unsigned char*)c->dalloc(lv.type.size());

@@ -30,7 +30,7 @@ struct KernelSet {
 bool find_kernels_d2q9(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d2q37(int model, int storage, const int* block, KernelSet& out);
-bool find_kernels_d2q21(int model, int storage, const int* block, KernelSet& out);
+bool find_kernels_d2q21(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
 
 int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
                      float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);

@@ -314,6 +314,17 @@ __device__ __forceinline__ int find_level_list(const StepArgs& a, int list, long
     return a.active[k];
 }
 
+// Pull-source term of one axis for local coordinate lc and velocity component c: the source
+// lc - c wrapped into the block (neighbour digit o + 1 in {0, 1, 2}, scaled by DIG) and its
+// local offset scaled by STRIDE, packed as (digit << 20) | offset.
+template <int B, int STRIDE, int DIG>
+__device__ __forceinline__ unsigned axis_term(int lc, int c) {
+    int s = lc - c;
+    const int o = s < 0 ? -1 : (s >= B ? 1 : 0);
+    s -= o * B;
+    return ((unsigned)((o + 1) * DIG) << 20) | (unsigned)(s * STRIDE);
+}
+
 // Coalescence (Eq. coalescence) of every unknown population of every coarse ghost of the
 // block, shared out over all the block's threads: the (ghost, population) pairs are numbered by
 // a block prefix sum and thread t takes pairs t, t + BS, ...; each pair's 2^D children are
@@ -418,9 +429,12 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
     const long long b = FAST ? (long long)(entry >> 1) : (long long)entry;
     const bool streaming = FAST && (entry & 1);
     const int l = threadIdx.x;
+    // element offset of each neighbour block's populations (the zero block for a missing one)
+    __shared__ unsigned nboff_s[27];
     if (l < 27) {
         const int v = L.nbr[b * 27 + l];
         nbr_s[l] = (FAST && v < 0) ? (int)L.nb : v;
+        nboff_s[l] = (unsigned)(v < 0 ? L.nb : v) * (unsigned)(M::Q * BS);
     }
     if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
     if constexpr (COOP) {
@@ -455,14 +469,11 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
             const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
 #pragma unroll
             for (int q = 0; q < M::Q; ++q) {
-                int sx = lx - M::cx(q), sy = ly - M::cy(q), sz = lz - M::cz(q);
-                const int ox = sx < 0 ? -1 : (sx >= BX ? 1 : 0);
-                const int oy = sy < 0 ? -1 : (sy >= BY ? 1 : 0);
-                const int oz = sz < 0 ? -1 : (sz >= BZ ? 1 : 0);
-                sx -= ox * BX; sy -= oy * BY; sz -= oz * BZ;
-                const int kk = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
-                const int nb = (kk == 13) ? (int)b : nbr_s[kk];
-                const long long i = (long long)nb * (M::Q * BS) + q * BS + (sz * BY + sy) * BX + sx;
+                // one packed term per axis (neighbour digit << 20 | local offset), summed: the
+                // terms depend on a single velocity component each and are shared between q
+                const unsigned P = axis_term<BX, 1, 1>(lx, M::cx(q)) + axis_term<BY, BX, 3>(ly, M::cy(q)) +
+                                   axis_term<BZ, BX * BY, 9>(lz, M::cz(q));
+                const unsigned i = nboff_s[P >> 20] + (unsigned)(q * BS) + (P & 0xFFFFFu);
                 c.f[q] = Store<ST>::template load<M::DEV>(L.f[rd], i, ref_f<M, ST>(a.m, q));
                 if constexpr (M::HAS_G) c.g[q] = Store<ST>::template load<false>(L.g[rd], i, ref_g<M, ST>(a.m, q));
             }

@@ -178,4 +178,56 @@ __device__ __noinline__ int newton_solve(R ux, R uy, R Tt, R* lam, R* e, R tol, 
     return it;
 }
 
+// the same iteration inlined into the caller (the FP32 kernels keep its arrays in registers)
+template <int Q, typename R = double>
+__device__ __forceinline__ int newton_solve_inl(R ux, R uy, R Tt, R* lam, R* e, R tol, int max_iter, int* conv) {
+    const R u2 = ux * ux + uy * uy, t2 = u2 + R(4) * Tt;
+    const R tgt[8] = {R(1), ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
+    R G[8];
+    newton_eval<Q, R>(lam, tgt, e, G);
+    *conv = 0;
+    int it = 0;
+    for (;; ++it) {
+        R gmax = R(0);
+        bool fin = true;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            fin = fin && isfinite(G[a]);
+            gmax = fmax(gmax, fabs(G[a]));
+        }
+        if (fin && gmax < tol) { *conv = 1; break; }
+        if (!fin || it == max_iter) break;
+        R d[8];
+        newton_dir<Q, R>(e, G, d);
+        bool dfin = true;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) dfin = dfin && isfinite(d[a]);
+        if (!dfin) break;
+        R g0 = R(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
+        R t = R(1);
+        R trial[8], Gt[8];
+        bool take = false;
+#pragma unroll 1
+        for (int h = 0; h <= 30; ++h) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a) trial[a] = lam[a] + t * d[a];
+            newton_eval<Q, R>(trial, tgt, e, Gt);
+            R g1 = R(0);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
+            if (g1 < g0 || (h == 30 && isfinite(g1))) { take = true; break; }
+            t *= R(0.5);
+        }
+        if (!take) {                        // keep the current iterate (restore its e)
+            newton_eval<Q, R>(lam, tgt, e, G);
+            break;
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) { lam[a] = trial[a]; G[a] = Gt[a]; }
+    }
+    return it;
+}
+
 }  // namespace lbm
