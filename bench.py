@@ -329,6 +329,39 @@ def form_learned(args, stream, local):
             "err": "Newton runs to the same tolerance from every guess: results agree within it"}
 
 
+def form_d2q37(args, stream, local):
+    """D2Q37 polynomial-equilibrium DDF with the shock sensor on Sod tubes (inviscid, A = 1.5):
+    the 4096x64 tube uniform and with its middle half refined (2 levels), and a 16384x512 tube
+    for a bandwidth-sized case; FP32 and FP64 populations."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    out = {"workload": "Sod shock tube (rho, p) = (1, 1) | (0.125, 0.1), T = T0 p / rho, T0 = c_s^2 of D2Q37, "
+                       "Neumann ends, periodic across, inviscid with the kinetic sensor (A = 1.5)",
+           "bytes_per_update": {"f32": 592, "f64": 1184}}
+    peak, kind = peaks()
+    cases = {"4096x64": I.sod_spec(4096, 64), "4096x64_band": I.sod_spec(4096, 64, 2, (1024, 3072)),
+             "16384x512": I.sod_spec(16384, 512)}
+    for name, spec in cases.items():
+        for st in ("f32", "f64"):
+            ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
+            ctx.configure(spec, "D2Q37", "poly_ddf", st, nu0=0.0, sensor_A=1.5)
+            ctx.use_graph(True)
+            lv, xyz, _ = ctx.cells()
+            from paper_2504_04465_b300.lbmtree import lattice_cs2
+            T0 = lattice_cs2("D2Q37")
+            rho, u, T = I.sod_fields(I.cell_centres(xyz[:, :2], lv), spec.extent[0], T0)
+            ctx.init_fields(rho, u, T)
+            ctx.step(2)
+            upd = ctx.stats().cell_updates
+            K = 20
+            ms = _event_ms(stream, lambda: ctx.step(K)) / K
+            ctx.sync()
+            bpu = 592 if st == "f32" else 1184
+            out[f"{name}_{st}"] = {"ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS",
+                                   "hbm_frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind}
+            ctx.close()
+    return out
+
+
 def form_batched(args, stream, local):
     """48 uneven 2D cases (D2Q9 Taylor-Green and D2Q37 Sod tubes, 2-4 levels): one batched
     launch per lattice group per fine iteration (CUDA graph of the schedule period) against
@@ -443,21 +476,27 @@ def run_ours(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         n = rho.size
+        # inputs and outputs in pinned host memory
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        h_rho, h_u = pin(n), pin((3, n))
+        h_rho[:] = rho
+        h_u[:] = u
+        o_rho, o_u, o_T = pin(n), pin(3 * n), pin(n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.init_fields(rho, u)
+        ctx.init_fields(h_rho, h_u)
         for _ in range(args.steps):
             ctx.step(1)
             ctx.conserved()
-        m = ctx.moments()
+        ctx.moments(out=(o_rho, o_u, o_T))
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        h2d = (rho.nbytes + u.nbytes) / args.steps
-        d2h = 5 * 8 + sum(a.nbytes for a in m) / args.steps
+        h2d = (h_rho.nbytes + h_u.nbytes) / args.steps
+        d2h = 5 * 8 + (o_rho.nbytes + o_u.nbytes + o_T.nbytes) / args.steps
         e2e = {"value": updates_per_step * args.steps * world / te / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "note": "init_fields from host arrays once, step + conserved() per step, read_moments once; "
-                       "bytes per step are the totals / steps"}
+               "note": "pinned host buffers; init_fields once, step + conserved() (FP64 totals read back) per "
+                       "step, read_moments once; bytes per step are the totals / steps"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -479,7 +518,8 @@ def run_ours(args, world, rank, local):
         forms = {}
         for name, fn in (("fp16_store", lambda: form_fp16(args, stream, local, t_max / args.steps)),
                          ("learned", lambda: form_learned(args, stream, local)),
-                         ("batched", lambda: form_batched(args, stream, local))):
+                         ("batched", lambda: form_batched(args, stream, local)),
+                         ("d2q37_sod", lambda: form_d2q37(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -515,7 +555,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched", help="which forms to run (comma list)")
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod", help="which forms to run (comma list)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block", type=int, nargs=3, default=None)
     ap.add_argument("--variant", type=int, default=None)

@@ -136,6 +136,9 @@ typedef struct {
 /* Create a context bound to `device` and `stream` (cudaStream_t, or NULL for a stream owned by
  * the context).  dim = 2 or 3.
  * device < 0 makes a host-only context: grids can be built and inspected, nothing runs. */
+/* Velocity count, dimension, reach and lattice temperature c_s^2 of a velocity set (LBM_D2Q*,
+ * LBM_D3Q27; D2Q37's c_s^2 is the one the library derives from the isotropy conditions). */
+int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2);
 int lbm_create(lbm_ctx** out, int dim, int device, void* stream);
 /* Release every device and host resource of the context.  NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);

@@ -107,6 +107,7 @@ struct lbm_ctx {
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;
     float* d_mlp = nullptr;         // Newton-guess network, weights bf16-rounded (own allocation, kept across grid rebuilds)
+    int* d_slot = nullptr;          // slot of every listed cell within its level (device copy of h_slot)
     std::vector<float> mlp_master;  // its parameters before rounding
     double mlp_m[8] = {0}, mlp_s[8] = {0};
     int64_t total_blocks = 0;
@@ -125,7 +126,7 @@ struct lbm_ctx {
         allocs.clear();
         dev_bytes = 0;
         for (auto& d : dl) d = DevLevel{};
-        d_status = nullptr; d_nstat = nullptr; d_partial = nullptr; d_out5 = nullptr;
+        d_status = nullptr; d_nstat = nullptr; d_partial = nullptr; d_out5 = nullptr; d_slot = nullptr;
     }
     int L() const { return grid.n_levels; }
     int64_t period() const { return int64_t(1) << (grid.n_levels - 1); }
@@ -361,6 +362,23 @@ int ledger_launch_args(lbm_ctx* c, StepArgs* a, long long* nblocks, KernelSet* k
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2) {
+    int q = 0, d = 2, r = 1;
+    double c2 = 1.0 / 3.0;
+    switch (lattice) {
+        case LBM_D2Q9: q = 9; break;
+        case LBM_D3Q27: q = 27; d = 3; break;
+        case LBM_D2Q21: q = 21; r = 3; c2 = 2.0 / 3.0; break;
+        case LBM_D2Q37: q = 37; r = 3; c2 = constants().cs2_37; break;
+        default: return fail(LBM_ERR_ARG, "unknown lattice");
+    }
+    if (Q) *Q = q;
+    if (D) *D = d;
+    if (reach) *reach = r;
+    if (cs2) *cs2 = c2;
+    return LBM_OK;
+}
 
 int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
     if (!out) return fail(LBM_ERR_ARG, "out is null");
@@ -677,6 +695,18 @@ int lbm_velocities(lbm_ctx* c, int* Q, const int32_t** xi) {
     return LBM_OK;
 }
 
+// device copy of the listing -> slot table (made on first use, freed with the grid)
+int ensure_slots(lbm_ctx* c) {
+    if (c->d_slot) return LBM_OK;
+    const int64_t n = (int64_t)c->h_slot.size();
+    std::vector<int32_t> s32(n);
+    for (int64_t k = 0; k < n; ++k) s32[k] = (int32_t)c->h_slot[k];
+    c->d_slot = (int*)c->dalloc(size_t(n) * 4);
+    if (!c->d_slot) return fail(LBM_ERR_OOM, "slot table");
+    CU(cudaMemcpy(c->d_slot, s32.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double* T) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
@@ -688,35 +718,39 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double
     const int BS = c->grid.BS;
     StepArgs a;
     fill_args(c, a);
+    if (int r = ensure_slots(c)) return r;
+    // the fields in listing order on the device (one copy per field), then per level moved to
+    // slot order and turned into equilibria
+    const int nc = 1 + c->dim + (comp ? 1 : 0);
+    int64_t maxcell = 0;
+    for (int i = 0; i < c->L(); ++i) maxcell = std::max<int64_t>(maxcell, c->grid.levels[i].nb * BS);
+    double *d_list = nullptr, *d_lev = nullptr;
     int rc = LBM_OK;
+    if (cudaMalloc(&d_list, size_t(nc) * n * 8) != cudaSuccess || cudaMalloc(&d_lev, size_t(5) * maxcell * 8) != cudaSuccess) {
+        rc = fail(LBM_ERR_OOM, "initialisation staging");
+    } else if (cudaMemcpyAsync(d_list, rho, size_t(n) * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+               cudaMemcpyAsync(d_list + n, u, size_t(c->dim) * n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+               (comp && cudaMemcpyAsync(d_list + (1 + c->dim) * n, T, size_t(n) * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)) {
+        rc = fail(LBM_ERR_CUDA, "initialisation upload");
+    }
     for (int i = 0; i < c->L() && rc == LBM_OK; ++i) {
         const int64_t ncell = c->grid.levels[i].nb * BS;
         if (!ncell) continue;
-        std::vector<double> hr(ncell, 1.0), hu(size_t(3) * ncell, 0.0), hT(ncell, c->T0());
-        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
-            const int64_t s = c->h_slot[k];
-            hr[s] = rho[k];
-            for (int d = 0; d < c->dim; ++d) hu[d * ncell + s] = u[d * n + k];
-            if (comp) hT[s] = T[k];
-        }
-        double *pr = nullptr, *pu = nullptr, *pT = nullptr;
-        if (cudaMalloc(&pr, ncell * 8) != cudaSuccess || cudaMalloc(&pu, 3 * ncell * 8) != cudaSuccess ||
-            cudaMalloc(&pT, ncell * 8) != cudaSuccess) {
-            rc = fail(LBM_ERR_OOM, "initialisation staging");
-        } else if (cudaMemcpy(pr, hr.data(), ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-                   cudaMemcpy(pu, hu.data(), 3 * ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-                   cudaMemcpy(pT, hT.data(), ncell * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
-            rc = fail(LBM_ERR_CUDA, "initialisation upload");
-        } else {
-            c->ks.init(a, i, pr, pu, pT, c->stream);
-            cudaError_t e = cudaStreamSynchronize(c->stream);
-            if (e == cudaSuccess) e = cudaGetLastError();
-            if (e != cudaSuccess) rc = fail(LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
-        }
-        cudaFree(pr);
-        cudaFree(pu);
-        cudaFree(pT);
+        const int64_t f0 = c->level_first[i], cnt = c->level_first[i + 1] - f0;
+        double* pr = d_lev;
+        double* pu = d_lev + ncell;
+        double* pT = d_lev + 4 * ncell;
+        cudaMemsetAsync(d_lev, 0, size_t(5) * ncell * 8, c->stream);
+        launch_scatter(c->d_slot + f0, cnt, d_list + f0, n, 1, pr, ncell, c->stream);
+        launch_scatter(c->d_slot + f0, cnt, d_list + n + f0, n, c->dim, pu, ncell, c->stream);
+        if (comp) launch_scatter(c->d_slot + f0, cnt, d_list + (1 + c->dim) * n + f0, n, 1, pT, ncell, c->stream);
+        c->ks.init(a, i, pr, pu, pT, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);      // the staging buffer is reused per level
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
     }
+    cudaFree(d_list);
+    cudaFree(d_lev);
     if (rc) return rc;
     int st = 0;
     CU(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -869,45 +903,52 @@ int lbm_sync(lbm_ctx* c) {
     return LBM_OK;
 }
 
-static int read_common(lbm_ctx* c, int which, int ncomp, std::vector<std::vector<double>>& per_level) {
+// readout of per-cell quantities (which: 0 moments rho, u(3), T; 1 f; 2 g; 3 lambda) into a
+// device buffer in listing order, ncomp components of n values each
+static int read_common(lbm_ctx* c, int which, int ncomp, double** d_out) {
     if (int r = ready(c)) return r;
+    if (int r = ensure_slots(c)) return r;
     StepArgs a;
     current_args(c, a);
     const int BS = c->grid.BS;
-    per_level.assign(c->L(), {});
+    const int64_t n = (int64_t)c->h_type.size();
+    int64_t maxcell = 0;
+    for (int i = 0; i < c->L(); ++i) maxcell = std::max<int64_t>(maxcell, c->grid.levels[i].nb * BS);
+    double *d = nullptr, *lst = nullptr;
+    if (cudaMalloc(&d, size_t(ncomp) * maxcell * 8) != cudaSuccess || cudaMalloc(&lst, size_t(ncomp) * n * 8) != cudaSuccess) {
+        cudaFree(d);
+        return fail(LBM_ERR_OOM, "readout buffer");
+    }
     for (int i = 0; i < c->L(); ++i) {
         const int64_t ncell = c->grid.levels[i].nb * BS;
         if (!ncell) continue;
-        double* d = nullptr;
-        if (cudaMalloc(&d, size_t(ncomp) * ncell * 8) != cudaSuccess) return fail(LBM_ERR_OOM, "readout buffer");
+        const int64_t f0 = c->level_first[i], cnt = c->level_first[i + 1] - f0;
         cudaMemsetAsync(d, 0, size_t(ncomp) * ncell * 8, c->stream);
         c->ks.read(a, i, which, d, c->stream);
-        per_level[i].resize(size_t(ncomp) * ncell);
-        cudaError_t e1 = cudaMemcpyAsync(per_level[i].data(), d, size_t(ncomp) * ncell * 8, cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e2 = cudaStreamSynchronize(c->stream);
-        cudaFree(d);
-        if (e1 != cudaSuccess || e2 != cudaSuccess)
-            return fail(LBM_ERR_CUDA, std::string("readout: ") + cudaGetErrorString(e2 != cudaSuccess ? e2 : e1));
+        launch_gather(c->d_slot + f0, cnt, d, ncell, ncomp, lst + f0, n, c->stream);
     }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaFree(lst);
+        return fail(LBM_ERR_CUDA, std::string("readout: ") + cudaGetErrorString(e));
+    }
+    *d_out = lst;
     return LBM_OK;
 }
 
 int lbm_read_moments(lbm_ctx* c, double* rho, double* u, double* T) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (!rho || !u) return fail(LBM_ERR_ARG, "null output");
-    std::vector<std::vector<double>> pl;
-    if (int r = read_common(c, 0, 5, pl)) return r;
+    double* lst = nullptr;
+    if (int r = read_common(c, 0, 5, &lst)) return r;
     const int64_t n = (int64_t)c->h_type.size();
-    const int BS = c->grid.BS;
-    for (int i = 0; i < c->L(); ++i) {
-        const int64_t ncell = c->grid.levels[i].nb * BS;
-        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
-            const int64_t s = c->h_slot[k];
-            rho[k] = pl[i][s];
-            for (int d = 0; d < c->dim; ++d) u[d * n + k] = pl[i][(1 + d) * ncell + s];
-            if (T) T[k] = pl[i][4 * ncell + s];
-        }
-    }
+    cudaError_t e = cudaMemcpy(rho, lst, size_t(n) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(u, lst + n, size_t(c->dim) * n * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && T) e = cudaMemcpy(T, lst + 4 * n, size_t(n) * 8, cudaMemcpyDeviceToHost);
+    cudaFree(lst);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("readout copy: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
@@ -917,17 +958,12 @@ int lbm_read_populations(lbm_ctx* c, int which, double* out) {
     if (which == 1 && !c->comp()) return fail(LBM_ERR_ARG, "model has no g populations");
     if (which == 2 && c->model != LBM_COMP_NUMERICAL) return fail(LBM_ERR_ARG, "model has no multipliers");
     const int ncomp = which == 2 ? 8 : c->grid.lat.Q;
-    std::vector<std::vector<double>> pl;
-    if (int r = read_common(c, which + 1, ncomp, pl)) return r;
+    double* lst = nullptr;
+    if (int r = read_common(c, which + 1, ncomp, &lst)) return r;
     const int64_t n = (int64_t)c->h_type.size();
-    const int BS = c->grid.BS;
-    for (int i = 0; i < c->L(); ++i) {
-        const int64_t ncell = c->grid.levels[i].nb * BS;
-        for (int64_t k = c->level_first[i]; k < c->level_first[i + 1]; ++k) {
-            const int64_t s = c->h_slot[k];
-            for (int q = 0; q < ncomp; ++q) out[q * n + k] = pl[i][q * ncell + s];
-        }
-    }
+    cudaError_t e = cudaMemcpy(out, lst, size_t(ncomp) * n * 8, cudaMemcpyDeviceToHost);
+    cudaFree(lst);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("readout copy: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 

@@ -33,7 +33,7 @@ __device__ __forceinline__ void poly_guess21(R ux, R uy, R Tt, R* lam) {
         const R w = sizeof(R) == 4 ? R(cw21f[q]) : R(cw21[q]);
         const R fp = w * s;
         if (fp > R(0)) {
-            const R y = R(-1) - log(fp);
+            const R y = R(-1) - r_log(fp);
             int k = 0;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -51,7 +51,7 @@ __device__ __forceinline__ void poly_guess21(R ux, R uy, R Tt, R* lam) {
     const R tgt[8] = {R(1), ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
     bool fin = true;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) fin = fin && isfinite(fit[a]);
+    for (int a = 0; a < 8; ++a) fin = fin && r_finite(fit[a]);
     R e[21], G[8], gf = R(0), g0 = R(0);
     if (fin) {
         newton_eval<21, R>(fit, tgt, e, G);

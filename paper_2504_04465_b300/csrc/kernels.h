@@ -34,6 +34,10 @@ bool find_kernels_d2q21(int model, int storage, const int* block, bool newton_fp
 
 int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
                      float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);
+void launch_scatter(const int* slot, long long count, const double* src, long long src_stride, int ncomp, double* dst,
+                    long long dst_stride, cudaStream_t s);
+void launch_gather(const int* slot, long long count, const double* src, long long src_stride, int ncomp, double* dst,
+                   long long dst_stride, cudaStream_t s);
 void launch_newton_batch_d2q21(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s);
 
 // Constant tables of the D2Q37 and D2Q21 translation units (current device).

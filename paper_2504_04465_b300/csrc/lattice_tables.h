@@ -59,6 +59,21 @@ LBM_HD constexpr int enum37(int q, int want_y) {
     return 0;
 }
 
+// the same enumerations as switch tables: folded to constants where q is known at compile time
+// (unrolled loops), a jump table otherwise
+LBM_HD constexpr int d2q21_x(int q) {
+    switch (q) { case 0: return 0; case 1: return -2; case 2: return 0; case 3: return 2; case 4: return -1; case 5: return 0; case 6: return 1; case 7: return -3; case 8: return -2; case 9: return -1; case 10: return 0; case 11: return 1; case 12: return 2; case 13: return 3; case 14: return -1; case 15: return 0; case 16: return 1; case 17: return -2; case 18: return 0; case 19: return 2; case 20: return 0; default: return 0; }
+}
+LBM_HD constexpr int d2q21_y(int q) {
+    switch (q) { case 0: return -3; case 1: return -2; case 2: return -2; case 3: return -2; case 4: return -1; case 5: return -1; case 6: return -1; case 7: return 0; case 8: return 0; case 9: return 0; case 10: return 0; case 11: return 0; case 12: return 0; case 13: return 0; case 14: return 1; case 15: return 1; case 16: return 1; case 17: return 2; case 18: return 2; case 19: return 2; case 20: return 3; default: return 0; }
+}
+LBM_HD constexpr int d2q37_x(int q) {
+    switch (q) { case 0: return -1; case 1: return 0; case 2: return 1; case 3: return -2; case 4: return -1; case 5: return 0; case 6: return 1; case 7: return 2; case 8: return -3; case 9: return -2; case 10: return -1; case 11: return 0; case 12: return 1; case 13: return 2; case 14: return 3; case 15: return -3; case 16: return -2; case 17: return -1; case 18: return 0; case 19: return 1; case 20: return 2; case 21: return 3; case 22: return -3; case 23: return -2; case 24: return -1; case 25: return 0; case 26: return 1; case 27: return 2; case 28: return 3; case 29: return -2; case 30: return -1; case 31: return 0; case 32: return 1; case 33: return 2; case 34: return -1; case 35: return 0; case 36: return 1; default: return 0; }
+}
+LBM_HD constexpr int d2q37_y(int q) {
+    switch (q) { case 0: return -3; case 1: return -3; case 2: return -3; case 3: return -2; case 4: return -2; case 5: return -2; case 6: return -2; case 7: return -2; case 8: return -1; case 9: return -1; case 10: return -1; case 11: return -1; case 12: return -1; case 13: return -1; case 14: return -1; case 15: return 0; case 16: return 0; case 17: return 0; case 18: return 0; case 19: return 0; case 20: return 0; case 21: return 0; case 22: return 1; case 23: return 1; case 24: return 1; case 25: return 1; case 26: return 1; case 27: return 1; case 28: return 1; case 29: return 2; case 30: return 2; case 31: return 2; case 32: return 2; case 33: return 2; case 34: return 3; case 35: return 3; case 36: return 3; default: return 0; }
+}
+
 template <int Q> struct Lat;
 
 template <> struct Lat<9> {
@@ -77,15 +92,15 @@ template <> struct Lat<27> {
 
 template <> struct Lat<21> {
     static constexpr int Q = 21, D = 2, R = 3;
-    LBM_HD static constexpr int cx(int q) { return enum21(q, 0); }
-    LBM_HD static constexpr int cy(int q) { return enum21(q, 1); }
+    LBM_HD static constexpr int cx(int q) { return d2q21_x(q); }
+    LBM_HD static constexpr int cy(int q) { return d2q21_y(q); }
     LBM_HD static constexpr int cz(int) { return 0; }
 };
 
 template <> struct Lat<37> {
     static constexpr int Q = 37, D = 2, R = 3;
-    LBM_HD static constexpr int cx(int q) { return enum37(q, 0); }
-    LBM_HD static constexpr int cy(int q) { return enum37(q, 1); }
+    LBM_HD static constexpr int cx(int q) { return d2q37_x(q); }
+    LBM_HD static constexpr int cy(int q) { return d2q37_y(q); }
     LBM_HD static constexpr int cz(int) { return 0; }
 };
 

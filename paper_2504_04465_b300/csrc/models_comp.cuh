@@ -13,6 +13,20 @@
 
 namespace lbm {
 
+// math of the solver's own precision (no promotion of FP32 arguments to the FP64 routines)
+__device__ __forceinline__ float r_exp(float x) { return expf(x); }
+__device__ __forceinline__ double r_exp(double x) { return ::exp(x); }
+__device__ __forceinline__ float r_log(float x) { return logf(x); }
+__device__ __forceinline__ double r_log(double x) { return ::log(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ float r_fabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double r_fabs(double x) { return ::fabs(x); }
+__device__ __forceinline__ float r_fmax(float x, float y) { return fmaxf(x, y); }
+__device__ __forceinline__ double r_fmax(double x, double y) { return ::fmax(x, y); }
+__device__ __forceinline__ bool r_finite(float x) { return __finitef(x) != 0; }
+__device__ __forceinline__ bool r_finite(double x) { return isfinite(x); }
+
 // thermal Hermite moments a_k, components ordered (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (3,0) (2,1)
 // (1,2) (0,3) (4,0) (3,1) (2,2) (1,3) (0,4); dT = T - theta
 template <typename T>
@@ -65,7 +79,7 @@ __device__ __forceinline__ void newton_eval(const R* lam, const R* tgt, R* e, R*
         R s = R(1);
 #pragma unroll
         for (int a = 0; a < 8; ++a) s += lam[a] * R(MB<Q>::m(q, a));
-        e[q] = exp(-s);
+        e[q] = r_exp(-s);
 #pragma unroll
         for (int a = 0; a < 8; ++a) G[a] += e[q] * R(MB<Q>::m(q, a));
     }
@@ -79,7 +93,7 @@ __device__ __forceinline__ void chol8_solve(R* A, const R* G, R* d) {
         R s = A[j * (j + 1) / 2 + j];
 #pragma unroll
         for (int k = 0; k < j; ++k) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-        const R djj = sqrt(s);
+        const R djj = r_sqrt(s);
         A[j * (j + 1) / 2 + j] = djj;
 #pragma unroll
         for (int i = j + 1; i < 8; ++i) {
@@ -140,8 +154,8 @@ __device__ __noinline__ int newton_solve(R ux, R uy, R Tt, R* lam, R* e, R tol, 
         bool fin = true;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-            fin = fin && isfinite(G[a]);
-            gmax = fmax(gmax, fabs(G[a]));
+            fin = fin && r_finite(G[a]);
+            gmax = r_fmax(gmax, r_fabs(G[a]));
         }
         if (fin && gmax < tol) { *conv = 1; break; }
         if (!fin || it == max_iter) break;
@@ -149,7 +163,7 @@ __device__ __noinline__ int newton_solve(R ux, R uy, R Tt, R* lam, R* e, R tol, 
         newton_dir<Q, R>(e, G, d);
         bool dfin = true;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) dfin = dfin && isfinite(d[a]);
+        for (int a = 0; a < 8; ++a) dfin = dfin && r_finite(d[a]);
         if (!dfin) break;
         R g0 = R(0);
 #pragma unroll
@@ -165,7 +179,7 @@ __device__ __noinline__ int newton_solve(R ux, R uy, R Tt, R* lam, R* e, R tol, 
             R g1 = R(0);
 #pragma unroll
             for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
-            if (g1 < g0 || (h == 30 && isfinite(g1))) { take = true; break; }
+            if (g1 < g0 || (h == 30 && r_finite(g1))) { take = true; break; }
             t *= R(0.5);
         }
         if (!take) {                        // keep the current iterate (restore its e)
@@ -192,8 +206,8 @@ __device__ __forceinline__ int newton_solve_inl(R ux, R uy, R Tt, R* lam, R* e, 
         bool fin = true;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-            fin = fin && isfinite(G[a]);
-            gmax = fmax(gmax, fabs(G[a]));
+            fin = fin && r_finite(G[a]);
+            gmax = r_fmax(gmax, r_fabs(G[a]));
         }
         if (fin && gmax < tol) { *conv = 1; break; }
         if (!fin || it == max_iter) break;
@@ -201,7 +215,7 @@ __device__ __forceinline__ int newton_solve_inl(R ux, R uy, R Tt, R* lam, R* e, 
         newton_dir<Q, R>(e, G, d);
         bool dfin = true;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) dfin = dfin && isfinite(d[a]);
+        for (int a = 0; a < 8; ++a) dfin = dfin && r_finite(d[a]);
         if (!dfin) break;
         R g0 = R(0);
 #pragma unroll
@@ -217,7 +231,7 @@ __device__ __forceinline__ int newton_solve_inl(R ux, R uy, R Tt, R* lam, R* e, 
             R g1 = R(0);
 #pragma unroll
             for (int a = 0; a < 8; ++a) g1 += Gt[a] * Gt[a];
-            if (g1 < g0 || (h == 30 && isfinite(g1))) { take = true; break; }
+            if (g1 < g0 || (h == 30 && r_finite(g1))) { take = true; break; }
             t *= R(0.5);
         }
         if (!take) {                        // keep the current iterate (restore its e)

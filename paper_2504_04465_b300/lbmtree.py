@@ -89,6 +89,7 @@ _sig = {
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
     "lbm_set_guess": [_P, C.c_int],
+    "lbm_lattice_info": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D],
     "lbm_set_newton_precision": [_P, C.c_int, C.c_double],
     "lbm_batch_create": [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
     "lbm_batch_destroy": [C.c_void_p],
@@ -147,6 +148,16 @@ class Batch:
 class MlpTrainParams(C.Structure):
     _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
                 ("seed", C.c_uint64), ("final_loss", C.c_float)]
+
+
+def lattice_info(name: str) -> dict:
+    q, d, r, c2 = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    _check(_lib.lbm_lattice_info(LATTICE[name], C.byref(q), C.byref(d), C.byref(r), C.byref(c2)), "lbm_lattice_info")
+    return {"Q": q.value, "D": d.value, "reach": r.value, "cs2": c2.value}
+
+
+def lattice_cs2(name: str) -> float:
+    return lattice_info(name)["cs2"]
 
 
 def mlp_nparams() -> int:
@@ -326,11 +337,16 @@ class Context:
         _check(_lib.lbm_sync(self._h), "lbm_sync")
 
     # -------------------------------------------------------------- outputs
-    def moments(self):
+    def moments(self, out=None):
+        """(rho, u (dim, n), T) in lbm_cells order; ``out`` = preallocated (rho, u, T) float64
+        arrays (for instance in pinned host memory) to write into."""
         n = self.cells()[0].size
-        rho = np.empty(n)
-        u = np.empty(self.dim * n)
-        T = np.empty(n)
+        if out is None:
+            rho, u, T = np.empty(n), np.empty(self.dim * n), np.empty(n)
+        else:
+            rho, u, T = out
+            if rho.size != n or u.size != self.dim * n or T.size != n:
+                raise ValueError("output arrays of the wrong size")
         _check(_lib.lbm_read_moments(self._h, _dptr(rho), _dptr(u), _dptr(T)), "lbm_read_moments")
         return rho, u.reshape(self.dim, n), T
 

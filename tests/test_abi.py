@@ -147,3 +147,13 @@ def test_batch_case_recipe_builds(lt):
         ctx.close()
     assert 20e6 <= total <= 30e6, total
     assert levels == {2, 3, 4}
+
+
+def test_lattice_info_matches_the_oracle_lattices(lt):
+    for name in ("D2Q9", "D2Q21", "D2Q37", "D3Q27"):
+        info = lt.lattice_info(name)
+        ref = L.LATTICES[name]
+        assert info["Q"] == ref.Q and info["D"] == ref.D
+        assert abs(info["cs2"] - ref.cs2) < 1e-14
+    with pytest.raises(lt.LbmError):
+        lt._check(lt._lib.lbm_lattice_info(13, None, None, None, None), "lbm_lattice_info")
