@@ -15,6 +15,7 @@ namespace lbm {
 static __constant__ double cw21[21];
 static __constant__ float cw21f[21], cinvw21f[21];   // the weights in FP32 and their reciprocals
 static __constant__ double cH21[21][10];
+static __constant__ float cH21f[21][10];   // the same in FP32
 
 template <typename R>
 __device__ __forceinline__ void poly_guess21(R ux, R uy, R Tt, R* lam) {
@@ -29,7 +30,7 @@ __device__ __forceinline__ void poly_guess21(R ux, R uy, R Tt, R* lam) {
     for (int q = 0; q < 21; ++q) {
         R s = R(0);
 #pragma unroll
-        for (int k = 0; k < 10; ++k) s += R(cH21[q][k]) * a[k];
+        for (int k = 0; k < 10; ++k) s += (sizeof(R) == 4 ? R(cH21f[q][k]) : R(cH21[q][k])) * a[k];
         const R w = sizeof(R) == 4 ? R(cw21f[q]) : R(cw21[q]);
         const R fp = w * s;
         if (fp > R(0)) {
@@ -179,6 +180,9 @@ cudaError_t upload_tables_d2q21(const double* w21, const double* H21) {
     }
     if ((e = cudaMemcpyToSymbol(cw21f, wf, sizeof(wf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(cinvw21f, iwf, sizeof(iwf))) != cudaSuccess) return e;
+    float hf[21 * 10];
+    for (int i = 0; i < 21 * 10; ++i) hf[i] = (float)H21[i];
+    if ((e = cudaMemcpyToSymbol(cH21f, hf, sizeof(hf))) != cudaSuccess) return e;
     return cudaMemcpyToSymbol(cH21, H21, sizeof(double) * 21 * 10);
 }
 

@@ -10,7 +10,9 @@ namespace lbm {
 static __constant__ double cw37[37];
 static __constant__ float cw37f[37], cinvw37f[37];   // the weights in FP32 and their reciprocals
 static __constant__ double cH37[37][15];
+static __constant__ float cH37f[37][15];   // the same in FP32 (no conversion in the FP32 kernels)
 static __constant__ double ccs2_37;
+static __constant__ float ccs2_37f;
 
 struct D2Q37M {
     static constexpr int D = 2, Q = 37;
@@ -31,14 +33,15 @@ struct D2Q37M {
                                typename Store<ST>::T uy, typename Store<ST>::T Tt, double*,
                                typename Store<ST>::T* f, int* iters, int* conv) {
         using T = typename Store<ST>::T;
+        constexpr bool F = sizeof(T) == 4;
         T a[15];
-        thermal_moments<T>(rho, ux, uy, Tt - T(ccs2_37), 4, a);
+        thermal_moments<T>(rho, ux, uy, Tt - (F ? T(ccs2_37f) : T(ccs2_37)), 4, a);
 #pragma unroll
         for (int i = 0; i < 37; ++i) {
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < 15; ++k) s += T(cH37[i][k]) * a[k];
-            f[i] = T(cw37[i]) * s;
+            for (int k = 0; k < 15; ++k) s += (F ? T(cH37f[i][k]) : T(cH37[i][k])) * a[k];
+            f[i] = (F ? T(cw37f[i]) : T(cw37[i])) * s;
         }
         *iters = 0;
         *conv = 1;
@@ -62,6 +65,11 @@ cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2
     if ((e = cudaMemcpyToSymbol(cw37f, wf, sizeof(wf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(cinvw37f, iwf, sizeof(iwf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(cH37, H37, sizeof(double) * 37 * 15)) != cudaSuccess) return e;
+    float hf[37 * 15];
+    for (int i = 0; i < 37 * 15; ++i) hf[i] = (float)H37[i];
+    if ((e = cudaMemcpyToSymbol(cH37f, hf, sizeof(hf))) != cudaSuccess) return e;
+    const float c2f = (float)cs2_37;
+    if ((e = cudaMemcpyToSymbol(ccs2_37f, &c2f, sizeof(float))) != cudaSuccess) return e;
     return cudaMemcpyToSymbol(ccs2_37, &cs2_37, sizeof(double));
 }
 

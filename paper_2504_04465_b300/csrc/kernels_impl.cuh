@@ -260,13 +260,15 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
 }
 
 // ------------------------------------------------------------------ collision
-template <class M, int ST>
+// REL: write the binary16 storage value f*/(w rho_ref) - 1 (weakly compressible RR, F16DEV)
+template <class M, int ST, bool REL = false>
 __device__ __forceinline__ int collide(const ModelDev& m, const LevelDev& L, Cell<M, ST>& c, int* conv) {
     using T = typename Store<ST>::T;
     *conv = 1;
     const double tau = L.tau;
     if constexpr (!M::HAS_G) {
-        if constexpr (sizeof(T) == 4) weak_collide<M::D, M::RR, T>(c.f, L.omega_f, m.rho_ref_f);
+        if constexpr (REL) weak_collide<M::D, true, T, true>(c.f, L.omega_f, m.rho_ref_f, m.inv_rho_ref_f);
+        else if constexpr (sizeof(T) == 4) weak_collide<M::D, M::RR, T>(c.f, L.omega_f, m.rho_ref_f);
         else weak_collide<M::D, M::RR, T>(c.f, T(L.omega), T(m.rho_ref));
         return 0;
     } else {
@@ -369,13 +371,16 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l
             if (s_cnt[mid] <= p) lo = mid;
             else hi = mid;
         }
-        unsigned long long m = s_um[lo];
-        for (int r = p - s_cnt[lo]; r > 0; --r) m &= m - 1;
-        const int q = __ffsll((long long)m) - 1;
-        int cx = 0, cy = 0, cz = 0;
-#pragma unroll
-        for (int qq = 0; qq < M::Q; ++qq)
-            if (qq == q) { cx = M::cx(qq); cy = M::cy(qq); cz = M::cz(qq); }
+        // the r-th set bit of the owner's mask (0-based), 32 bits at a time
+        const unsigned long long m = s_um[lo];
+        const int r = p - s_cnt[lo];
+        const unsigned m0 = (unsigned)m, m1 = (unsigned)(m >> 32);
+        const int c0 = __popc(m0);
+        unsigned w = r < c0 ? m0 : m1;
+        const int rr = r < c0 ? r : r - c0;          // < popc(w): w keeps a set bit below
+        for (int i = 0; i < rr; ++i) w &= w - 1;
+        const int q = (r < c0 ? 0 : 32) + __ffs((int)w) - 1;
+        const int cx = M::cx(q), cy = M::cy(q), cz = M::cz(q);
         const long long ch0 = s_child[lo];
         T v[NK];
 #pragma unroll
@@ -484,14 +489,26 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         } else if constexpr (!FAST) {
             assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv, stage_ptr(sx));
         }
+        // interior kernel, binary16 deviations, recursive regularization: the collision writes
+        // the storage value directly (fine ghosts, which do not collide, are scaled instead)
+        constexpr bool REL = FAST && ST == ST_F16DEV && !M::HAS_G && M::RR && M::DEV;
         if (type != C_FGHOST) {
-            const int it = collide<M, ST>(a.m, L, c, &conv2);
+            const int it = collide<M, ST, REL>(a.m, L, c, &conv2);
             if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
             if (!conv || !conv2) set_status(a.status, -6);
+        } else if constexpr (REL) {
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) c.f[q] *= inv_ref_f<M, ST>(a.m, q);
         }
         // fine ghosts stream purely: stored as gathered (post-collision = pre-collision)
+        if constexpr (REL) {
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, wr, cell, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+            for (int q = 0; q < M::Q; ++q)
+                ((__half*)L.f[wr])[pidx<BX * BY * BZ, M::Q>(cell, q)] = __float2half_rn(c.f[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, wr, cell, q, a.m, c.f[q], M::HAS_G ? c.g[q] : T(0));
+        }
         if constexpr (M::HAS_LAM) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) L.lam[((long long)wr * 8 + j) * L.ncell + cell] = c.lam[j];

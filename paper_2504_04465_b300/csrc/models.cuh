@@ -118,9 +118,13 @@ __host__ __device__ __forceinline__ void tp_moments(const T* d, T& drho, T* j, T
 
 // Weakly compressible collision in place, on deviations d_i = f_i - w_i rho_ref.
 // RR = true: recursive regularization, else BGK (same equilibrium).
-template <int D, bool RR, typename T>
-__host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) {
+// REL (recursive regularization only): the result is written relative to the reference,
+// f*_i / (w_i rho_ref) - 1, the binary16 storage value, with inv_rho_ref = 1 / rho_ref: the
+// division by 18^D and by w_i rho_ref fold into one product by 1 / (W_x W_y W_z).
+template <int D, bool RR, typename T, bool REL = false>
+__host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, T inv_rho_ref = T(1)) {
     constexpr int NZ = TP<D>::NZ;
+    static_assert(!REL || RR, "relative output only for the regularized collision");
     T drho, j[3], m2[6];
     tp_moments<D, T>(f, drho, j, m2);
     const T rho = rho_ref + drho;
@@ -132,7 +136,7 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) 
     T kxx = 0, kyy = 0, kzz = 0, kxy = 0, kxz = 0, kyz = 0;
     if constexpr (RR) {
         // (1 - 1/tau) Pi_ab, Pi_ab = sum xi_a xi_b f - rho (u_a u_b + c_s^2 delta_ab)
-        const T keep = T(1) - omega;
+        const T keep = REL ? (T(1) - omega) * inv_rho_ref : T(1) - omega;
         kxx = keep * (m2[0] - drho / T(3) - rho * ux * ux);
         kyy = keep * (m2[1] - drho / T(3) - rho * uy * uy);
         kxy = keep * (m2[3] - rho * ux * uy);
@@ -141,6 +145,10 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) 
             kxz = keep * (m2[4] - rho * ux * uz);
             kyz = keep * (m2[5] - rho * uy * uz);
         }
+    }
+    if constexpr (REL) {                 // equilibrium part divided by rho_ref as well
+        drho = drho * inv_rho_ref;
+        rho_ref = T(1);
     }
 #pragma unroll
     for (int ix = 0; ix < 3; ++ix)
@@ -160,7 +168,8 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) 
             if constexpr (D == 2) {
                 const int q = ix + 3 * iy;
                 const T num = A0 + N0;
-                if constexpr (RR) f[q] = div_den<T>(num, den, rden);
+                if constexpr (REL) f[q] = num * T(1.0 / (Wc(ix) * Wc(iy)));
+                else if constexpr (RR) f[q] = div_den<T>(num, den, rden);
                 else f[q] += omega * (div_den<T>(A0, den, rden) - f[q]);
             } else {
                 const T B0 = rho_ref * T(Wc(ix) * Wc(iy));
@@ -170,7 +179,8 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref) 
                     const T eq = A0 * az.E[iz] + B0 * az.e[iz];
                     if constexpr (RR) {
                         const T num = eq + N0 * az.E[iz] + N1 * T(X2c(iz)) + N2 * az.X1[iz];
-                        f[q] = div_den<T>(num, den, rden);
+                        if constexpr (REL) f[q] = num * T(1.0 / (Wc(ix) * Wc(iy) * Wc(iz)));
+                        else f[q] = div_den<T>(num, den, rden);
                     } else {
                         f[q] += omega * (div_den<T>(eq, den, rden) - f[q]);
                     }
