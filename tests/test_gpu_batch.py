@@ -96,6 +96,24 @@ def test_batch_f32_with_variant_equals_individual():
         assert_same(s, t, False)
 
 
+@pytest.mark.parametrize("storage", ["f16dev", "f32"])
+def test_batch_mixed_lattices_equal_individual(storage):
+    """D2Q9 (binary16 storage value written by the collision) and D2Q37 groups in one batch."""
+    from paper_2504_04465_b300.lbmtree import Batch
+    cases = small_cases()
+    solo = [make(c, storage) for c in cases]
+    together = [make(c, storage) for c in cases]
+    b = Batch(together)
+    b.use_graph(True)
+    b.step_fine(35)
+    b.sync()
+    for s in solo:
+        s.step_fine(35)
+        s.sync()
+    for c, s, t in zip(cases, solo, together):
+        assert_same(s, t, c["model"] == "poly_ddf")
+
+
 def test_batch_rejects_lattices_without_batched_kernels():
     from paper_2504_04465_b300.lbmtree import Batch, LbmError
     spec = I.sphere_spec(4)
