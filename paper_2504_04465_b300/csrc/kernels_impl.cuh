@@ -363,15 +363,15 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l
     if (P == 0) return;
     const LevelDev& F = a.lv[lev - 1];
     const int rdf = a.rd[lev - 1];
-    // decode pair p: owner cell and the population (the r-th set bit of its unknown mask)
-    auto decode = [&](int p, int& lo, int& q) {
-        lo = 0;
-        int hi = BS;                            // owner: the largest o with s_cnt[o] <= p
+#pragma unroll 1
+    for (int p = l; p < P; p += BS) {
+        int lo = 0, hi = BS;                    // owner: the largest o with s_cnt[o] <= p
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (s_cnt[mid] <= p) lo = mid;
             else hi = mid;
         }
+        // the r-th set bit of the owner's mask (0-based), 32 bits at a time
         const unsigned long long m = s_um[lo];
         const int r = p - s_cnt[lo];
         const unsigned m0 = (unsigned)m, m1 = (unsigned)(m >> 32);
@@ -379,11 +379,10 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l
         unsigned w = r < c0 ? m0 : m1;
         const int rr = r < c0 ? r : r - c0;          // < popc(w): w keeps a set bit below
         for (int i = 0; i < rr; ++i) w &= w - 1;
-        q = (r < c0 ? 0 : 32) + __ffs((int)w) - 1;
-    };
-    auto load_children = [&](int lo, int q, T* v) {
+        const int q = (r < c0 ? 0 : 32) + __ffs((int)w) - 1;
         const int cx = M::cx(q), cy = M::cy(q), cz = M::cz(q);
         const long long ch0 = s_child[lo];
+        T v[NK];
 #pragma unroll
         for (int kk = 0; kk < NK; ++kk) {
             const long long ch = ch0 + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
@@ -391,27 +390,10 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l
             T vg;
             load_pop<M, ST, BS>(F, rdf, s, q, a.m, v[kk], vg);
         }
-    };
-    // two pairs per round, so that both sets of child loads are in flight together
-#pragma unroll 1
-    for (int p = l; p < P; p += 2 * BS) {
-        int lo0, q0, lo1 = 0, q1 = 0;
-        decode(p, lo0, q0);
-        const bool two = p + BS < P;
-        if (two) decode(p + BS, lo1, q1);
-        T v0[NK], v1[NK];
-        load_children(lo0, q0, v0);
-        if (two) load_children(lo1, q1, v1);
-        T s0 = 0;
+        T sf = 0;
 #pragma unroll
-        for (int kk = 0; kk < NK; ++kk) s0 += v0[kk];
-        out[q0 * BS + lo0] = s0 / T(NK);
-        if (two) {
-            T s1 = 0;
-#pragma unroll
-            for (int kk = 0; kk < NK; ++kk) s1 += v1[kk];
-            out[q1 * BS + lo1] = s1 / T(NK);
-        }
+        for (int kk = 0; kk < NK; ++kk) sf += v[kk];
+        out[q * BS + lo] = sf / T(NK);
     }
 }
 
