@@ -37,9 +37,9 @@ from paper_2504_04465_b300 import inputs as I  # noqa: E402
 BYTES_PER_UPDATE = {"f64": 432, "f32": 216, "f16dev": 108}   # 27 populations read + written
 WORKLOAD = ("D3Q27 recursive-regularized, flow past a sphere (D = 64 finest cells), 4 levels, "
             "1024x512x512 finest-unit box, Ma 0.1, Re 3900")
-# dram bytes per cell update of the step kernel from the ncu capture summarised in
-# profiles/k_step_d3q27_sphere.md (None until a capture of the current kernel exists)
-NCU_TRAFFIC_PER_UPDATE = {"f32": None, "f16dev": None, "f64": None}
+# DRAM bytes per cell update of both step kernels over one full-size coarse step (16 launches),
+# from the single-pass ncu capture summarised in profiles/k_step_d3q27_sphere.md
+NCU_TRAFFIC_PER_UPDATE = {"f32": 230.6, "f16dev": 115.6, "f64": None}
 
 
 def peaks():
@@ -470,7 +470,9 @@ def run_ours(args, world, rank, local):
     traffic = NCU_TRAFFIC_PER_UPDATE.get(args.storage)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "bytes_per_update": bpu,
-            "traffic": None if traffic is None else traffic * updates_per_step * args.steps / max(launches, 1)}
+            "per": "coarse step: the interior and general step kernels of 8 fine iterations (event-timed together)",
+            "traffic": None if (traffic is None or args.scale != 1) else traffic * updates_per_step,
+            "traffic_per_update": traffic if args.scale == 1 else None}
     # end to end through the public API with host buffers: upload the fields, step, read the
     # conserved totals every step and the moments at the end
     e2e = None

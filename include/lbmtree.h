@@ -230,6 +230,19 @@ int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
  * the array: calls that overlap on the GPU race.  LBM_ERR_STATE off a synchronisation instant. */
 int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
 
+/* ---------------------------------------------------------------- checkpoint / restart */
+/* Write the state (populations of both buffers, multipliers, fine iteration counter, device
+ * status and Newton counters) to a file; synchronous.  lbm_load restores it into a context
+ * configured and built the same way (lattice, model, storage, block shape, grid): the file
+ * records a signature of these and is rejected (LBM_ERR_STATE) for another configuration. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Time every compiled step variant (occupancy targets, lbm_variants) over n_coarse coarse steps
+ * (after one warm-up step each) on the context's stream, select the fastest and return it; the
+ * steps advance the state.  ms_per_step (optional) receives one time per variant. */
+int lbm_autotune(lbm_ctx* ctx, int n_coarse, int* best_variant, float* ms_per_step);
+
 /* ---------------------------------------------------------------- batched cases */
 /* Several independent cases (contexts built and initialised on one device) advanced together:
  * each fine iteration launches, per group of cases sharing lattice, model, storage, block

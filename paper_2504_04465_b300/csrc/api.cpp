@@ -8,6 +8,7 @@
 // with period 2 * 2^(L-1) fine iterations, which is the span captured in the CUDA graph.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -860,6 +861,161 @@ int lbm_newton_batch(lbm_ctx* c, const double* d_uT, int64_t n, int guess, doubl
     m.guess = guess;
     launch_newton_batch_d2q21(d_uT, n, m, d_lambda, d_iters, c->stream);
     CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+// File: magic, format version, a signature of the configuration (lattice, model, storage, block,
+// levels, blocks and cell counts per level, a checksum of the cell types), the fine iteration
+// counter, the device status and Newton counters, then per level the populations of both
+// buffers (f, g) and the multipliers, as stored.
+namespace {
+constexpr uint64_t CKPT_MAGIC = 0x4C424D545245454BULL;   // "LBMTREEK"
+constexpr uint32_t CKPT_VERSION = 1;
+
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, lattice, model, storage;
+    int32_t block[3], n_levels;
+    int64_t nb[8], ncell[8];
+    uint64_t type_sum;
+    int64_t t;
+};
+
+CkptHeader ckpt_header(const lbm_ctx* c) {
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = CKPT_MAGIC;
+    h.version = CKPT_VERSION;
+    h.lattice = (uint32_t)c->lattice;
+    h.model = (uint32_t)c->model;
+    h.storage = (uint32_t)c->storage;
+    for (int d = 0; d < 3; ++d) h.block[d] = c->block[d];
+    h.n_levels = c->L();
+    uint64_t s = 1469598103934665603ULL;               // FNV-1a over the cell types
+    for (int i = 0; i < c->L() && i < 8; ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        h.nb[i] = lv.nb;
+        h.ncell[i] = lv.nb * c->grid.BS;
+        for (uint8_t v : lv.type) s = (s ^ v) * 1099511628211ULL;
+    }
+    h.type_sum = s;
+    h.t = c->t;
+    return h;
+}
+
+// the device arrays of the state with their sizes in bytes
+std::vector<std::pair<void*, size_t>> state_arrays(lbm_ctx* c) {
+    std::vector<std::pair<void*, size_t>> v;
+    const int Q = c->grid.lat.Q;
+    const size_t es = c->storage == LBM_F64 ? 8 : c->storage == LBM_F32 ? 4 : 2;
+    for (int i = 0; i < c->L(); ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * c->grid.BS;
+        const size_t bytes = size_t(Q) * (ncell + c->grid.BS) * es;
+        for (int k = 0; k < 2; ++k) {
+            v.push_back({c->dl[i].f[k], bytes});
+            if (c->dl[i].g[k]) v.push_back({c->dl[i].g[k], bytes});
+        }
+        if (c->dl[i].lam) v.push_back({c->dl[i].lam, size_t(2) * 8 * ncell * 8});
+    }
+    v.push_back({c->d_status, sizeof(int)});
+    v.push_back({c->d_nstat, 19 * sizeof(unsigned long long)});
+    return v;
+}
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!path) return fail(LBM_ERR_ARG, "null path");
+    if (int r = ready(c)) return r;
+    CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(LBM_ERR_ARG, std::string("cannot open ") + path);
+    const CkptHeader h = ckpt_header(c);
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+    std::vector<char> buf;
+    for (auto& [p, n] : state_arrays(c)) {
+        if (!ok) break;
+        buf.resize(n);
+        if (cudaMemcpy(buf.data(), p, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(fp);
+            return fail(LBM_ERR_CUDA, "checkpoint read-back");
+        }
+        ok = std::fwrite(buf.data(), 1, n, fp) == n;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(LBM_ERR_ARG, std::string("write failed: ") + path);
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!path) return fail(LBM_ERR_ARG, "null path");
+    if (!c->built || c->host_only) return fail(LBM_ERR_STATE, "build the same grid on a device first");
+    CU(cudaSetDevice(c->device));
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(LBM_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) {
+        std::fclose(fp);
+        return fail(LBM_ERR_ARG, "not a checkpoint of this format");
+    }
+    CkptHeader mine = ckpt_header(c);
+    mine.t = h.t;
+    if (std::memcmp(&h, &mine, sizeof(h)) != 0) {
+        std::fclose(fp);
+        return fail(LBM_ERR_STATE, "checkpoint of another configuration or grid");
+    }
+    std::vector<char> buf;
+    for (auto& [p, n] : state_arrays(c)) {
+        buf.resize(n);
+        if (std::fread(buf.data(), 1, n, fp) != n) {
+            std::fclose(fp);
+            return fail(LBM_ERR_ARG, "truncated checkpoint");
+        }
+        if (cudaMemcpy(p, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(fp);
+            return fail(LBM_ERR_CUDA, "checkpoint upload");
+        }
+    }
+    std::fclose(fp);
+    c->t = h.t;
+    c->initialized = true;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- variant tuning
+int lbm_autotune(lbm_ctx* c, int n_coarse, int* best_variant, float* ms_per_step) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (int r = ready(c)) return r;
+    if (n_coarse < 1) return fail(LBM_ERR_ARG, "n_coarse must be positive");
+    CU(cudaSetDevice(c->device));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int best = c->variant;
+    float best_ms = -1.0f;
+    const int saved = c->variant;
+    for (int v = 0; v < c->ks.n_variants; ++v) {
+        lbm_set_variant(c, v);
+        if (int r = lbm_step(c, 1)) return r;                 // warm-up (builds the graph)
+        cudaEventRecord(e0, c->stream);
+        if (int r = lbm_step(c, n_coarse)) return r;
+        cudaEventRecord(e1, c->stream);
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)n_coarse;
+        if (ms_per_step) ms_per_step[v] = ms;
+        if (best_ms < 0 || ms < best_ms) { best_ms = ms; best = v; }
+    }
+    (void)saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbm_set_variant(c, best);
+    if (best_variant) *best_variant = best;
     return LBM_OK;
 }
 

@@ -17,7 +17,7 @@ static __constant__ float ccs2_37f;
 struct D2Q37M {
     static constexpr int D = 2, Q = 37;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
-    static constexpr int MINB_FAST = 2, MINB_GEN = 2;
+    static constexpr int MINB_FAST = 4, MINB_GEN = 2;
     static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
     static constexpr bool BATCH = true;   // compile the batched multi-case launch
     static constexpr bool DEV = false;

@@ -89,6 +89,9 @@ _sig = {
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
     "lbm_set_guess": [_P, C.c_int],
+    "lbm_save": [_P, C.c_char_p],
+    "lbm_load": [_P, C.c_char_p],
+    "lbm_autotune": [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)],
     "lbm_lattice_info": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D],
     "lbm_set_newton_precision": [_P, C.c_int, C.c_double],
     "lbm_batch_create": [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
@@ -230,6 +233,20 @@ class Context:
         p = CollisionParams(nu0, T0, gamma, int(sensor_A is not None), sensor_A or 0.0, newton_tol,
                             newton_max_iter, GUESS[guess], rho_ref, int(newton_fp32))
         _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
+
+    def save(self, path: str) -> None:
+        _check(_lib.lbm_save(self._h, str(path).encode()), "lbm_save")
+
+    def load(self, path: str) -> None:
+        _check(_lib.lbm_load(self._h, str(path).encode()), "lbm_load")
+
+    def autotune(self, n_coarse: int = 4):
+        """Select the fastest step variant; returns (variant, ms per coarse step of each)."""
+        nv = len(self.variants())
+        best = C.c_int()
+        ms = (C.c_float * nv)()
+        _check(_lib.lbm_autotune(self._h, n_coarse, C.byref(best), ms), "lbm_autotune")
+        return best.value, list(ms)
 
     def set_guess(self, guess: str) -> None:
         _check(_lib.lbm_set_guess(self._h, GUESS[guess]), "lbm_set_guess")

@@ -157,3 +157,12 @@ def test_lattice_info_matches_the_oracle_lattices(lt):
         assert abs(info["cs2"] - ref.cs2) < 1e-14
     with pytest.raises(lt.LbmError):
         lt._check(lt._lib.lbm_lattice_info(13, None, None, None, None), "lbm_lattice_info")
+
+
+def test_checkpoint_calls_check_their_arguments(lt, tmp_path):
+    ctx = lt.Context(2, device=-1)
+    ctx.configure(I.taylor_green_spec(32, 8, 24, 2), "D2Q9", "rr", "f64", nu0=0.02)
+    with pytest.raises(lt.LbmError):
+        ctx.save(str(tmp_path / "a.ckpt"))          # host-only context: nothing to save
+    with pytest.raises(lt.LbmError):
+        ctx.load(str(tmp_path / "missing.ckpt"))
