@@ -24,6 +24,7 @@
 #ifndef LBMTREE_H
 #define LBMTREE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -139,6 +140,17 @@ typedef struct {
 /* Velocity count, dimension, reach and lattice temperature c_s^2 of a velocity set (LBM_D2Q*,
  * LBM_D3Q27; D2Q37's c_s^2 is the one the library derives from the isotropy conditions). */
 int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2);
+/* Device memory of the grid's arrays (populations, tables, multipliers) from the caller's
+ * allocator, for instance a framework's caching allocator: alloc(bytes, user) returns device
+ * memory on the context's device (NULL on failure), free(ptr, user) returns it.  Set before
+ * lbm_build_grid; NULL restores cudaMalloc.  Temporary buffers of initialisation, readout and
+ * training still use cudaMalloc. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} lbm_allocator;
+int lbm_set_allocator(lbm_ctx* ctx, const lbm_allocator* allocator);
 int lbm_create(lbm_ctx** out, int dim, int device, void* stream);
 /* Release every device and host resource of the context.  NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);

@@ -113,17 +113,28 @@ struct lbm_ctx {
     double mlp_m[8] = {0}, mlp_s[8] = {0};
     int64_t total_blocks = 0;
 
+    lbm_allocator alloc_cb{nullptr, nullptr, nullptr};   // caller's device allocator (optional)
     void* dalloc(size_t bytes) {
         void* p = nullptr;
         if (bytes == 0) bytes = 16;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        bytes = (bytes + 255) & ~size_t(255);              // 256-byte aligned sizes
+        if (alloc_cb.alloc) {
+            p = alloc_cb.alloc(bytes, alloc_cb.user);
+            if (!p) return nullptr;
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            return nullptr;
+        }
         allocs.push_back(p);
         dev_bytes += (int64_t)bytes;
         return p;
     }
+    void dfree(void* p) {
+        if (alloc_cb.alloc) alloc_cb.free(p, alloc_cb.user);
+        else cudaFree(p);
+    }
     void release() {
         if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) dfree(p);
         allocs.clear();
         dev_bytes = 0;
         for (auto& d : dl) d = DevLevel{};
@@ -363,6 +374,14 @@ int ledger_launch_args(lbm_ctx* c, StepArgs* a, long long* nblocks, KernelSet* k
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_set_allocator(lbm_ctx* c, const lbm_allocator* a) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (c->built) return fail(LBM_ERR_STATE, "the allocator must be set before lbm_build_grid");
+    if (a && (!a->alloc || !a->free)) return fail(LBM_ERR_ARG, "allocator needs both alloc and free");
+    c->alloc_cb = a ? *a : lbm_allocator{nullptr, nullptr, nullptr};
+    return LBM_OK;
+}
 
 int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2) {
     int q = 0, d = 2, r = 1;

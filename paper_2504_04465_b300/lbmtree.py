@@ -89,6 +89,7 @@ _sig = {
     "lbm_mlp_nparams": [],
     "lbm_mlp_get": [_P, C.POINTER(C.c_float), _D, _D],
     "lbm_set_guess": [_P, C.c_int],
+    "lbm_set_allocator": [_P, C.c_void_p],
     "lbm_save": [_P, C.c_char_p],
     "lbm_load": [_P, C.c_char_p],
     "lbm_autotune": [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)],
@@ -110,6 +111,33 @@ _lib.lbm_last_error.argtypes = []
 _lib.lbm_last_error.restype = C.c_char_p
 
 EXPORTED = sorted(list(_sig) + ["lbm_last_error"])
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+def torch_allocator(device: int = 0, stream: int = 0) -> Allocator:
+    """lbm_allocator backed by PyTorch's caching allocator (keep the returned object alive as
+    long as the context)."""
+    import torch
+
+    def _alloc(nbytes, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+        except Exception:
+            return None
+
+    def _free(ptr, _user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+    a._keep = (_alloc, _free)
+    return a
 
 
 class Batch:
@@ -247,6 +275,12 @@ class Context:
         ms = (C.c_float * nv)()
         _check(_lib.lbm_autotune(self._h, n_coarse, C.byref(best), ms), "lbm_autotune")
         return best.value, list(ms)
+
+    def set_allocator(self, allocator: "Allocator | None") -> None:
+        """Device memory of the grid from ``allocator`` (see torch_allocator); None: cudaMalloc."""
+        self._allocator = allocator
+        _check(_lib.lbm_set_allocator(self._h, C.byref(allocator) if allocator is not None else None),
+               "lbm_set_allocator")
 
     def set_guess(self, guess: str) -> None:
         _check(_lib.lbm_set_guess(self._h, GUESS[guess]), "lbm_set_guess")

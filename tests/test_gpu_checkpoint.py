@@ -50,3 +50,29 @@ def test_autotune_selects_a_compiled_variant():
     assert 0 <= best < len(ctx.variants())
     assert len(ms) == len(ctx.variants()) and all(m > 0 for m in ms)
     assert ms[best] == min(ms)
+
+
+def test_grid_arrays_from_the_torch_caching_allocator():
+    import torch
+    from paper_2504_04465_b300 import lbmtree as lt
+    a = H.make_gpu(SPEC, "D2Q9", "rr", "f32", fields, nu0=0.08)
+    before = torch.cuda.memory_allocated(0)
+    ctx = lt.Context(2, device=0)
+    alloc = lt.torch_allocator(0)
+    ctx.set_allocator(alloc)
+    ctx.configure(SPEC, "D2Q9", "rr", "f32", nu0=0.08)
+    assert torch.cuda.memory_allocated(0) - before >= ctx.stats().device_bytes > 0
+    lv, xyz, ty = ctx.cells()
+    rho = np.ones(lv.size)
+    u = np.zeros((2, lv.size))
+    for level in np.unique(lv):
+        m = lv == level
+        r, uu = fields(int(level), xyz[m, :2], I.cell_centres(xyz[m, :2], int(level)))
+        rho[m], u[:, m] = r, uu
+    ctx.init_fields(rho, u)
+    a.step_fine(12)
+    ctx.step_fine(12)
+    a.sync()
+    ctx.sync()
+    assert np.array_equal(a.populations("f"), ctx.populations("f"))
+    ctx.close()
