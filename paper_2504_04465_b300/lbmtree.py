@@ -340,6 +340,15 @@ class Context:
         self.build_grid(spec.extent, spec.n_levels, spec.boxes, spec.solids)
 
     # -------------------------------------------------------------- cells
+    def n_cells(self) -> int:
+        """Number of listed cells (the length of the arrays of cells(), moments(), populations())."""
+        n = C.c_int64()
+        lv = C.POINTER(C.c_int32)()
+        xyz = C.POINTER(C.c_int32)()
+        ty = C.POINTER(C.c_uint8)()
+        _check(_lib.lbm_cells(self._h, C.byref(n), C.byref(lv), C.byref(xyz), C.byref(ty)), "lbm_cells")
+        return n.value
+
     def cells(self):
         """(level (n,), xyz (n, 3), type (n,)) in the library's cell order (copies)."""
         n = C.c_int64()
@@ -402,7 +411,7 @@ class Context:
         return rho, u.reshape(self.dim, n), T
 
     def populations(self, which: str = "f") -> np.ndarray:
-        n = self.cells()[0].size
+        n = self.n_cells()
         k = {"f": 0, "g": 1, "lambda": 2}[which]
         m = 8 if which == "lambda" else self.velocities().shape[0]
         out = np.empty(m * n)
