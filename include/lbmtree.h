@@ -39,7 +39,7 @@ extern "C" {
 #define LBM_ERR_OOM         -4   /* device or host allocation failed                           */
 #define LBM_ERR_GRID        -5   /* the requested grid violates a builder invariant            */
 #define LBM_ERR_NEWTON      -6   /* a Newton solve did not converge (result still written)     */
-#define LBM_ERR_NONFINITE   -7   /* a NaN/Inf was found by a reduction                        */
+#define LBM_ERR_NONFINITE   -7   /* a NaN/Inf was found by a reduction (lbm_conserved)         */
 #define LBM_ERR_UNSUPPORTED -10  /* combination of lattice/model/storage not built            */
 
 /* ---------------------------------------------------------------- enums */

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Not in the paper: the learned guess is a BASELINE-only extension.  The network maps
+Not in the paper: the learned guess is an extension beyond it.  The network maps
 x = (u_x, u_y, T/T0 - 1) to the 8 Lagrange multipliers of Eq. exponential through
     h1 = tanh(W1 x + b1)   (64)
     h2 = tanh(W2 h1 + b2)  (64)

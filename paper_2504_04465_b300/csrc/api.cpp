@@ -8,6 +8,7 @@
 // with period 2 * 2^(L-1) fine iterations, which is the span captured in the CUDA graph.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -1153,6 +1154,8 @@ int lbm_conserved(lbm_ctx* c, double out[5]) {
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(out, c->d_out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 5; ++k)
+        if (!std::isfinite(out[k])) return fail(LBM_ERR_NONFINITE, "the state holds NaN or Inf (conserved totals not finite)");
     return LBM_OK;
 }
 
