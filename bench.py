@@ -99,6 +99,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def replica_totals(ms: float, updates: int, dist=None, device: str = "cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's time and the sum of the
+    ranks' cell updates (value = updates / time)."""
+    if dist is None:
+        return ms, updates
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(float(n.item())))
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -456,12 +469,7 @@ def run_ours(args, world, rank, local):
             dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.stats().kernel_launches - l0
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    total_updates = updates_per_step * args.steps * world
+    t_max, total_updates = replica_totals(ms, updates_per_step * args.steps, dist, "cuda")
     value = total_updates / (t_max * 1e-3) / 1e6
     # roofline of the step kernel: it is the only kernel of the timed region
     bpu = BYTES_PER_UPDATE[args.storage]
