@@ -110,6 +110,9 @@ struct lbm_ctx {
     cudaGraphExec_t gexec = nullptr;
     float* d_mlp = nullptr;         // Newton-guess network, weights bf16-rounded (own allocation, kept across grid rebuilds)
     int* d_slot = nullptr;          // slot of every listed cell within its level (device copy of h_slot)
+    double* d_rd_lev = nullptr;     // readout scratch (slot order of one level), kept for repeated reads
+    double* d_rd_lst = nullptr;     // readout result in listing order
+    size_t rd_lev_bytes = 0, rd_lst_bytes = 0;
     std::vector<float> mlp_master;  // its parameters before rounding
     double mlp_m[8] = {0}, mlp_s[8] = {0};
     int64_t total_blocks = 0;
@@ -140,6 +143,10 @@ struct lbm_ctx {
         dev_bytes = 0;
         for (auto& d : dl) d = DevLevel{};
         d_status = nullptr; d_nstat = nullptr; d_partial = nullptr; d_out5 = nullptr; d_slot = nullptr;
+        if (d_rd_lev) cudaFree(d_rd_lev);
+        if (d_rd_lst) cudaFree(d_rd_lst);
+        d_rd_lev = d_rd_lst = nullptr;
+        rd_lev_bytes = rd_lst_bytes = 0;
     }
     int L() const { return grid.n_levels; }
     int64_t period() const { return int64_t(1) << (grid.n_levels - 1); }
@@ -1090,11 +1097,24 @@ static int read_common(lbm_ctx* c, int which, int ncomp, double** d_out) {
     const int64_t n = (int64_t)c->h_type.size();
     int64_t maxcell = 0;
     for (int i = 0; i < c->L(); ++i) maxcell = std::max<int64_t>(maxcell, c->grid.levels[i].nb * BS);
-    double *d = nullptr, *lst = nullptr;
-    if (cudaMalloc(&d, size_t(ncomp) * maxcell * 8) != cudaSuccess || cudaMalloc(&lst, size_t(ncomp) * n * 8) != cudaSuccess) {
-        cudaFree(d);
-        return fail(LBM_ERR_OOM, "readout buffer");
+    // scratch kept by the context between reads (grown on demand)
+    const size_t need_lev = size_t(ncomp) * maxcell * 8, need_lst = size_t(ncomp) * n * 8;
+    if (c->rd_lev_bytes < need_lev) {
+        if (c->d_rd_lev) cudaFree(c->d_rd_lev);
+        c->d_rd_lev = nullptr;
+        c->rd_lev_bytes = 0;
+        if (cudaMalloc(&c->d_rd_lev, need_lev) != cudaSuccess) { c->d_rd_lev = nullptr; return fail(LBM_ERR_OOM, "readout buffer"); }
+        c->rd_lev_bytes = need_lev;
     }
+    if (c->rd_lst_bytes < need_lst) {
+        if (c->d_rd_lst) cudaFree(c->d_rd_lst);
+        c->d_rd_lst = nullptr;
+        c->rd_lst_bytes = 0;
+        if (cudaMalloc(&c->d_rd_lst, need_lst) != cudaSuccess) { c->d_rd_lst = nullptr; return fail(LBM_ERR_OOM, "readout buffer"); }
+        c->rd_lst_bytes = need_lst;
+    }
+    double* d = c->d_rd_lev;
+    double* lst = c->d_rd_lst;
     for (int i = 0; i < c->L(); ++i) {
         const int64_t ncell = c->grid.levels[i].nb * BS;
         if (!ncell) continue;
@@ -1105,11 +1125,7 @@ static int read_common(lbm_ctx* c, int which, int ncomp, double** d_out) {
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
-    cudaFree(d);
-    if (e != cudaSuccess) {
-        cudaFree(lst);
-        return fail(LBM_ERR_CUDA, std::string("readout: ") + cudaGetErrorString(e));
-    }
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("readout: ") + cudaGetErrorString(e));
     *d_out = lst;
     return LBM_OK;
 }
@@ -1123,7 +1139,6 @@ int lbm_read_moments(lbm_ctx* c, double* rho, double* u, double* T) {
     cudaError_t e = cudaMemcpy(rho, lst, size_t(n) * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(u, lst + n, size_t(c->dim) * n * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && T) e = cudaMemcpy(T, lst + 4 * n, size_t(n) * 8, cudaMemcpyDeviceToHost);
-    cudaFree(lst);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("readout copy: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -1138,7 +1153,6 @@ int lbm_read_populations(lbm_ctx* c, int which, double* out) {
     if (int r = read_common(c, which + 1, ncomp, &lst)) return r;
     const int64_t n = (int64_t)c->h_type.size();
     cudaError_t e = cudaMemcpy(out, lst, size_t(ncomp) * n * 8, cudaMemcpyDeviceToHost);
-    cudaFree(lst);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("readout copy: ") + cudaGetErrorString(e));
     return LBM_OK;
 }

@@ -327,6 +327,25 @@ __device__ __forceinline__ unsigned axis_term(int lc, int c) {
     return ((unsigned)((o + 1) * DIG) << 20) | (unsigned)(s * STRIDE);
 }
 
+// Branch-free pull of every population of cell l of a block whose sources all exist (or read
+// the zero block): nboff_s holds the element offsets of the 27 neighbour blocks.
+template <class M, int ST, int BX, int BY, int BZ>
+__device__ __forceinline__ void gather_fast(const LevelDev& L, int rd, int l, const unsigned* nboff_s,
+                                            const ModelDev& m, Cell<M, ST>& c) {
+    constexpr int BS = BX * BY * BZ;
+    const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) {
+        // one packed term per axis (neighbour digit << 20 | local offset), summed: the terms
+        // depend on a single velocity component each and are shared between q
+        const unsigned P = axis_term<BX, 1, 1>(lx, M::cx(q)) + axis_term<BY, BX, 3>(ly, M::cy(q)) +
+                           axis_term<BZ, BX * BY, 9>(lz, M::cz(q));
+        const unsigned i = nboff_s[P >> 20] + (unsigned)(q * BS) + (P & 0xFFFFFu);
+        c.f[q] = Store<ST>::template load<M::DEV>(L.f[rd], i, ref_f<M, ST>(m, q));
+        if constexpr (M::HAS_G) c.g[q] = Store<ST>::template load<false>(L.g[rd], i, ref_g<M, ST>(m, q));
+    }
+}
+
 // Coalescence (Eq. coalescence) of every unknown population of every coarse ghost of the
 // block, shared out over all the block's threads: the (ghost, population) pairs are numbered by
 // a block prefix sum and thread t takes pairs t, t + BS, ...; each pair's 2^D children are
@@ -471,17 +490,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         // fluid cells without a record (no bounce-back link) have every source live: gather
         // them branch-free also inside the general blocks
         if (FAST || (type == C_FLUID && L.rec_id[cell] < 0)) {
-            const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
-#pragma unroll
-            for (int q = 0; q < M::Q; ++q) {
-                // one packed term per axis (neighbour digit << 20 | local offset), summed: the
-                // terms depend on a single velocity component each and are shared between q
-                const unsigned P = axis_term<BX, 1, 1>(lx, M::cx(q)) + axis_term<BY, BX, 3>(ly, M::cy(q)) +
-                                   axis_term<BZ, BX * BY, 9>(lz, M::cz(q));
-                const unsigned i = nboff_s[P >> 20] + (unsigned)(q * BS) + (P & 0xFFFFFu);
-                c.f[q] = Store<ST>::template load<M::DEV>(L.f[rd], i, ref_f<M, ST>(a.m, q));
-                if constexpr (M::HAS_G) c.g[q] = Store<ST>::template load<false>(L.g[rd], i, ref_g<M, ST>(a.m, q));
-            }
+            gather_fast<M, ST, BX, BY, BZ>(L, rd, l, nboff_s, a.m, c);
             if constexpr (M::HAS_LAM) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + cell];
@@ -665,31 +674,56 @@ template <class M, int ST, int BX, int BY, int BZ>
 __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, double* partial) {
     constexpr int BS = BX * BY * BZ;
     __shared__ int nbr_s[27];
+    __shared__ unsigned nboff_s[27];
     __shared__ double red[5][BS];
     long long b;
     const int lev = find_level(a, bid, &b);
     const LevelDev& L = a.lv[lev];
     const int l = threadIdx.x;
-    if (l < 27) nbr_s[l] = L.nbr[b * 27 + l];
+    if (l < 27) {
+        const int v = L.nbr[b * 27 + l];
+        nbr_s[l] = v;
+        nboff_s[l] = (unsigned)(v < 0 ? L.nb : v) * (unsigned)(M::Q * BS);
+    }
     __syncthreads();
     const long long cell = b * BS + l;
-    const bool simple = L.bflag[b] == 1;
+    const int bf = L.bflag[b];
+    const bool simple = bf == 1;
     const int type = simple ? (int)C_FLUID : (int)L.type[cell];
     double v[5] = {0, 0, 0, 0, 0};
     if (type == C_FLUID || type == C_BC || type == C_CGHOST) {
         Cell<M, ST> c;
         int conv;
-        assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+        // fluid cells of simple and streaming blocks have every source: the branch-free pull
+        if (bf != 0 && type == C_FLUID) gather_fast<M, ST, BX, BY, BZ>(L, a.rd[lev], l, nboff_s, a.m, c);
+        else assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
         const double V = double(1ll << (lev * M::D));
+        // per-cell sums in the arithmetic type of the stored values (the deviations f - w rho_ref
+        // of the weak models are small, so FP32 sums keep their absolute error far below the
+        // FP64 totals' rounding); the reference part rho_ref (sum w, sum w |xi|^2 / 2) is added in
+        // FP64, then the level's cell volume
+        using T = typename Store<ST>::T;
+        T s[5] = {0, 0, 0, 0, 0};
 #pragma unroll
         for (int q = 0; q < M::Q; ++q) {
-            const double fq = M::DEV ? (double)c.f[q] + M::w(q) * a.m.rho_ref : (double)c.f[q];
-            v[0] += fq;
-            v[1] += M::cx(q) * fq;
-            v[2] += M::cy(q) * fq;
-            v[3] += M::cz(q) * fq;
-            v[4] += 0.5 * double(M::cx(q) * M::cx(q) + M::cy(q) * M::cy(q) + M::cz(q) * M::cz(q)) * fq;
-            if constexpr (M::HAS_G) v[4] += 0.5 * (double)c.g[q];
+            const T fq = c.f[q];
+            s[0] += fq;
+            if (M::cx(q)) s[1] += T(M::cx(q)) * fq;
+            if (M::cy(q)) s[2] += T(M::cy(q)) * fq;
+            if (M::cz(q)) s[3] += T(M::cz(q)) * fq;
+            const int x2 = M::cx(q) * M::cx(q) + M::cy(q) * M::cy(q) + M::cz(q) * M::cz(q);
+            if (x2) s[4] += T(0.5 * x2) * fq;
+            if constexpr (M::HAS_G) s[4] += T(0.5) * c.g[q];
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = (double)s[j];
+        if constexpr (M::DEV) {
+            double e_ref = 0.0;
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q)
+                e_ref += 0.5 * M::w(q) * double(M::cx(q) * M::cx(q) + M::cy(q) * M::cy(q) + M::cz(q) * M::cz(q));
+            v[0] += a.m.rho_ref;
+            v[4] += a.m.rho_ref * e_ref;
         }
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] *= V;
@@ -712,17 +746,17 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_ledger(const StepArgs a, doubl
     ledger_block<M, ST, BX, BY, BZ>(a, blockIdx.x, partial);
 }
 
-static __global__ void __launch_bounds__(256) k_ledger_final(const double* partial, long long n, double* out) {
-    __shared__ double red[5][256];
+static __global__ void __launch_bounds__(1024) k_ledger_final(const double* partial, long long n, double* out) {
+    __shared__ double red[5][1024];
     const int l = threadIdx.x;
     double v[5] = {0, 0, 0, 0, 0};
-    for (long long i = l; i < n; i += 256)
+    for (long long i = l; i < n; i += 1024)
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] += partial[i * 5 + j];
 #pragma unroll
     for (int j = 0; j < 5; ++j) red[j][l] = v[j];
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    for (int s = 512; s > 0; s >>= 1) {
         if (l < s) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) red[j][l] += red[j][l + s];
@@ -861,7 +895,7 @@ struct Launch {
     }
     static void ledger(const StepArgs& a, long long nblocks, double* partial, double* out, cudaStream_t s) {
         if (nblocks) k_ledger<M, ST, BX, BY, BZ><<<(unsigned)nblocks, BX * BY * BZ, 0, s>>>(a, partial);
-        k_ledger_final<<<1, 256, 0, s>>>(partial, nblocks, out);
+        k_ledger_final<<<1, 1024, 0, s>>>(partial, nblocks, out);
     }
     static void init(const StepArgs& a, int lev, const double* r, const double* u, const double* t, cudaStream_t s) {
         if (!a.lv[lev].nb) return;
