@@ -375,6 +375,36 @@ def form_d2q37(args, stream, local):
     return out
 
 
+def form_d2q9(args, stream, local):
+    """D2Q9 recursive regularization on large periodic Taylor-Green domains (the paper's tree
+    benchmarks are D2Q9 at 2^13 x 2^13): a uniform 8192^2 grid and a 4096^2 coarse grid with its
+    central half refined once; FP32 and FP64 populations."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    out = {"bytes_per_update": {"f32": 72, "f64": 144}}
+    peak, kind = peaks()
+    s = 1 if args.scale == 1 else 4
+    cases = {f"uniform_{8192 // s}": (I.taylor_green_spec(8192 // s, 0, 0, 1), 8192 // s, 1),
+             f"two_level_{4096 // s}": (I.taylor_green_spec(4096 // s, 1024 // s, 3072 // s, 2), 4096 // s, 2)}
+    for name, (spec, nc, levels) in cases.items():
+        for st in ("f32", "f64"):
+            ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
+            ctx.configure(spec, "D2Q9", "rr", st, nu0=0.01 * 2 ** (levels - 1))
+            ctx.use_graph(True)
+            lv, xyz, _ = ctx.cells()
+            rho, u = I.taylor_green_fields(I.cell_centres(xyz[:, :2], lv), nc, levels, 0.05, 1.0 / 3.0)
+            ctx.init_fields(rho, u)
+            ctx.step(4)
+            upd = ctx.stats().cell_updates
+            K = 20
+            ms = _event_ms(stream, lambda: ctx.step(K)) / K
+            ctx.sync()
+            bpu = 72 if st == "f32" else 144
+            out[f"{name}_{st}"] = {"cells": int(lv.size), "ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS",
+                                   "hbm_frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind}
+            ctx.close()
+    return out
+
+
 def form_batched(args, stream, local):
     """48 uneven 2D cases (D2Q9 Taylor-Green and D2Q37 Sod tubes, 2-4 levels): one batched
     launch per lattice group per fine iteration (CUDA graph of the schedule period) against
@@ -529,7 +559,8 @@ def run_ours(args, world, rank, local):
         for name, fn in (("fp16_store", lambda: form_fp16(args, stream, local, t_max / args.steps)),
                          ("learned", lambda: form_learned(args, stream, local)),
                          ("batched", lambda: form_batched(args, stream, local)),
-                         ("d2q37_sod", lambda: form_d2q37(args, stream, local))):
+                         ("d2q37_sod", lambda: form_d2q37(args, stream, local)),
+                         ("d2q9_tg", lambda: form_d2q9(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -565,7 +596,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod", help="which forms to run (comma list)")
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg",
+                    help="which forms to run (comma list)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block", type=int, nargs=3, default=None)
     ap.add_argument("--variant", type=int, default=None)
