@@ -400,7 +400,7 @@ class Context:
     def moments(self, out=None):
         """(rho, u (dim, n), T) in lbm_cells order; ``out`` = preallocated (rho, u, T) float64
         arrays (for instance in pinned host memory) to write into."""
-        n = self.cells()[0].size
+        n = self.n_cells()
         if out is None:
             rho, u, T = np.empty(n), np.empty(self.dim * n), np.empty(n)
         else:
