@@ -675,7 +675,7 @@ __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, d
     constexpr int BS = BX * BY * BZ;
     __shared__ int nbr_s[27];
     __shared__ unsigned nboff_s[27];
-    __shared__ double red[5][BS];
+    __shared__ double red[5][BS / 32];
     long long b;
     const int lev = find_level(a, bid, &b);
     const LevelDev& L = a.lv[lev];
@@ -728,17 +728,22 @@ __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, d
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] *= V;
     }
+    // fixed-order tree: within each warp by shuffles, then the warps' sums in warp order
 #pragma unroll
-    for (int j = 0; j < 5; ++j) red[j][l] = v[j];
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    constexpr int NW = BS / 32;
+    if ((l & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) red[j][l >> 5] = v[j];
     __syncthreads();
-    for (int s = BS / 2; s > 0; s >>= 1) {
-        if (l < s) {
+    if (l < 5) {
+        double s = red[l][0];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) red[j][l] += red[j][l + s];
-        }
-        __syncthreads();
+        for (int w = 1; w < NW; ++w) s += red[l][w];
+        partial[bid * 5 + l] = s;
     }
-    if (l < 5) partial[bid * 5 + l] = red[l][0];
 }
 
 template <class M, int ST, int BX, int BY, int BZ>
