@@ -74,6 +74,16 @@ LBM_HD constexpr int d2q37_y(int q) {
     switch (q) { case 0: return -3; case 1: return -3; case 2: return -3; case 3: return -2; case 4: return -2; case 5: return -2; case 6: return -2; case 7: return -2; case 8: return -1; case 9: return -1; case 10: return -1; case 11: return -1; case 12: return -1; case 13: return -1; case 14: return -1; case 15: return 0; case 16: return 0; case 17: return 0; case 18: return 0; case 19: return 0; case 20: return 0; case 21: return 0; case 22: return 1; case 23: return 1; case 24: return 1; case 25: return 1; case 26: return 1; case 27: return 1; case 28: return 1; case 29: return 2; case 30: return 2; case 31: return 2; case 32: return 2; case 33: return 2; case 34: return 3; case 35: return 3; case 36: return 3; default: return 0; }
 }
 
+// the switch tables agree with the enumeration for every velocity (checked at compile time)
+LBM_HD constexpr bool tables_match() {
+    for (int q = 0; q < 21; ++q)
+        if (d2q21_x(q) != enum21(q, 0) || d2q21_y(q) != enum21(q, 1)) return false;
+    for (int q = 0; q < 37; ++q)
+        if (d2q37_x(q) != enum37(q, 0) || d2q37_y(q) != enum37(q, 1)) return false;
+    return true;
+}
+static_assert(tables_match(), "D2Q21/D2Q37 switch tables differ from the enumeration");
+
 template <int Q> struct Lat;
 
 template <> struct Lat<9> {
