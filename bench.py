@@ -375,6 +375,52 @@ def form_d2q37(args, stream, local):
     return out
 
 
+def form_sod_numerical(args, stream, local):
+    """The paper's compressible performance benchmark (Sec. 5, Sod tube, L = 2^13, single
+    precision): D2Q21 and D2Q37 DDF with the numerical equilibrium (8 constraints), FP32
+    populations and FP32 Newton (tolerance 1e-5, warm start), inviscid with the kinetic sensor
+    (A = 1.5), on the L x L domain uniform and with the refinement patches of Sec. 4.2 (band:
+    x/L in [1/4, 3/4); sqr: a centred square of side L/2; hori: the half y/L < 1/2); L counts
+    finest cells."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    L = 8192
+    grids = {"unif": I.sod_spec(L, L), "band": I.sod_spec(L, L, 2, (L // 4, 3 * L // 4)),
+             "sqr": I.GridSpec(2, (L, L), 2, [(0, (L // 4, L // 4), (3 * L // 4, 3 * L // 4))], (False, True),
+                               {"x-": ("neumann",), "x+": ("neumann",)}),
+             "hori": I.GridSpec(2, (L, L), 2, [(0, (0, 0), (L, L // 2))], (False, True),
+                                {"x-": ("neumann",), "x+": ("neumann",)})}
+    T0s = {"D2Q21": 0.9, "D2Q37": 1.0}           # inviscid reference temperatures of Sec. 4.2
+    out = {"workload": f"Sod shock tube on {L}x{L} (finest cells), (rho, p) = (1, 1) | (0.125, 0.1), "
+                       "T = T0 p / rho, Neumann ends, periodic across, inviscid, kinetic sensor A = 1.5",
+           "storage": "f32", "newton": "fp32, tol 1e-5, warm start", "unit": "MLUPS (cell updates per second)"}
+    for lat in (("D2Q21", "D2Q37") if args.sod_lattices == "all" else args.sod_lattices.split(",")):
+        for gname in (args.sod_grids.split(",")):
+            spec = grids[gname]
+            ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
+            ctx.configure(spec, lat, "num_ddf", "f32", nu0=0.0, T0=T0s[lat], sensor_A=1.5, newton_fp32=True)
+            ctx.use_graph(True)
+            lv, xyz, _ = ctx.cells()
+            rho, u, T = I.sod_fields(I.cell_centres(xyz[:, :2], lv), L, T0s[lat])
+            del xyz
+            ctx.init_fields(rho, u, T)
+            del rho, u, T
+            ctx.step(2)
+            st0 = ctx.stats()
+            K = 4
+            ms = _event_ms(stream, lambda: ctx.step(K)) / K
+            ctx.sync()
+            st1 = ctx.stats()
+            upd = st1.cell_updates
+            it = (st1.newton_iter_sum - st0.newton_iter_sum) / max(1, st1.newton_updates - st0.newton_updates)
+            out[f"{lat}_{gname}"] = {"cells": int(lv.size), "ms_per_step": ms, "value": upd / ms / 1e3,
+                                     "newton_iterations": it, "nonconverged": int(st1.newton_nonconverged)}
+            ctx.close()
+    out["paper_a100"] = {"note": "Sec. 5 table, A100-SXM4, other machine: context only",
+                         "D2Q21": {"unif": 618.5, "hori": 555.9, "band": 588.2, "sqr": 544.4},
+                         "D2Q37": {"unif (L = 2^12)": 286.9, "hori": 263.0, "band": 307.4, "sqr": 266.1}}
+    return out
+
+
 def form_d2q9(args, stream, local):
     """D2Q9 recursive regularization on large periodic Taylor-Green domains (the paper's tree
     benchmarks are D2Q9 at 2^13 x 2^13): a uniform 8192^2 grid and a 4096^2 coarse grid with its
@@ -560,7 +606,8 @@ def run_ours(args, world, rank, local):
                          ("learned", lambda: form_learned(args, stream, local)),
                          ("batched", lambda: form_batched(args, stream, local)),
                          ("d2q37_sod", lambda: form_d2q37(args, stream, local)),
-                         ("d2q9_tg", lambda: form_d2q9(args, stream, local))):
+                         ("d2q9_tg", lambda: form_d2q9(args, stream, local)),
+                         ("sod_numerical", lambda: form_sod_numerical(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -597,7 +644,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
     ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg",
-                    help="which forms to run (comma list)")
+                    help="which forms to run (comma list; sod_numerical is the paper's Sec. 5 Sod benchmark)")
+    ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
+    ap.add_argument("--sod-grids", default="unif,band,sqr,hori", help="sod_numerical: grids")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block", type=int, nargs=3, default=None)
     ap.add_argument("--variant", type=int, default=None)

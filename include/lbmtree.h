@@ -52,7 +52,7 @@ extern "C" {
 /* Collision models (Appendix A): BGK and recursive regularization with the Hermite equilibrium
  * of Eq. GenEq (weakly compressible); compressible polyatomic DDF (Eqs. gEq, polyTemp) with the
  * thermal polynomial equilibrium (D2Q37) or with the numerical max-entropy equilibrium of
- * Eq. exponential solved by Newton-Raphson in FP64 (D2Q21). */
+ * Eq. exponential solved by Newton-Raphson in FP64 or FP32 (D2Q21 and D2Q37, Sec. 4.2). */
 #define LBM_BGK             1
 #define LBM_RR              2
 #define LBM_COMP_POLY       3
@@ -311,12 +311,13 @@ typedef struct {
 } lbm_mlp_train_params;
 
 /* Train the context's network on n device samples: uT[n*3] = (u_x, u_y, T) and the converged
- * multipliers lambda[n*8] (for instance from lbm_newton_batch).  m and s are the per-output
+ * multipliers lambda[n*8] (for instance from lbm_newton_batch); the context's model must be
+ * LBM_COMP_NUMERICAL (D2Q21 or D2Q37).  m and s are the per-output
  * mean and standard deviation of lambda; training minimises the loss of lbm_mlp_grad on
  * (lambda - m)/s with the project's kernels; the context then uses the network for
  * LBM_GUESS_MLP.  Allocates temporary device memory; synchronous with the context's stream. */
 int lbm_mlp_train(lbm_ctx* ctx, const double* d_uT, const double* d_lambda, int64_t n, lbm_mlp_train_params* p);
-/* Batched equilibrium solve of the context's model (D2Q21 numerical): samples uT[n*3] =
+/* Batched FP64 equilibrium solve of the context's numerical model (D2Q21 or D2Q37): samples uT[n*3] =
  * (u_x, u_y, T) on the device, guess ZERO, POLY or MLP; writes lambda[n*8] and the Newton
  * iterations per sample (-1 if not converged) on the context's stream. */
 int lbm_newton_batch(lbm_ctx* ctx, const double* d_uT, int64_t n, int guess, double* d_lambda, int* d_iters);

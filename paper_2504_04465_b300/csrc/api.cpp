@@ -66,7 +66,7 @@ bool find_kernels(int lattice, int model, int storage, const int* blk, bool newt
     switch (lattice) {
         case LBM_D2Q9: return find_kernels_d2q9(model, storage, blk, out);
         case LBM_D3Q27: return find_kernels_d3q27(model, storage, blk, out);
-        case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, out);
+        case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, newton_fp32, out);
         case LBM_D2Q21: return find_kernels_d2q21(model, storage, blk, newton_fp32, out);
     }
     return false;
@@ -578,7 +578,7 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     const bool weak = c->model == LBM_BGK || c->model == LBM_RR;
     if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27)) ||
         (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
-        (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21))
+        (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21 && c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
     if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
@@ -853,7 +853,7 @@ int lbm_mlp_train(lbm_ctx* c, const double* d_uT, const double* d_lambda, int64_
     if (!d_uT || !d_lambda || !p || n <= 0) return fail(LBM_ERR_ARG, "bad arguments");
     if (p->steps < 1 || p->batch < 1 || !(p->lr > 0) || p->lr_final < 0) return fail(LBM_ERR_ARG, "bad training parameters");
     if (c->host_only) return fail(LBM_ERR_STATE, "host-only context");
-    if (c->model != LBM_COMP_NUMERICAL || c->lattice != LBM_D2Q21) return fail(LBM_ERR_UNSUPPORTED, "needs the D2Q21 numerical model");
+    if (c->model != LBM_COMP_NUMERICAL) return fail(LBM_ERR_UNSUPPORTED, "needs a numerical-equilibrium model");
     CU(cudaSetDevice(c->device));
     const int np = lbm_mlp_nparams();
     if (!c->d_mlp && cudaMalloc(&c->d_mlp, np * sizeof(float)) != cudaSuccess) {
@@ -878,7 +878,7 @@ int lbm_newton_batch(lbm_ctx* c, const double* d_uT, int64_t n, int guess, doubl
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (!d_uT || !d_lambda || !d_iters || n < 0) return fail(LBM_ERR_ARG, "bad arguments");
     if (c->host_only || !c->built) return fail(LBM_ERR_STATE, "grid not built on a device");
-    if (c->model != LBM_COMP_NUMERICAL || c->lattice != LBM_D2Q21) return fail(LBM_ERR_UNSUPPORTED, "needs the D2Q21 numerical model");
+    if (c->model != LBM_COMP_NUMERICAL) return fail(LBM_ERR_UNSUPPORTED, "needs a numerical-equilibrium model");
     if (guess < LBM_GUESS_ZERO || guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "guess must be ZERO, POLY or MLP");
     if (guess == LBM_GUESS_MLP && !c->d_mlp) return fail(LBM_ERR_STATE, "no network set");
     CU(cudaSetDevice(c->device));
@@ -886,7 +886,8 @@ int lbm_newton_batch(lbm_ctx* c, const double* d_uT, int64_t n, int guess, doubl
     fill_args(c, a);
     ModelDev m = a.m;
     m.guess = guess;
-    launch_newton_batch_d2q21(d_uT, n, m, d_lambda, d_iters, c->stream);
+    if (c->lattice == LBM_D2Q37) launch_newton_batch_d2q37(d_uT, n, m, d_lambda, d_iters, c->stream);
+    else launch_newton_batch_d2q21(d_uT, n, m, d_lambda, d_iters, c->stream);
     CU(cudaGetLastError());
     return LBM_OK;
 }

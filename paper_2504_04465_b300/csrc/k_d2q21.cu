@@ -21,81 +21,13 @@ template <typename R>
 __device__ __forceinline__ void poly_guess21(R ux, R uy, R Tt, R* lam) {
     R a[15];
     thermal_moments<R>(R(1), ux, uy, Tt - R(2.0 / 3.0), 3, a);
-    R A[36], b[8];
-#pragma unroll
-    for (int k = 0; k < 36; ++k) A[k] = R(0);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) b[k] = R(0);
-#pragma unroll
-    for (int q = 0; q < 21; ++q) {
+    poly_guess_fit<21, R>(ux, uy, Tt, [&](int q, R& w) {
         R s = R(0);
 #pragma unroll
         for (int k = 0; k < 10; ++k) s += (sizeof(R) == 4 ? R(cH21f[q][k]) : R(cH21[q][k])) * a[k];
-        const R w = sizeof(R) == 4 ? R(cw21f[q]) : R(cw21[q]);
-        const R fp = w * s;
-        if (fp > R(0)) {
-            const R y = R(-1) - r_log(fp);
-            int k = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                b[i] += w * R(MB<21>::m(q, i)) * y;
-#pragma unroll
-                for (int j = 0; j <= i; ++j) A[k++] += w * R(MB<21>::m(q, i) * MB<21>::m(q, j));
-            }
-        }
-    }
-    R fit[8];
-    chol8_solve<R>(A, b, fit);
-    // keep the fit where it is finite and closer to the root than lambda = 0 (at large |u| or T
-    // far from the lattice temperature the truncated polynomial is a poor start)
-    const R u2 = ux * ux + uy * uy, t2 = u2 + R(4) * Tt;
-    const R tgt[8] = {R(1), ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
-    bool fin = true;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) fin = fin && r_finite(fit[a]);
-    R e[21], G[8], gf = R(0), g0 = R(0);
-    if (fin) {
-        newton_eval<21, R>(fit, tgt, e, G);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) gf += G[a] * G[a];
-        const R zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        newton_eval<21, R>(zero, tgt, e, G);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
-    }
-    const bool keep = fin && (gf < g0);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) lam[a] = keep ? fit[a] : R(0);
-}
-
-// network guess lambda0 = m + s * y(u_x, u_y, T/T0 - 1), evaluated without per-thread arrays in
-// memory: layer-1 units one at a time into 64 layer-2 accumulators (same summation order as the
-// training kernels' forward pass)
-template <typename R>
-__device__ __forceinline__ void mlp_guess21(const ModelDev& m, R ux, R uy, R Tt, R* lam) {
-    const float* P = m.mlp;
-    const float x0 = (float)ux, x1 = (float)uy, x2 = (float)((double)Tt / m.T0 - 1.0);
-    float acc[MLP_H];
-#pragma unroll
-    for (int j = 0; j < MLP_H; ++j) acc[j] = __ldg(P + MLP_B2 + j);
-#pragma unroll 1
-    for (int i = 0; i < MLP_H; ++i) {
-        const float h1 = tanhf(fmaf(__ldg(P + MLP_W1 + 3 * i), x0, fmaf(__ldg(P + MLP_W1 + 3 * i + 1), x1,
-                               fmaf(__ldg(P + MLP_W1 + 3 * i + 2), x2, __ldg(P + MLP_B1 + i)))));
-#pragma unroll
-        for (int j = 0; j < MLP_H; ++j) acc[j] = fmaf(__ldg(P + MLP_W2 + MLP_H * j + i), h1, acc[j]);
-    }
-    float y[MLP_OUT];
-#pragma unroll
-    for (int o = 0; o < MLP_OUT; ++o) y[o] = __ldg(P + MLP_B3 + o);
-#pragma unroll
-    for (int j = 0; j < MLP_H; ++j) {
-        const float h2 = tanhf(acc[j]);
-#pragma unroll
-        for (int o = 0; o < MLP_OUT; ++o) y[o] = fmaf(__ldg(P + MLP_W3 + MLP_H * o + j), h2, y[o]);
-    }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) lam[a] = R(m.mlp_m[a] + m.mlp_s[a] * (double)y[a]);
+        w = sizeof(R) == 4 ? R(cw21f[q]) : R(cw21[q]);
+        return w * s;
+    }, lam);
 }
 
 // N32: Newton in FP32 (the multipliers stay FP64 between steps), else FP64
@@ -127,7 +59,7 @@ struct D2Q21M {
         } else if (m.guess == 2) {
             poly_guess21<R>(R(ux), R(uy), R(Tt), l);
         } else if (m.guess == 3) {
-            mlp_guess21<R>(m, R(ux), R(uy), R(Tt), l);
+            mlp_guess<R>(m.mlp, m.T0, m.mlp_m, m.mlp_s, R(ux), R(uy), R(Tt), l);
         } else {
 #pragma unroll
             for (int a = 0; a < 8; ++a) l[a] = R(lam[a]);
@@ -151,7 +83,7 @@ __global__ void __launch_bounds__(128) k_newton_batch(const double* __restrict__
     const double ux = uT[3 * i], uy = uT[3 * i + 1], Tt = uT[3 * i + 2];
     double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (m.guess == 2) poly_guess21<double>(ux, uy, Tt, lam);
-    else if (m.guess == 3) mlp_guess21<double>(m, ux, uy, Tt, lam);
+    else if (m.guess == 3) mlp_guess<double>(m.mlp, m.T0, m.mlp_m, m.mlp_s, ux, uy, Tt, lam);
     double e[21];
     int conv = 0;
     const int it = newton_solve<21>(ux, uy, Tt, lam, e, m.newton_tol, m.newton_max_iter, &conv);

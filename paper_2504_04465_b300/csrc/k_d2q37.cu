@@ -3,7 +3,10 @@
 // expansion of Eq. GenEq to 4th order about theta = c_s^2 of the lattice with the thermal
 // moments of models_comp.cuh: f_eq,i = w_i sum_k H37[i][k] a_k, where H37[i][k] holds
 // h_a(xi_x) h_b(xi_y) / (a! b! theta^(a+b)) for component k = (a, b) (weights.cpp).
+#include <type_traits>
+
 #include "kernels_impl.cuh"
+#include "mlp.cuh"
 
 namespace lbm {
 
@@ -49,8 +52,94 @@ struct D2Q37M {
     __device__ static void init_guess(double, double, double, double*) {}
 };
 
-bool find_kernels_d2q37(int model, int storage, const int* blk, KernelSet& out) {
-    if (model == 3 && blk[0] == 16 && blk[1] == 16 && blk[2] == 1) return pick_storage<D2Q37M, 16, 16, 1>(storage, out);
+// ---------------------------------------------------------------- numerical equilibrium
+// The max-entropy equilibrium of Eq. exponential on D2Q37 (the paper's lattice for Mach 1.75 to
+// 2.5): the same eight constraints and Newton solve as D2Q21, the polynomial guess fitted to the
+// 4th-order thermal Hermite equilibrium about c_s^2 of D2Q37 (positive populations only, kept
+// where it beats lambda = 0), the learned guess evaluated like D2Q21's.
+template <typename R>
+__device__ __forceinline__ void poly_guess37(R ux, R uy, R Tt, R* lam) {
+    constexpr bool F = sizeof(R) == 4;
+    R a[15];
+    thermal_moments<R>(R(1), ux, uy, Tt - (F ? R(ccs2_37f) : R(ccs2_37)), 4, a);
+    poly_guess_fit<37, R>(ux, uy, Tt, [&](int q, R& w) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) s += (F ? R(cH37f[q][k]) : R(cH37[q][k])) * a[k];
+        w = F ? R(cw37f[q]) : R(cw37[q]);
+        return w * s;
+    }, lam);
+}
+
+template <bool N32>
+struct D2Q37N {
+    static constexpr int D = 2, Q = 37;
+    static constexpr int MINB_FAST = 2, MINB_GEN = 2;
+    static constexpr bool TUNE = false;
+    static constexpr bool BATCH = false;
+    static constexpr bool DEV = false;
+    static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
+    __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }
+    __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __device__ static double w(int q) { return cw37[q]; }
+    __device__ static float wf(int q) { return cw37f[q]; }
+    __device__ static float inv_wf(int q) { return cinvw37f[q]; }
+    template <int ST>
+    __device__ static void feq(const ModelDev& m, typename Store<ST>::T rho, typename Store<ST>::T ux,
+                               typename Store<ST>::T uy, typename Store<ST>::T Tt, double* lam,
+                               typename Store<ST>::T* f, int* iters, int* conv) {
+        using T = typename Store<ST>::T;
+        using R = typename std::conditional<N32, float, double>::type;
+        R l[8];
+        if (m.guess == 1) {
+#pragma unroll
+            for (int a2 = 0; a2 < 8; ++a2) l[a2] = R(0);
+        } else if (m.guess == 2) {
+            poly_guess37<R>(R(ux), R(uy), R(Tt), l);
+        } else if (m.guess == 3) {
+            mlp_guess<R>(m.mlp, m.T0, m.mlp_m, m.mlp_s, R(ux), R(uy), R(Tt), l);
+        } else {
+#pragma unroll
+            for (int a2 = 0; a2 < 8; ++a2) l[a2] = R(lam[a2]);
+        }
+        R e[37];
+        if constexpr (N32) *iters = newton_solve_inl<37, float>(R(ux), R(uy), R(Tt), l, e, R(m.newton_tol), m.newton_max_iter, conv);
+        else *iters = newton_solve<37>(R(ux), R(uy), R(Tt), l, e, R(m.newton_tol), m.newton_max_iter, conv);
+#pragma unroll
+        for (int a2 = 0; a2 < 8; ++a2) lam[a2] = double(l[a2]);
+#pragma unroll
+        for (int q = 0; q < 37; ++q) f[q] = T(R(rho) * e[q]);
+    }
+    __device__ static void init_guess(double ux, double uy, double Tt, double* lam) { poly_guess37<double>(ux, uy, Tt, lam); }
+};
+
+// batched equilibrium solve: samples (u_x, u_y, T), guess 1 zero, 2 polynomial, 3 network
+__global__ void __launch_bounds__(128) k_newton_batch37(const double* __restrict__ uT, long long n, ModelDev m,
+                                                        double* __restrict__ lam_out, int* __restrict__ iters) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double ux = uT[3 * i], uy = uT[3 * i + 1], Tt = uT[3 * i + 2];
+    double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (m.guess == 2) poly_guess37<double>(ux, uy, Tt, lam);
+    else if (m.guess == 3) mlp_guess<double>(m.mlp, m.T0, m.mlp_m, m.mlp_s, ux, uy, Tt, lam);
+    double e[37];
+    int conv = 0;
+    const int it = newton_solve<37>(ux, uy, Tt, lam, e, m.newton_tol, m.newton_max_iter, &conv);
+#pragma unroll
+    for (int a2 = 0; a2 < 8; ++a2) lam_out[8 * i + a2] = lam[a2];
+    iters[i] = conv ? it : -1;
+}
+
+void launch_newton_batch_d2q37(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s) {
+    if (n) k_newton_batch37<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(uT, n, m, lam, iters);
+}
+
+bool find_kernels_d2q37(int model, int storage, const int* blk, bool newton_fp32, KernelSet& out) {
+    if (blk[0] != 16 || blk[1] != 16 || blk[2] != 1) return false;
+    if (model == 4) return newton_fp32 ? pick_storage<D2Q37N<true>, 16, 16, 1>(storage, out)
+                                       : pick_storage<D2Q37N<false>, 16, 16, 1>(storage, out);
+    if (model == 3) return pick_storage<D2Q37M, 16, 16, 1>(storage, out);
     return false;
 }
 

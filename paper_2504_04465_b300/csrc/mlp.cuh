@@ -36,4 +36,34 @@ __device__ __forceinline__ void mlp_eval(const float* P, float x0, float x1, flo
     }
 }
 
+// network guess lambda0 = m + s * y(u_x, u_y, T/T0 - 1) for the Newton solve, evaluated without
+// per-thread arrays in memory: layer-1 units one at a time into 64 layer-2 accumulators (same
+// summation order as mlp_eval).  P holds bf16-rounded weights; mm, ms the output scaling.
+template <typename R>
+__device__ __forceinline__ void mlp_guess(const float* P, double T0, const double* mm, const double* ms,
+                                          R ux, R uy, R Tt, R* lam) {
+    const float x0 = (float)ux, x1 = (float)uy, x2 = (float)((double)Tt / T0 - 1.0);
+    float acc[MLP_H];
+#pragma unroll
+    for (int j = 0; j < MLP_H; ++j) acc[j] = __ldg(P + MLP_B2 + j);
+#pragma unroll 1
+    for (int i = 0; i < MLP_H; ++i) {
+        const float h1 = tanhf(fmaf(__ldg(P + MLP_W1 + 3 * i), x0, fmaf(__ldg(P + MLP_W1 + 3 * i + 1), x1,
+                               fmaf(__ldg(P + MLP_W1 + 3 * i + 2), x2, __ldg(P + MLP_B1 + i)))));
+#pragma unroll
+        for (int j = 0; j < MLP_H; ++j) acc[j] = fmaf(__ldg(P + MLP_W2 + MLP_H * j + i), h1, acc[j]);
+    }
+    float y[MLP_OUT];
+#pragma unroll
+    for (int o = 0; o < MLP_OUT; ++o) y[o] = __ldg(P + MLP_B3 + o);
+#pragma unroll
+    for (int j = 0; j < MLP_H; ++j) {
+        const float h2 = tanhf(acc[j]);
+#pragma unroll
+        for (int o = 0; o < MLP_OUT; ++o) y[o] = fmaf(__ldg(P + MLP_W3 + MLP_H * o + j), h2, y[o]);
+    }
+#pragma unroll
+    for (int a = 0; a < MLP_OUT; ++a) lam[a] = R(mm[a] + ms[a] * (double)y[a]);
+}
+
 }  // namespace lbm

@@ -244,4 +244,51 @@ __device__ __forceinline__ int newton_solve_inl(R ux, R uy, R Tt, R* lam, R* e, 
     return it;
 }
 
+// Polynomial Newton guess: weighted least-squares fit of -1 - ln f_poly onto the eight basis
+// functions over the populations with f_poly > 0 (weights w_i), kept only where it is finite and
+// closer to the root than lambda = 0.  fpoly(q, &w) returns f_poly,i (rho = 1) and sets w = w_i.
+template <int Q, typename R, typename FP>
+__device__ __forceinline__ void poly_guess_fit(R ux, R uy, R Tt, FP fpoly, R* lam) {
+    R A[36], b[8];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = R(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        R w;
+        const R fp = fpoly(q, w);
+        if (fp > R(0)) {
+            const R y = R(-1) - r_log(fp);
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                b[i] += w * R(MB<Q>::m(q, i)) * y;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) A[k++] += w * R(MB<Q>::m(q, i) * MB<Q>::m(q, j));
+            }
+        }
+    }
+    R fit[8];
+    chol8_solve<R>(A, b, fit);
+    const R u2 = ux * ux + uy * uy, t2 = u2 + R(4) * Tt;
+    const R tgt[8] = {R(1), ux, uy, ux * ux + Tt, ux * uy, uy * uy + Tt, ux * t2, uy * t2};
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fin = fin && r_finite(fit[a]);
+    R e[Q], G[8], gf = R(0), g0 = R(0);
+    if (fin) {
+        newton_eval<Q, R>(fit, tgt, e, G);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) gf += G[a] * G[a];
+        const R zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        newton_eval<Q, R>(zero, tgt, e, G);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) g0 += G[a] * G[a];
+    }
+    const bool keep = fin && (gf < g0);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) lam[a] = keep ? fit[a] : R(0);
+}
+
 }  // namespace lbm

@@ -122,6 +122,23 @@ def test_velocity_sets_match_oracle(lt):
         assert np.array_equal(xi[::-1], -xi)          # opposite of q is Q-1-q
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_numerical_equilibrium_lattices(lt, storage, fp32):
+    """The numerical equilibrium is built on D2Q21 and D2Q37 (Sec. 4.2), for either Newton
+    precision; the weakly compressible lattices refuse it."""
+    for latname in ("D2Q21", "D2Q37"):
+        c = lt.Context(2, device=-1)
+        c.configure(I.GridSpec(2, (32, 32), 1, [], (True, True)), latname, "num_ddf", storage, T0=0.9,
+                    newton_fp32=fp32)
+        assert c.n_cells() == 32 * 32
+    c = lt.Context(2, device=-1)
+    with pytest.raises(lt.LbmError) as e:
+        c.configure(I.GridSpec(2, (32, 32), 1, [], (True, True)), "D2Q9", "num_ddf", storage, T0=0.9,
+                    newton_fp32=fp32)
+    assert lt.ERR[e.value.code] == "UNSUPPORTED"
+
+
 def test_batch_needs_initialised_device_contexts(lt):
     ctx = lt.Context(2, device=-1)
     ctx.configure(I.taylor_green_spec(32, 8, 24, 2), "D2Q9", "rr", "f64", nu0=0.02)

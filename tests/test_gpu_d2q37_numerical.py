@@ -1,0 +1,117 @@
+"""D2Q37 compressible DDF with the numerical (max-entropy) equilibrium of Eq. exponential against
+the FP64 oracle: the lattice the paper pairs with that equilibrium for its supersonic airfoil
+runs (Sec. 4.2, Mach 1.75 to 2.5) and benchmarks on the Sod tube (Sec. 5).
+
+Tolerances: FP64 populations with FP64 Newton agree to 1e-12 relative (rounding order only);
+FP32 populations with FP64 Newton to the FP32 rounding of 37-term moment sums accumulated over
+the run (1e-5 for rho and T, 1e-4 for u, whose scale is ~0.1); FP32 Newton stops at an absolute
+residual of 1e-5 on the moment constraints, which moves u by up to ~1e-5 against |u| ~ 0.1
+(stated bounds 1e-4 for rho and T, 5e-4 for u)."""
+from __future__ import annotations
+
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+from oracle import lattices as L
+from oracle import numerical as nm
+from paper_2504_04465_b300 import inputs as I
+from tests import harness as H
+from tests.test_gpu_parity import SOD_SPEC
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# Sec. 4.2: T0 = 1.0 for inviscid runs on D2Q37, 0.4 for viscous ones
+T0_INV, T0_VISC = 1.0, 0.4
+N37_SPEC = I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True))
+
+
+@lru_cache(maxsize=None)
+def sod_oracle():
+    return H.run_oracle(SOD_SPEC, "D2Q37", "num_ddf", H.sod_fields(256, T0_INV), 20, nu0=0.0, T0=T0_INV,
+                        sensor_A=1.5)
+
+
+@lru_cache(maxsize=None)
+def smooth_oracle():
+    return H.run_oracle(N37_SPEC, "D2Q37", "num_ddf", H.smooth_comp_fields((96, 64), T0_VISC), 20, nu0=0.01,
+                        T0=T0_VISC, sensor_A=1.35)
+
+
+def test_sod_band_f64():
+    sol = sod_oracle()
+    ctx = H.make_gpu(SOD_SPEC, "D2Q37", "num_ddf", "f64", H.sod_fields(256, T0_INV), nu0=0.0, T0=T0_INV,
+                     sensor_A=1.5)
+    ctx.step_fine(20)
+    err = H.compare_moments(sol, ctx)
+    print("d2q37 numerical sod f64", err)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    s = ctx.stats()
+    assert s.newton_updates > 0 and s.newton_nonconverged == 0
+    ctx.close()
+
+
+def test_two_level_viscous_f64():
+    sol = smooth_oracle()
+    ctx = H.make_gpu(N37_SPEC, "D2Q37", "num_ddf", "f64", H.smooth_comp_fields((96, 64), T0_VISC), nu0=0.01,
+                     T0=T0_VISC, sensor_A=1.35)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    print("d2q37 numerical two-level f64", err)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    ctx.close()
+
+
+def test_two_level_viscous_f32_populations():
+    sol = smooth_oracle()
+    ctx = H.make_gpu(N37_SPEC, "D2Q37", "num_ddf", "f32", H.smooth_comp_fields((96, 64), T0_VISC), nu0=0.01,
+                     T0=T0_VISC, sensor_A=1.35)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    print("d2q37 numerical two-level f32", err)
+    assert err["rho"] < 1e-5 and err["u"] < 1e-4 and err["T"] < 1e-5, err
+    ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_two_level_viscous_fp32_newton(storage):
+    sol = smooth_oracle()
+    ctx = H.make_gpu(N37_SPEC, "D2Q37", "num_ddf", storage, H.smooth_comp_fields((96, 64), T0_VISC), nu0=0.01,
+                     T0=T0_VISC, sensor_A=1.35, newton_fp32=True)
+    ctx.step(10)
+    err = H.compare_moments(sol, ctx)
+    print("d2q37 numerical fp32 newton", storage, err)
+    assert err["rho"] < 1e-4 and err["u"] < 5e-4 and err["T"] < 1e-4, err
+    assert ctx.stats().newton_nonconverged == 0
+    ctx.close()
+
+
+def test_batched_newton_matches_oracle():
+    """The batched FP64 solve on D2Q37 from the polynomial and the zero guess reaches the
+    oracle's root; samples span the paper's D2Q37 range (|u| up to ~1.2, T within 40 % of T0)."""
+    rng = np.random.default_rng(37)
+    n = 4096
+    sp = rng.uniform(0.0, 1.2, n)
+    ang = rng.uniform(0.0, 2 * np.pi, n)
+    uT = np.stack([sp * np.cos(ang), sp * np.sin(ang), T0_INV * rng.uniform(0.6, 1.4, n)], axis=1)
+    ctx = H.make_gpu(N37_SPEC, "D2Q37", "num_ddf", "f64", H.smooth_comp_fields((96, 64), T0_INV), nu0=0.01,
+                     T0=T0_INV, sensor_A=1.35)
+    d_uT = torch.tensor(uT, dtype=torch.float64, device="cuda")
+    lat = L.LATTICES["D2Q37"]
+    sel = np.arange(0, n, 16)
+    u, T = uT[sel, :2].T, uT[sel, 2]
+    lam_o, _, it_o, conv_o = nm.newton(lat, u, T, nm.poly_guess(lat, u, T, 4), 1e-12, 50)
+    assert conv_o.all()
+    for guess in ("poly", "zero"):
+        d_lam = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+        d_it = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.newton_batch(d_uT.data_ptr(), n, guess, d_lam.data_ptr(), d_it.data_ptr())
+        ctx.sync()
+        it = d_it.cpu().numpy()
+        assert (it >= 0).all(), guess
+        assert np.abs(d_lam.cpu().numpy()[sel] - lam_o.T).max() < 1e-9, guess
+        if guess == "poly":
+            assert abs(it[sel].mean() - it_o.mean()) < 0.05
+    ctx.close()
