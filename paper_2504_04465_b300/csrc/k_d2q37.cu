@@ -74,7 +74,8 @@ __device__ __forceinline__ void poly_guess37(R ux, R uy, R Tt, R* lam) {
 template <bool N32>
 struct D2Q37N {
     static constexpr int D = 2, Q = 37;
-    static constexpr int MINB_FAST = 2, MINB_GEN = 2;
+    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
+    static constexpr int MINB_FAST = N32 ? 4 : 2, MINB_GEN = 2;
     static constexpr bool TUNE = false;
     static constexpr bool BATCH = false;
     static constexpr bool DEV = false;
