@@ -9,6 +9,7 @@
 // FP64, or FP32 when selected (step d = (sum e M M^T)^-1 G by Cholesky, backtracking halving of
 // the step until ||G||_2 decreases, at most 30 halvings, stop when max |G| < tol).
 #pragma once
+#include <utility>
 #include "device_common.cuh"
 
 namespace lbm {
@@ -61,6 +62,18 @@ __device__ __forceinline__ T sensor_alpha(T eps, T tau, T A) {
 }
 
 // ------------------------------------------------------------------ Newton (FP64)
+// f(integral_constant<int, 0>) ... f(integral_constant<int, N - 1>): the velocity index is a
+// compile-time constant in every instance, so the monomials fold to constants and the
+// per-velocity arrays stay in registers however large the body is
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 template <int Q> struct MB {
     // raw monomials 1, x, y, xx, xy, yy, x r2, y r2 of velocity q
     __host__ __device__ static constexpr double m(int q, int a) {
@@ -74,15 +87,15 @@ template <int Q, typename R = double>
 __device__ __forceinline__ void newton_eval(const R* lam, const R* tgt, R* e, R* G) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) G[a] = -tgt[a];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         R s = R(1);
 #pragma unroll
         for (int a = 0; a < 8; ++a) s += lam[a] * R(MB<Q>::m(q, a));
         e[q] = r_exp(-s);
 #pragma unroll
         for (int a = 0; a < 8; ++a) G[a] += e[q] * R(MB<Q>::m(q, a));
-    }
+    });
 }
 
 // Cholesky solve of the packed SPD system A d = G (A lower triangle, row-major packed)
@@ -125,14 +138,14 @@ __device__ __forceinline__ void newton_dir(const R* e, const R* G, R* d) {
     R A[36];
 #pragma unroll
     for (int k = 0; k < 36; ++k) A[k] = R(0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         int k = 0;
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b <= a; ++b) A[k++] += e[q] * R(MB<Q>::m(q, a) * MB<Q>::m(q, b));
-    }
+    });
     chol8_solve<R>(A, G, d);
 }
 
@@ -254,8 +267,8 @@ __device__ __forceinline__ void poly_guess_fit(R ux, R uy, R Tt, FP fpoly, R* la
     for (int k = 0; k < 36; ++k) A[k] = R(0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) b[k] = R(0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         R w;
         const R fp = fpoly(q, w);
         if (fp > R(0)) {
@@ -268,7 +281,7 @@ __device__ __forceinline__ void poly_guess_fit(R ux, R uy, R Tt, FP fpoly, R* la
                 for (int j = 0; j <= i; ++j) A[k++] += w * R(MB<Q>::m(q, i) * MB<Q>::m(q, j));
             }
         }
-    }
+    });
     R fit[8];
     chol8_solve<R>(A, b, fit);
     const R u2 = ux * ux + uy * uy, t2 = u2 + R(4) * Tt;
