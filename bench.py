@@ -303,11 +303,12 @@ def form_learned(args, stream, local):
         held[g] = {"mean_iters": float(it[it >= 0].mean()) if (it >= 0).any() else None,
                    "nonconverged": int((it < 0).sum()),
                    "max_abs_dlambda_vs_zero_guess": float(np.abs(d_l.cpu().numpy() - lam_ref[ntr:]).max())}
-    def timed_runs(K):
+    def timed_runs(K, tune):
         out = {}
         for g in ("poly", "mlp", "warm"):
             ctx.set_guess(g)
             ctx.step(1)
+            v = ctx.autotune(1)[0] if tune else 0     # occupancy variant for this guess
             s0 = ctx.stats()
             ms = _event_ms(stream, lambda: ctx.step(K)) / K
             ctx.sync()
@@ -315,14 +316,15 @@ def form_learned(args, stream, local):
             out[g] = {"ms_per_step": ms, "value": s1.cell_updates / ms / 1e3, "unit": "MLUPS",
                       "mean_newton_iters": (s1.newton_iter_sum - s0.newton_iter_sum) /
                       max(1, s1.newton_updates - s0.newton_updates),
-                      "nonconverged": s1.newton_nonconverged - s0.newton_nonconverged}
+                      "nonconverged": s1.newton_nonconverged - s0.newton_nonconverged,
+                      "variant_min_blocks": ctx.variants()[v]}
         return out
 
-    runs = timed_runs(1)
+    runs = timed_runs(1, False)
     # the same comparison with the solve on the FP32 pipe (tolerance 1e-5)
     ctx.set_newton_precision(True, 1e-5)
     try:
-        runs32 = timed_runs(3)
+        runs32 = timed_runs(3, True)
         fp32 = {"tol": 1e-5, "by_guess": runs32,
                 "speedup_mlp_vs_poly": runs32["poly"]["ms_per_step"] / runs32["mlp"]["ms_per_step"],
                 "speedup_vs_fp64_warm": runs["warm"]["ms_per_step"] / runs32["warm"]["ms_per_step"]}
@@ -405,6 +407,7 @@ def form_sod_numerical(args, stream, local):
             ctx.init_fields(rho, u, T)
             del rho, u, T
             ctx.step(2)
+            v, tune_ms = ctx.autotune(2)                # occupancy variant of the step kernels
             st0 = ctx.stats()
             K = 4
             ms = _event_ms(stream, lambda: ctx.step(K)) / K
@@ -413,7 +416,9 @@ def form_sod_numerical(args, stream, local):
             upd = st1.cell_updates
             it = (st1.newton_iter_sum - st0.newton_iter_sum) / max(1, st1.newton_updates - st0.newton_updates)
             out[f"{lat}_{gname}"] = {"cells": int(lv.size), "ms_per_step": ms, "value": upd / ms / 1e3,
-                                     "newton_iterations": it, "nonconverged": int(st1.newton_nonconverged)}
+                                     "newton_iterations": it, "nonconverged": int(st1.newton_nonconverged),
+                                     "variant_min_blocks": ctx.variants()[v],
+                                     "autotune_ms": dict(zip(map(str, ctx.variants()), tune_ms))}
             ctx.close()
     out["paper_a100"] = {"note": "Sec. 5 table, A100-SXM4, other machine: context only",
                          "D2Q21": {"unif": 618.5, "hori": 555.9, "band": 588.2, "sqr": 544.4},

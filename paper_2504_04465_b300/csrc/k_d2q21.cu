@@ -36,7 +36,11 @@ struct D2Q21M {
     static constexpr int D = 2, Q = 21;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = N32 ? 4 : 2, MINB_GEN = 2;
-    static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
+    // compile occupancy variants for the autotuner: a warm start (few iterations) runs fastest
+    // at 32 resident warps, the polynomial and network guesses at 16 (their state spills below
+    // 128 registers)
+    static constexpr bool TUNE = N32;
+    static constexpr int TUNE_V[3] = {62, 82, 84};   // their targets, 10 * interior + general
     static constexpr bool BATCH = false;  // compile the batched multi-case launch
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;

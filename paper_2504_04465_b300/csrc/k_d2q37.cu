@@ -76,7 +76,8 @@ struct D2Q37N {
     static constexpr int D = 2, Q = 37;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = N32 ? 4 : 2, MINB_GEN = 2;
-    static constexpr bool TUNE = false;
+    static constexpr bool TUNE = N32;        // compile occupancy variants for the autotuner
+    static constexpr int TUNE_V[3] = {62, 82, 44};   // their targets, 10 * interior + general
     static constexpr bool BATCH = false;
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;

@@ -919,18 +919,19 @@ KernelSet make_set() {
     k.n_variants = 1;
     if constexpr (M::BATCH) k.batch[0] = &LS::template batch<0, 0>;
     if constexpr (M::TUNE && ST != ST_F64) {       // occupancy targets tried by the autotuner
-        // (interior kernel, general kernel) resident 128-thread blocks; encoded 10 * F + G
-        k.variant[1] = &LS::template step<8, 4>;
-        k.variant[2] = &LS::template step<8, 6>;
-        k.variant[3] = &LS::template step<6, 6>;
+        // M::TUNE_V: (interior kernel, general kernel) resident 128-thread blocks, 10 * F + G
+        constexpr int V0 = M::TUNE_V[0], V1 = M::TUNE_V[1], V2 = M::TUNE_V[2];
+        k.variant[1] = &LS::template step<V0 / 10, V0 % 10>;
+        k.variant[2] = &LS::template step<V1 / 10, V1 % 10>;
+        k.variant[3] = &LS::template step<V2 / 10, V2 % 10>;
         if constexpr (M::BATCH) {
-            k.batch[1] = &LS::template batch<8, 4>;
-            k.batch[2] = &LS::template batch<8, 6>;
-            k.batch[3] = &LS::template batch<6, 6>;
+            k.batch[1] = &LS::template batch<V0 / 10, V0 % 10>;
+            k.batch[2] = &LS::template batch<V1 / 10, V1 % 10>;
+            k.batch[3] = &LS::template batch<V2 / 10, V2 % 10>;
         }
-        k.variant_minb[1] = 84;
-        k.variant_minb[2] = 86;
-        k.variant_minb[3] = 66;
+        k.variant_minb[1] = V0;
+        k.variant_minb[2] = V1;
+        k.variant_minb[3] = V2;
         k.n_variants = 4;
     }
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
