@@ -385,7 +385,7 @@ def form_sod_numerical(args, stream, local):
     x/L in [1/4, 3/4); sqr: a centred square of side L/2; hori: the half y/L < 1/2, whose
     interface meets the Neumann faces, which the grid builder refuses); L counts finest cells."""
     from paper_2504_04465_b300 import lbmtree as lt
-    L = 8192
+    L = 8192 // args.scale                        # --scale 4: the 2048^2 profiling case
     grids = {"unif": I.sod_spec(L, L), "band": I.sod_spec(L, L, 2, (L // 4, 3 * L // 4)),
              "sqr": I.GridSpec(2, (L, L), 2, [(0, (L // 4, L // 4), (3 * L // 4, 3 * L // 4))], (False, True),
                                {"x-": ("neumann",), "x+": ("neumann",)}),
@@ -648,7 +648,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg",
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical",
                     help="which forms to run (comma list; sod_numerical is the paper's Sec. 5 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",
