@@ -115,3 +115,35 @@ def test_batched_newton_matches_oracle():
         if guess == "poly":
             assert abs(it[sel].mean() - it_o.mean()) < 0.05
     ctx.close()
+
+
+@lru_cache(maxsize=None)
+def smooth_oracle_q21():
+    return H.run_oracle(N37_SPEC, "D2Q21", "num_ddf", H.smooth_comp_fields((96, 64), 0.9), 20, nu0=0.01, T0=0.9,
+                        sensor_A=1.35)
+
+
+@pytest.mark.parametrize("lattice", ["D2Q21", "D2Q37"])
+def test_fp32_newton_occupancy_variants(lattice):
+    """The autotuner's occupancy variants of the FP32-Newton step kernels differ only in their
+    register budgets, which may change the compiler's multiply-add fusion and so the FP32
+    rounding (the Newton then stops at another iterate within its tolerance): every variant must
+    meet the FP32-Newton bounds against the FP64 oracle (rho, T 1e-4; u 5e-4), whichever the
+    tuner picks."""
+    T0 = 0.9 if lattice == "D2Q21" else T0_VISC
+    sol = smooth_oracle_q21() if lattice == "D2Q21" else smooth_oracle()
+    fn = H.smooth_comp_fields((96, 64), T0)
+    n_var = None
+    v = 0
+    while n_var is None or v < n_var:
+        ctx = H.make_gpu(N37_SPEC, lattice, "num_ddf", "f32", fn, nu0=0.01, T0=T0, sensor_A=1.35, newton_fp32=True)
+        n_var = len(ctx.variants())
+        ctx.set_variant(v)
+        ctx.step(10)
+        err = H.compare_moments(sol, ctx)
+        print(lattice, "variant", ctx.variants()[v], err)
+        assert err["rho"] < 1e-4 and err["u"] < 5e-4 and err["T"] < 1e-4, (v, err)
+        assert ctx.stats().newton_nonconverged == 0
+        ctx.close()
+        v += 1
+    assert n_var == 4
