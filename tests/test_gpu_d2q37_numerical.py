@@ -147,3 +147,60 @@ def test_fp32_newton_occupancy_variants(lattice):
         ctx.close()
         v += 1
     assert n_var == 4
+
+
+def test_learned_guess_on_d2q37():
+    """The learned Newton guess on D2Q37 (the paper pairs D2Q37 with the numerical equilibrium
+    at high Mach numbers): a network trained by the project's kernels on equilibria of a D2Q37
+    run reaches the same roots as the zero guess in fewer iterations than the polynomial guess,
+    and the solver run from it equals the oracle's run from the same network (1e-12) and the
+    oracle's polynomial-guess run within the Newton tolerance accumulated over the run (1e-11)."""
+    from oracle import mlp
+    from tests.test_gpu_mlp import unflat
+    from tests.test_gpu_parity import SUP_SPEC, sup_fields
+    kw = dict(nu0=0.01, T0=T0_INV, sensor_A=1.35)
+    g0 = H.make_gpu(SUP_SPEC, "D2Q37", "num_ddf", "f64", sup_fields, guess="poly", **kw)
+    g0.step_fine(20)
+    g0.sync()
+    rho, u, T = g0.moments()
+    lv, xyz, ty = g0.cells()
+    keep = ty == 1
+    uT = np.stack([u[0, keep], u[1, keep], T[keep]], axis=1)
+    n = uT.shape[0]
+    d_uT = torch.tensor(uT, dtype=torch.float64, device="cuda")
+    out = {}
+    for guess in ("zero", "poly"):
+        d_lam = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+        d_it = torch.empty(n, dtype=torch.int32, device="cuda")
+        g0.newton_batch(d_uT.data_ptr(), n, guess, d_lam.data_ptr(), d_it.data_ptr())
+        g0.sync()
+        out[guess] = (d_lam, d_it.cpu().numpy())
+    loss = g0.mlp_train(d_uT.data_ptr(), out["zero"][0].data_ptr(), n, steps=1500, batch=1024)
+    assert np.isfinite(loss)
+    d_lam = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    d_it = torch.empty(n, dtype=torch.int32, device="cuda")
+    g0.newton_batch(d_uT.data_ptr(), n, "mlp", d_lam.data_ptr(), d_it.data_ptr())
+    g0.sync()
+    it_mlp = d_it.cpu().numpy()
+    assert (it_mlp >= 0).all() and (out["poly"][1] >= 0).all()
+    assert np.abs(d_lam.cpu().numpy() - out["zero"][0].cpu().numpy()).max() < 1e-9
+    print(f"D2Q37 batched Newton iterations: zero {out['zero'][1].mean():.3f} poly {out['poly'][1].mean():.3f} "
+          f"mlp {it_mlp.mean():.3f} (loss {loss:.4f})")
+    assert it_mlp.mean() < out["poly"][1].mean()
+    params, m, s = g0.mlp_get()
+    g0.close()
+
+    g = H.make_gpu(SUP_SPEC, "D2Q37", "num_ddf", "f64", sup_fields, guess="mlp", **kw)
+    g.mlp_set(params, m, s)
+    g.step_fine(30)
+    g.sync()
+    st = g.stats()
+    assert st.newton_nonconverged == 0
+    sol_mlp = H.run_oracle(SUP_SPEC, "D2Q37", "num_ddf", sup_fields, 30, guess="mlp",
+                           mlp=mlp.guess(unflat(params), m, s, T0_INV), **kw)
+    err = H.compare_moments(sol_mlp, g)
+    assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    sol_poly = H.run_oracle(SUP_SPEC, "D2Q37", "num_ddf", sup_fields, 30, guess="poly", **kw)
+    err = H.compare_moments(sol_poly, g)
+    assert err["rho"] < 1e-11 and err["u"] < 1e-11 and err["T"] < 1e-11, err
+    g.close()
