@@ -50,7 +50,8 @@ extern "C" {
 #define LBM_D3Q27 27
 
 /* Collision models (Appendix A): BGK and recursive regularization with the Hermite equilibrium
- * of Eq. GenEq (weakly compressible); compressible polyatomic DDF (Eqs. gEq, polyTemp) with the
+ * of Eq. GenEq (weakly compressible: D2Q9 and D3Q27 on their tensor-product bases, all storage
+ * formats; D2Q21 on every component up to order 3, FP64 and FP32); compressible polyatomic DDF (Eqs. gEq, polyTemp) with the
  * thermal polynomial equilibrium (D2Q37) or with the numerical max-entropy equilibrium of
  * Eq. exponential solved by Newton-Raphson in FP64 or FP32 (D2Q21 and D2Q37, Sec. 4.2). */
 #define LBM_BGK             1

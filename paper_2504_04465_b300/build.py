@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblbmtree.so")
-SOURCES = ["k_d2q9.cu", "k_d3q27.cu", "k_d2q37.cu", "k_d2q21.cu", "noalloc.cu", "k_mlp.cu", "k_io.cu", "api.cpp", "builder.cpp", "weights.cpp"]
+SOURCES = ["k_d2q9.cu", "k_d3q27.cu", "k_d2q37.cu", "k_d2q21.cu", "k_d2q21w.cu", "noalloc.cu", "k_mlp.cu", "k_io.cu", "api.cpp", "builder.cpp", "weights.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

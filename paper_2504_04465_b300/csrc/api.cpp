@@ -67,7 +67,9 @@ bool find_kernels(int lattice, int model, int storage, const int* blk, bool newt
         case LBM_D2Q9: return find_kernels_d2q9(model, storage, blk, out);
         case LBM_D3Q27: return find_kernels_d3q27(model, storage, blk, out);
         case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, newton_fp32, out);
-        case LBM_D2Q21: return find_kernels_d2q21(model, storage, blk, newton_fp32, out);
+        case LBM_D2Q21:
+            return (model == LBM_BGK || model == LBM_RR) ? find_kernels_d2q21w(model, storage, blk, out)
+                                                          : find_kernels_d2q21(model, storage, blk, newton_fp32, out);
     }
     return false;
 }
@@ -174,8 +176,9 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     a.n_levels = L;
     const int BS = c->grid.BS;
     // tau = nu / theta + 1/2 in each level's units, nu_i = nu_0 / 2^i (Eq. tau_fine_to_coarse);
-    // theta = c_s^2 for the weakly compressible models and T0 for the compressible ones
-    const double theta = c->comp() ? c->T0() : 1.0 / 3.0;
+    // theta = c_s^2 for the weakly compressible models (1/3, or 2/3 on D2Q21) and T0 for the
+    // compressible ones
+    const double theta = c->comp() ? c->T0() : (c->lattice == LBM_D2Q21 ? 2.0 / 3.0 : 1.0 / 3.0);
     for (int i = 0; i < L; ++i) {
         const BuiltLevel& bl = c->grid.levels[i];
         LevelDev& d = a.lv[i];
@@ -458,6 +461,7 @@ int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
             const Constants& k = constants();
             e = upload_tables_d2q37(k.w37, k.H37, k.cs2_37);
             if (e == cudaSuccess) e = upload_tables_d2q21(k.w21, k.H21);
+            if (e == cudaSuccess) e = upload_tables_d2q21w(k.w21, k.H21);
             if (e != cudaSuccess) {
                 delete c;
                 return fail(LBM_ERR_CUDA, std::string("constant upload: ") + cudaGetErrorString(e));
@@ -576,7 +580,7 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     if (!c->lattice || !c->params_set) return fail(LBM_ERR_STATE, "set lattice and collision model first");
     if (c->built) return fail(LBM_ERR_STATE, "grid already built");
     const bool weak = c->model == LBM_BGK || c->model == LBM_RR;
-    if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27)) ||
+    if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27 || c->lattice == LBM_D2Q21)) ||
         (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
         (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21 && c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");

@@ -31,6 +31,7 @@ bool find_kernels_d2q9(int model, int storage, const int* block, KernelSet& out)
 bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d2q37(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
 bool find_kernels_d2q21(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
+bool find_kernels_d2q21w(int model, int storage, const int* block, KernelSet& out);
 
 int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
                      float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);
@@ -44,6 +45,7 @@ void launch_newton_batch_d2q37(const double* uT, long long n, const ModelDev& m,
 // Constant tables of the D2Q37 and D2Q21 translation units (current device).
 cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37);
 cudaError_t upload_tables_d2q21(const double* w21, const double* H21);
+cudaError_t upload_tables_d2q21w(const double* w21, const double* H21);
 
 // weights.cpp: D2Q37 weights re-derived from isotropy, Hermite tables of both lattices
 void lattice_constants(double w37[37], double H37[37 * 15], double* cs2_37, double w21[21], double H21[21 * 10]);

@@ -15,6 +15,7 @@
 //   template <int ST> static void feq(m, rho, ux, uy, T, lam, feq, iters, conv)
 //   static void init_guess(ux, uy, T, lam)
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -23,6 +24,13 @@
 #include "models_comp.cuh"
 
 namespace lbm {
+
+// Weakly compressible models on lattices that are not tensor products of D1Q3 (D2Q21) carry
+// their own equilibrium and collision (HERMITE_WEAK); the others use the separable forms.
+template <class M, class = void> struct hermite_weak : std::false_type {};
+template <class M>
+struct hermite_weak<M, std::void_t<decltype(M::HERMITE_WEAK)>> : std::bool_constant<M::HERMITE_WEAK> {};
+
 
 enum Mode { MODE_STEP = 0, MODE_READ = 1, MODE_LEDGER = 2 };
 
@@ -248,7 +256,8 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
         rho = M::DEV ? r + T(a.m.rho_ref) : r;
     }
     if constexpr (!M::HAS_G) {
-        weak_feq_dev<M::D, T>(rho, T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), T(a.m.rho_ref), c.f);
+        if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(rho, T(fd.u[0]), T(fd.u[1]), T(a.m.rho_ref), c.f);
+        else weak_feq_dev<M::D, T>(rho, T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), T(a.m.rho_ref), c.f);
     } else {
         int it = 0, conv = 1;
         M::template feq<ST>(a.m, rho, T(fd.u[0]), T(fd.u[1]), T(fd.T), c.lam, c.f, &it, &conv);
@@ -267,7 +276,10 @@ __device__ __forceinline__ int collide(const ModelDev& m, const LevelDev& L, Cel
     *conv = 1;
     const double tau = L.tau;
     if constexpr (!M::HAS_G) {
-        if constexpr (REL) weak_collide<M::D, true, T, true>(c.f, L.omega_f, m.rho_ref_f, m.inv_rho_ref_f);
+        if constexpr (hermite_weak<M>::value) {
+            if constexpr (sizeof(T) == 4) M::template collide<T>(c.f, L.omega_f, m.rho_ref_f);
+            else M::template collide<T>(c.f, T(L.omega), T(m.rho_ref));
+        } else if constexpr (REL) weak_collide<M::D, true, T, true>(c.f, L.omega_f, m.rho_ref_f, m.inv_rho_ref_f);
         else if constexpr (sizeof(T) == 4) weak_collide<M::D, M::RR, T>(c.f, L.omega_f, m.rho_ref_f);
         else weak_collide<M::D, M::RR, T>(c.f, T(L.omega), T(m.rho_ref));
         return 0;
@@ -800,7 +812,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
     const T ux = T(u_in[cell]), uy = T(u_in[n + cell]), uz = T(M::D == 3 ? u_in[2 * n + cell] : 0.0);
     T feq[M::Q];
     if constexpr (!M::HAS_G) {
-        weak_feq_dev<M::D, T>(rho, ux, uy, uz, T(a.m.rho_ref), feq);
+        if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(rho, ux, uy, T(a.m.rho_ref), feq);
+        else weak_feq_dev<M::D, T>(rho, ux, uy, uz, T(a.m.rho_ref), feq);
 #pragma unroll
         for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, feq[q], T(0));
     } else {

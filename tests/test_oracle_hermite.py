@@ -105,7 +105,7 @@ def test_thermal_equilibrium_moments_d2q37():
     assert np.allclose((xi[:, 0] * r2) @ feq, rho * u[0] * (u2 + 4 * T), atol=1e-12, rtol=0)
 
 
-@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27", "D2Q21"])
 def test_rr_invariants(name):
     lat = L.LATTICES[name]
     n = 25
@@ -128,3 +128,18 @@ def test_rr_invariants(name):
     assert np.allclose(hm.collide_rr(lat, f, 1.0), feq, atol=1e-15, rtol=0)
     # BGK at tau = 1 as well
     assert np.allclose(hm.collide_weak(lat, f, 1.0, "bgk"), feq, atol=1e-15, rtol=0)
+
+
+def test_d2q21_athermal_equilibrium_is_thermal_at_cs2():
+    """On D2Q21 the weakly compressible equilibrium (every component to order 3, T0 = c_s^2) is
+    the thermal 3rd-order expansion at T = c_s^2, and its contracted third moment is the
+    Maxwellian's rho u_x (|u|^2 + (D + 2) c_s^2)."""
+    lat = L.D2Q21
+    n = 30
+    rho = 1 + 0.1 * RNG.random(n)
+    u = 0.1 * RNG.normal(size=(2, n))
+    feq = hm.feq_athermal(lat, rho, u)
+    assert np.allclose(feq, hm.feq_thermal(lat, rho, u, np.full(n, lat.cs2), 3), atol=1e-15, rtol=0)
+    xi = lat.xi.astype(float)
+    r2 = (xi ** 2).sum(1)
+    assert np.allclose((xi[:, 0] * r2) @ feq, rho * u[0] * ((u ** 2).sum(0) + 4 * lat.cs2), atol=1e-13, rtol=0)
