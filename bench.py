@@ -377,6 +377,34 @@ def form_d2q37(args, stream, local):
     return out
 
 
+def form_d2q21_weak(args, stream, local):
+    """Weakly compressible D2Q21 (Hermite basis to order 3) on a periodic shear layer, uniform
+    4096^2 (--scale divides the side): RR and BGK, FP32 deviations."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    n = 4096 // args.scale
+    spec = I.GridSpec(2, (n, n), 1, [], (True, True))
+    out = {"workload": f"D2Q21 weakly compressible, periodic {n}x{n}, u_x = 0.05 sin(2 pi y / L), rho = 1, "
+                       "nu0 = 0.01", "bytes_per_update": 168, "unit": "MLUPS"}
+    peak, kind = peaks()
+    for model in ("rr", "bgk"):
+        ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
+        ctx.configure(spec, "D2Q21", model, "f32", nu0=0.01)
+        ctx.use_graph(True)
+        lv, xyz, _ = ctx.cells()
+        y = I.cell_centres(xyz[:, :2], lv)[:, 1]
+        u = np.stack([0.05 * np.sin(2 * np.pi * y / n), np.zeros_like(y)])
+        ctx.init_fields(np.ones(y.size), u)
+        ctx.step(3)
+        K = 20
+        ms = _event_ms(stream, lambda: ctx.step(K)) / K
+        ctx.sync()
+        upd = ctx.stats().cell_updates
+        out[model] = {"ms_per_step": ms, "value": upd / ms / 1e3, "hbm_frac": 168 * upd / ms / 1e6 / peak,
+                      "peak_kind": kind}
+        ctx.close()
+    return out
+
+
 def form_sod_numerical(args, stream, local):
     """The paper's compressible performance benchmark (Sec. 5, Sod tube, L = 2^13, single
     precision): D2Q21 and D2Q37 DDF with the numerical equilibrium (8 constraints), FP32
@@ -612,7 +640,8 @@ def run_ours(args, world, rank, local):
                          ("batched", lambda: form_batched(args, stream, local)),
                          ("d2q37_sod", lambda: form_d2q37(args, stream, local)),
                          ("d2q9_tg", lambda: form_d2q9(args, stream, local)),
-                         ("sod_numerical", lambda: form_sod_numerical(args, stream, local))):
+                         ("sod_numerical", lambda: form_sod_numerical(args, stream, local)),
+                         ("d2q21_weak", lambda: form_d2q21_weak(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -648,7 +677,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical",
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak",
                     help="which forms to run (comma list; sod_numerical is the paper's Sec. 5 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",
