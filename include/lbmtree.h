@@ -239,9 +239,22 @@ int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
  * context's stream (read it after lbm_sync()).  The per-block partial sums go to a fixed device
  * array of the library holding at most 524288 blocks (20 MiB, kept by every GPU that loads the
  * library until the process exits); larger grids are rejected with LBM_ERR_ARG.  The first call on
- * a device looks up that array's address, so make it before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race.  LBM_ERR_STATE off a synchronisation instant. */
+ * a device looks up that array's address, so make it before any stream capture; the address is
+ * kept per device and driver context and looked up again if the device's context was recreated.
+ * All calls share the array: calls that overlap on the GPU race.  Unlike lbm_conserved, the call
+ * does not check the totals for NaN/Inf (they never reach the host): a caller that needs that
+ * check tests d_out after lbm_sync().  LBM_ERR_STATE off a synchronisation instant. */
 int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
+
+/* ---------------------------------------------------------------- measurement */
+/* Floating-point throughput of the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add pipe of
+ * `device`, the compute denominator of the roofline of compute-bound step kernels (no
+ * counterpart in the paper).  One wave of resident 256-thread blocks runs 8 independent FMA
+ * chains per thread for `iters` rounds (16 flops per round per thread); the best of 5 timed
+ * launches after one warm-up gives *flop_per_s (FMA counted as 2 operations) and *ms.  The
+ * result is at whatever SM clock the GPU runs at: sample the clock beside it.  Allocates a small
+ * output buffer; synchronous. */
+int lbm_pipe_peak(int device, int fp64, int iters, double* flop_per_s, float* ms);
 
 /* ---------------------------------------------------------------- checkpoint / restart */
 /* Write the state (populations of both buffers, multipliers, fine iteration counter, device

@@ -1,120 +1,21 @@
-// D2Q37 compressible double-distribution kernels with the thermal polynomial equilibrium and
-// the kinetic shock sensor (Appendix A of arXiv 2504.04465).  The equilibrium is the Hermite
-// expansion of Eq. GenEq to 4th order about theta = c_s^2 of the lattice with the thermal
-// moments of models_comp.cuh: f_eq,i = w_i sum_k H37[i][k] a_k, where H37[i][k] holds
-// h_a(xi_x) h_b(xi_y) / (a! b! theta^(a+b)) for component k = (a, b) (weights.cpp).
-#include <type_traits>
-
-#include "kernels_impl.cuh"
-#include "mlp.cuh"
+// D2Q37 compressible double-distribution kernels (Appendix A of arXiv 2504.04465): the kernel
+// sets of the thermal polynomial equilibrium, the batched equilibrium solve, and the lookup of
+// every D2Q37 kernel set.  The Newton-solved sets are compiled in translation units of their
+// own (k_d2q37_n64.cu: FP64 Newton; k_d2q37_n32_*.cu: FP32 Newton, one per storage format).
+#include "d2q37.cuh"
 
 namespace lbm {
 
-static __constant__ double cw37[37];
-static __constant__ float cw37f[37], cinvw37f[37];   // the weights in FP32 and their reciprocals
-static __constant__ double cH37[37][15];
-static __constant__ float cH37f[37][15];   // the same in FP32 (no conversion in the FP32 kernels)
-static __constant__ double ccs2_37;
-static __constant__ float ccs2_37f;
-
-struct D2Q37M {
-    static constexpr int D = 2, Q = 37;
-    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
-    static constexpr int MINB_FAST = 4, MINB_GEN = 2;
-    static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
-    static constexpr bool BATCH = true;   // compile the batched multi-case launch
-    static constexpr bool DEV = false;
-    static constexpr bool HAS_G = true, HAS_LAM = false, RR = false;
-    __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }
-    __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }
-    __host__ __device__ static constexpr int cz(int) { return 0; }
-    __device__ static double w(int q) { return cw37[q]; }
-    __device__ static float wf(int q) { return cw37f[q]; }
-    __device__ static float inv_wf(int q) { return cinvw37f[q]; }
-    template <int ST>
-    __device__ static void feq(const ModelDev&, typename Store<ST>::T rho, typename Store<ST>::T ux,
-                               typename Store<ST>::T uy, typename Store<ST>::T Tt, double*,
-                               typename Store<ST>::T* f, int* iters, int* conv) {
-        using T = typename Store<ST>::T;
-        constexpr bool F = sizeof(T) == 4;
-        T a[15];
-        thermal_moments<T>(rho, ux, uy, Tt - (F ? T(ccs2_37f) : T(ccs2_37)), 4, a);
-#pragma unroll
-        for (int i = 0; i < 37; ++i) {
-            T s = 0;
-#pragma unroll
-            for (int k = 0; k < 15; ++k) s += (F ? T(cH37f[i][k]) : T(cH37[i][k])) * a[k];
-            f[i] = (F ? T(cw37f[i]) : T(cw37[i])) * s;
-        }
-        *iters = 0;
-        *conv = 1;
-    }
-    __device__ static void init_guess(double, double, double, double*) {}
-};
-
-// ---------------------------------------------------------------- numerical equilibrium
-// The max-entropy equilibrium of Eq. exponential on D2Q37 (the paper's lattice for Mach 1.75 to
-// 2.5): the same eight constraints and Newton solve as D2Q21, the polynomial guess fitted to the
-// 4th-order thermal Hermite equilibrium about c_s^2 of D2Q37 (positive populations only, kept
-// where it beats lambda = 0), the learned guess evaluated like D2Q21's.
-template <typename R>
-__device__ __forceinline__ void poly_guess37(R ux, R uy, R Tt, R* lam) {
-    constexpr bool F = sizeof(R) == 4;
-    R a[15];
-    thermal_moments<R>(R(1), ux, uy, Tt - (F ? R(ccs2_37f) : R(ccs2_37)), 4, a);
-    poly_guess_fit<37, R>(ux, uy, Tt, [&](int q, R& w) {
-        R s = R(0);
-#pragma unroll
-        for (int k = 0; k < 15; ++k) s += (F ? R(cH37f[q][k]) : R(cH37[q][k])) * a[k];
-        w = F ? R(cw37f[q]) : R(cw37[q]);
-        return w * s;
-    }, lam);
-}
-
-template <bool N32>
-struct D2Q37N {
-    static constexpr int D = 2, Q = 37;
-    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
-    static constexpr int MINB_FAST = N32 ? 4 : 2, MINB_GEN = 2;
-    static constexpr bool TUNE = N32;        // compile occupancy variants for the autotuner
-    static constexpr int TUNE_V[3] = {62, 82, 44};   // their targets, 10 * interior + general
-    static constexpr bool BATCH = false;
-    static constexpr bool DEV = false;
-    static constexpr bool HAS_G = true, HAS_LAM = true, RR = false;
-    __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }
-    __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }
-    __host__ __device__ static constexpr int cz(int) { return 0; }
-    __device__ static double w(int q) { return cw37[q]; }
-    __device__ static float wf(int q) { return cw37f[q]; }
-    __device__ static float inv_wf(int q) { return cinvw37f[q]; }
-    template <int ST>
-    __device__ static void feq(const ModelDev& m, typename Store<ST>::T rho, typename Store<ST>::T ux,
-                               typename Store<ST>::T uy, typename Store<ST>::T Tt, double* lam,
-                               typename Store<ST>::T* f, int* iters, int* conv) {
-        using T = typename Store<ST>::T;
-        using R = typename std::conditional<N32, float, double>::type;
-        R l[8];
-        if (m.guess == 1) {
-#pragma unroll
-            for (int a2 = 0; a2 < 8; ++a2) l[a2] = R(0);
-        } else if (m.guess == 2) {
-            poly_guess37<R>(R(ux), R(uy), R(Tt), l);
-        } else if (m.guess == 3) {
-            mlp_guess<R>(m.mlp, m.T0, m.mlp_m, m.mlp_s, R(ux), R(uy), R(Tt), l);
-        } else {
-#pragma unroll
-            for (int a2 = 0; a2 < 8; ++a2) l[a2] = R(lam[a2]);
-        }
-        R e[37];
-        if constexpr (N32) *iters = newton_solve_inl<37, float>(R(ux), R(uy), R(Tt), l, e, R(m.newton_tol), m.newton_max_iter, conv);
-        else *iters = newton_solve<37>(R(ux), R(uy), R(Tt), l, e, R(m.newton_tol), m.newton_max_iter, conv);
-#pragma unroll
-        for (int a2 = 0; a2 < 8; ++a2) lam[a2] = double(l[a2]);
-#pragma unroll
-        for (int q = 0; q < 37; ++q) f[q] = T(R(rho) * e[q]);
-    }
-    __device__ static void init_guess(double ux, double uy, double Tt, double* lam) { poly_guess37<double>(ux, uy, Tt, lam); }
-};
+extern template KernelSet make_set<D2Q37N<false>, ST_F64, 16, 16, 1>();
+extern template KernelSet make_set<D2Q37N<false>, ST_F32, 16, 16, 1>();
+extern template KernelSet make_set<D2Q37N<false>, ST_F16DEV, 16, 16, 1>();
+extern template KernelSet make_set<D2Q37N<true>, ST_F64, 16, 16, 1>();
+extern template KernelSet make_set<D2Q37N<true>, ST_F32, 16, 16, 1>();
+extern template KernelSet make_set<D2Q37N<true>, ST_F16DEV, 16, 16, 1>();
+cudaError_t upload_tables_d2q37_n64(const double*, const double*, double);
+cudaError_t upload_tables_d2q37_n32_f64(const double*, const double*, double);
+cudaError_t upload_tables_d2q37_n32_f32(const double*, const double*, double);
+cudaError_t upload_tables_d2q37_n32_f16(const double*, const double*, double);
 
 // batched equilibrium solve: samples (u_x, u_y, T), guess 1 zero, 2 polynomial, 3 network
 __global__ void __launch_bounds__(128) k_newton_batch37(const double* __restrict__ uT, long long n, ModelDev m,
@@ -137,31 +38,30 @@ void launch_newton_batch_d2q37(const double* uT, long long n, const ModelDev& m,
     if (n) k_newton_batch37<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(uT, n, m, lam, iters);
 }
 
+template <bool N32>
+static bool numerical_set(int storage, KernelSet& out) {
+    switch (storage) {
+        case ST_F64: out = make_set<D2Q37N<N32>, ST_F64, 16, 16, 1>(); return true;
+        case ST_F32: out = make_set<D2Q37N<N32>, ST_F32, 16, 16, 1>(); return true;
+        case ST_F16DEV: out = make_set<D2Q37N<N32>, ST_F16DEV, 16, 16, 1>(); return true;
+    }
+    return false;
+}
+
 bool find_kernels_d2q37(int model, int storage, const int* blk, bool newton_fp32, KernelSet& out) {
     if (blk[0] != 16 || blk[1] != 16 || blk[2] != 1) return false;
-    if (model == 4) return newton_fp32 ? pick_storage<D2Q37N<true>, 16, 16, 1>(storage, out)
-                                       : pick_storage<D2Q37N<false>, 16, 16, 1>(storage, out);
+    if (model == 4) return newton_fp32 ? numerical_set<true>(storage, out) : numerical_set<false>(storage, out);
     if (model == 3) return pick_storage<D2Q37M, 16, 16, 1>(storage, out);
     return false;
 }
 
 cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37) {
-    cudaError_t e;
-    if ((e = cudaMemcpyToSymbol(cw37, w37, sizeof(double) * 37)) != cudaSuccess) return e;
-    float wf[37], iwf[37];
-    for (int q = 0; q < 37; ++q) {
-        wf[q] = (float)w37[q];
-        iwf[q] = (float)(1.0 / w37[q]);
-    }
-    if ((e = cudaMemcpyToSymbol(cw37f, wf, sizeof(wf))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cinvw37f, iwf, sizeof(iwf))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cH37, H37, sizeof(double) * 37 * 15)) != cudaSuccess) return e;
-    float hf[37 * 15];
-    for (int i = 0; i < 37 * 15; ++i) hf[i] = (float)H37[i];
-    if ((e = cudaMemcpyToSymbol(cH37f, hf, sizeof(hf))) != cudaSuccess) return e;
-    const float c2f = (float)cs2_37;
-    if ((e = cudaMemcpyToSymbol(ccs2_37f, &c2f, sizeof(float))) != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(ccs2_37, &cs2_37, sizeof(double));
+    cudaError_t e = upload37_here(w37, H37, cs2_37);
+    if (e == cudaSuccess) e = upload_tables_d2q37_n64(w37, H37, cs2_37);
+    if (e == cudaSuccess) e = upload_tables_d2q37_n32_f64(w37, H37, cs2_37);
+    if (e == cudaSuccess) e = upload_tables_d2q37_n32_f32(w37, H37, cs2_37);
+    if (e == cudaSuccess) e = upload_tables_d2q37_n32_f16(w37, H37, cs2_37);
+    return e;
 }
 
 }  // namespace lbm

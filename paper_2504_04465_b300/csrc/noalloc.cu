@@ -12,11 +12,18 @@
 // The per-block partial sums go to `g_ledger_scratch`, a file-scope device array of
 // kLedgerMaxBlocks x 5 doubles (20 MiB), held by every GPU on which the library's device code is
 // loaded, until the process exits.  Host code cannot use the array's name as a device address; the
-// address is looked up once per device with cudaGetSymbolAddress (the first call on a device does
-// this, so that first call should come before any stream capture) and passed to the kernels.
+// address is looked up with cudaGetSymbolAddress the first time a call runs on a device (so that
+// first call should come before any stream capture) and passed to the kernels.  The address is
+// cached per device together with the driver context it belongs to: if the device's context was
+// torn down and recreated (cudaDeviceReset by the host framework), the next call looks it up
+// again instead of using an address of the old context.
+// The totals stay on the device, so this call cannot report non-finite values the way
+// lbm_conserved does (LBM_ERR_NONFINITE): a caller that needs that check reads d_out after
+// lbm_sync() and tests it.
 // Every call shares the array and it keeps the last call's contents: each call overwrites the
 // partials it reads before reading them, so nothing has to be cleared, but two calls whose work
 // overlaps on the GPU (different streams, different contexts on one device) race on the array.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,6 +43,24 @@ __device__ __align__(256) double g_ledger_scratch[kLedgerMaxBlocks * 5];
 
 std::mutex g_mu;
 double* g_addr[256] = {nullptr};
+CUcontext g_ctx[256] = {nullptr};   // the driver context g_addr[d] was looked up in
+
+// The calling thread's current driver context (nullptr if it cannot be queried).  The driver
+// entry point is fetched through the runtime, so the library needs no link to libcuda.
+CUcontext current_context() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    static GetCurrent fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<GetCurrent>(p);
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 }  // namespace
 
 extern "C" int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out) {
@@ -54,8 +79,10 @@ extern "C" int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out) {
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[device]) {
-            // the context's device is current here (ledger_launch_args sets it)
+        // the context's device is current here (ledger_launch_args sets it)
+        const CUcontext cur = current_context();
+        if (!g_addr[device] || !cur || cur != g_ctx[device]) {
+            g_ctx[device] = cur;
             cudaError_t e = cudaGetSymbolAddress((void**)&g_addr[device], g_ledger_scratch);
             if (e != cudaSuccess) {
                 g_addr[device] = nullptr;

@@ -184,17 +184,24 @@ NACA_BOXES = [((-0.1, 1.1), (-0.15, 0.15)), ((-0.5, 2.0), (-0.5, 0.5)), ((-2.0, 
 NACA_SEED = 1504
 
 
+# Reduced form for parity runs at small chords: the finest box is wide enough that the airfoil
+# stays more than the reach of the 37- and 21-velocity lattices (3 cells) from its fine ghosts.
+NACA_BOXES_SMALL = [((-0.25, 1.25), (-0.3, 0.3)), ((-0.75, 2.0), (-0.75, 0.75))]
+
+
 def naca_spec(chord: int, mach: float, T0: float, gamma: float = 1.4, n_levels: int = 5,
-              supersonic: bool = True) -> GridSpec:
+              supersonic: bool = True, half_domain: float = 15.0, level_boxes=None) -> GridSpec:
     """Multi-level box around a NACA0012 at zero incidence, chord ``chord`` finest cells.
 
-    The leading edge sits at the domain centre (15C, 15C).  Inflow at x-: every macroscopic
-    field imposed (supersonic inlet) or density extrapolated (subsonic); Neumann on the other
-    faces.  Box edges are rounded outwards to whole cells of the next coarser level."""
-    ext = 30 * chord
-    cx, cy = 15 * chord, 15 * chord
+    The domain is [-h C, h C]^2 around the leading edge (h = ``half_domain``), which sits at the
+    domain centre.  Inflow at x-: every macroscopic field imposed (supersonic inlet) or density
+    extrapolated (subsonic); Neumann on the other faces.  ``level_boxes`` (default NACA_BOXES)
+    gives the refined boxes in chords, finest level first; box edges are rounded outwards to
+    whole cells of the next coarser level."""
+    ext = int(round(2 * half_domain * chord))
+    cx, cy = ext // 2, ext // 2
     boxes = []
-    for lev, ((x0, x1), (y0, y1)) in enumerate(NACA_BOXES[:n_levels - 1]):
+    for lev, ((x0, x1), (y0, y1)) in enumerate((level_boxes or NACA_BOXES)[:n_levels - 1]):
         a = 2 ** (lev + 1)
         lo = (int(np.floor((cx + x0 * chord) / a)) * a, int(np.floor((cy + y0 * chord) / a)) * a)
         hi = (int(np.ceil((cx + x1 * chord) / a)) * a, int(np.ceil((cy + y1 * chord) / a)) * a)

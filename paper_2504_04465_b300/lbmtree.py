@@ -102,6 +102,7 @@ _sig = {
     "lbm_batch_sync": [C.c_void_p],
     "lbm_batch_info": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "lbm_mlp_train": [_P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
+    "lbm_pipe_peak": [C.c_int, C.c_int, C.c_int, _D, C.POINTER(C.c_float)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -189,6 +190,13 @@ def lattice_info(name: str) -> dict:
 
 def lattice_cs2(name: str) -> float:
     return lattice_info(name)["cs2"]
+
+
+def pipe_peak(fp64: bool, device: int = 0, iters: int = 8192) -> tuple[float, float]:
+    """(flop/s, ms) of the FP32 or FP64 fused multiply-add pipe of ``device`` (lbm_pipe_peak)."""
+    out, ms = C.c_double(), C.c_float()
+    _check(_lib.lbm_pipe_peak(device, int(fp64), iters, C.byref(out), C.byref(ms)), "lbm_pipe_peak")
+    return out.value, ms.value
 
 
 def mlp_nparams() -> int:

@@ -97,6 +97,47 @@ def compare_moments(sol, ctx):
     return out
 
 
+def near_interface(sol, width=None):
+    """Per level, oracle indices of bulk and boundary cells within ``width`` cells (Chebyshev
+    distance in the level's own units; default twice the lattice reach) of a coarse ghost, a
+    fine ghost or a solid cell: the cells a coupling or bounce-back error reaches first."""
+    w = 2 * sol.lat.reach if width is None else width
+    out = []
+    for lv in sol.g.levels:
+        dense = np.zeros(lv.shape, dtype=bool)
+        special = np.isin(lv.ctype, (G.CGHOST, G.FGHOST, G.SOLID))
+        dense[tuple(lv.coords[special].T)] = True
+        near = G._dilate(dense, w, sol.g.periodic)
+        hit = near[tuple(lv.coords.T)] & np.isin(lv.ctype, (G.FLUID, G.BC))
+        out.append(np.nonzero(hit)[0])
+    return out
+
+
+def compare_near(sol, ctx, width=None):
+    """Largest pointwise error of rho, u (every component) and T over the cells of
+    ``near_interface``, relative to the largest magnitude of that field on the same level;
+    also the number of cells checked."""
+    rho_g, u_g, T_g = ctx.moments()
+    idx = gpu_index(ctx, sol.g.D)
+    near = near_interface(sol, width)
+    worst = {"rho": 0.0, "u": 0.0, "n": 0}
+    for lev, lv in enumerate(sol.g.levels):
+        sel = near[lev]
+        if sel.size == 0:
+            continue
+        allc = np.nonzero(np.isin(lv.ctype, (G.FLUID, G.BC)))[0]
+        gi = np.array([idx[(lev, *map(int, lv.coords[k]))] for k in sel], dtype=np.int64)
+        rho_o, u_o, T_o = sol.moments(lev)
+        worst["n"] += int(sel.size)
+        pairs = [("rho", rho_g[gi], rho_o[sel], np.abs(rho_o[allc]).max()),
+                 ("u", u_g[:, gi], u_o[:, sel], np.abs(u_o[:, allc]).max())]
+        if T_o is not None:
+            pairs.append(("T", T_g[gi], T_o[sel], np.abs(T_o[allc]).max()))
+        for k, a, b, scale in pairs:
+            worst[k] = max(worst.get(k, 0.0), float(np.abs(a - b).max() / max(scale, 1e-300)))
+    return worst
+
+
 def population_map(sol, ctx):
     """perm such that gpu population perm[q] is oracle population q."""
     xi_g = ctx.velocities()[:, : sol.g.D]
@@ -115,6 +156,24 @@ def compare_populations(sol, ctx, which="f"):
         g = pops[perm][:, gi]
         worst = max(worst, float(np.abs(g - o).max() / max(np.abs(o).max(), 1e-300)))
     return worst
+
+
+def error_curve(spec, latname, model, storage, fields_fn, checkpoints, **params):
+    """Step the oracle and the CUDA path side by side and compare them at each checkpoint (fine
+    iterations): whole-domain relative L2 (``compare_moments``) and the interface-local relative
+    max-abs (``compare_near``, keys prefixed ``near_``).  Returns (oracle, context, curve)."""
+    sol = run_oracle(spec, latname, model, fields_fn, 0, **params)
+    ctx = make_gpu(spec, latname, model, storage, fields_fn, **params)
+    curve, t = [], 0
+    for c in checkpoints:
+        sol.step_fine(c - t)
+        ctx.step_fine(c - t)
+        ctx.sync()
+        t = c
+        e = compare_moments(sol, ctx)
+        e.update({"near_" + k: v for k, v in compare_near(sol, ctx).items()})
+        curve.append((c, e))
+    return sol, ctx, curve
 
 
 # ------------------------------------------------------------------ seeded initial fields

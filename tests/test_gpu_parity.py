@@ -112,6 +112,9 @@ def test_channel_three_levels_cylinder_f64():
     ctx.step(40)
     err = H.compare_moments(sol, ctx)
     assert err["rho"] < 1e-12 and err["u"] < 1e-12, err
+    near = H.compare_near(sol, ctx)
+    assert near["n"] > 0 and near["rho"] < 1e-12 and near["u"] < 1e-12, near
+    assert H.compare_populations(sol, ctx) < 1e-12
 
 
 # ------------------------------------------------------------------ D3Q27 two levels with a sphere
@@ -140,6 +143,10 @@ def test_d3q27_two_level_sphere(storage, tol):
     err = H.compare_moments(sol, ctx)
     print("d3q27", storage, err)
     assert err["rho"] < tol and err["u"] < tol, err
+    if storage == "f64":
+        near = H.compare_near(sol, ctx)
+        assert near["n"] > 0 and near["rho"] < 1e-12 and near["u"] < 1e-12, near
+        assert H.compare_populations(sol, ctx) < 1e-12
 
 
 # ------------------------------------------------------------------ D2Q37 polynomial DDF, Sod band
@@ -159,6 +166,11 @@ def test_d2q37_sod_band(storage, tol):
     err = H.compare_moments(sol, ctx)
     print("d2q37", storage, err)
     assert err["rho"] < tol and err["u"] < tol and err["T"] < tol, err
+    if storage == "f64":
+        near = H.compare_near(sol, ctx)
+        assert near["n"] > 0 and max(near["rho"], near["u"], near["T"]) < 1e-12, near
+        assert H.compare_populations(sol, ctx, "f") < 1e-12
+        assert H.compare_populations(sol, ctx, "g") < 1e-12
 
 
 # ------------------------------------------------------------------ D2Q21 numerical DDF
@@ -172,6 +184,10 @@ def test_d2q21_numerical_two_level_f64():
     ctx.step(10)
     err = H.compare_moments(sol, ctx)
     assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    near = H.compare_near(sol, ctx)
+    assert near["n"] > 0 and max(near["rho"], near["u"], near["T"]) < 1e-12, near
+    assert H.compare_populations(sol, ctx, "f") < 1e-12
+    assert H.compare_populations(sol, ctx, "g") < 1e-12
     s = ctx.stats()
     assert s.newton_updates > 0 and s.newton_nonconverged == 0
     assert s.newton_iter_sum / s.newton_updates < 4
@@ -194,6 +210,8 @@ def test_d2q21_supersonic_inlet_f64(guess):
     ctx.step_fine(30)
     err = H.compare_moments(sol, ctx)
     assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
+    assert H.compare_populations(sol, ctx, "f") < 1e-12
+    assert H.compare_populations(sol, ctx, "g") < 1e-12
 
 
 def test_d2q21_f32_populations_fp64_newton():
