@@ -69,8 +69,20 @@ def _stale(src: str, obj: str, dfile: str, stamp: str, sig: str) -> bool:
     return False
 
 
+def _lib_current() -> bool:
+    """The library exists and is newer than every source and header (no object files needed)."""
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp", ".h", ".cuh"))]
+    files.append(os.path.join(HERE, "..", "include", "lbmtree.h"))
+    return all(os.path.getmtime(f) <= t for f in files)
+
+
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     """Compile the stale translation units for sm_103a and link liblbmtree.so next to this file."""
+    if not force and not extra and _lib_current():
+        return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     flags = _flags(extra)
     sig = hashlib.sha256(" ".join([_nvcc(), *flags]).encode()).hexdigest()

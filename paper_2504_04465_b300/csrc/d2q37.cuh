@@ -1,11 +1,10 @@
 // D2Q37 compressible double-distribution models (Appendix A of arXiv 2504.04465), shared by the
 // translation units that compile their kernel sets.
 //
-// D2Q37M: the thermal polynomial equilibrium and the kinetic shock sensor.  The equilibrium is
-// the Hermite expansion of Eq. GenEq to 4th order about theta = c_s^2 of the lattice with the
-// thermal moments of models_comp.cuh: f_eq,i = w_i sum_k H37[i][k] a_k, where H37[i][k] holds
-// h_a(xi_x) h_b(xi_y) / (a! b! theta^(a+b)) for component k = (a, b) (weights.cpp).
-// D2Q37N: the max-entropy equilibrium of Eq. exponential, Newton-solved in FP64 or FP32.
+// D2Q37N: the max-entropy equilibrium of Eq. exponential, Newton-solved in FP64 or FP32; its
+// polynomial guess uses the per-velocity thermal Hermite table H37[i][k] =
+// h_a(xi_x) h_b(xi_y) / (a! b! theta^(a+b)) for component k = (a, b) (weights.cpp).  The
+// polynomial-equilibrium model D2Q37M lives in k_d2q37.cu.
 //
 // The constant tables are internal to each translation unit that includes this header; every
 // such unit exports an upload function that fills its own copy (k_d2q37.cu calls them all).
@@ -23,41 +22,6 @@ static __constant__ double cH37[37][15];
 static __constant__ float cH37f[37][15];   // the same in FP32 (no conversion in the FP32 kernels)
 static __constant__ double ccs2_37;
 static __constant__ float ccs2_37f;
-
-struct D2Q37M {
-    static constexpr int D = 2, Q = 37;
-    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
-    static constexpr int MINB_FAST = 4, MINB_GEN = 2;
-    static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
-    static constexpr bool BATCH = true;   // compile the batched multi-case launch
-    static constexpr bool DEV = false;
-    static constexpr bool HAS_G = true, HAS_LAM = false, RR = false;
-    __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }
-    __host__ __device__ static constexpr int cy(int q) { return Lat<37>::cy(q); }
-    __host__ __device__ static constexpr int cz(int) { return 0; }
-    __device__ static double w(int q) { return cw37[q]; }
-    __device__ static float wf(int q) { return cw37f[q]; }
-    __device__ static float inv_wf(int q) { return cinvw37f[q]; }
-    template <int ST>
-    __device__ static void feq(const ModelDev&, typename Store<ST>::T rho, typename Store<ST>::T ux,
-                               typename Store<ST>::T uy, typename Store<ST>::T Tt, double*,
-                               typename Store<ST>::T* f, int* iters, int* conv) {
-        using T = typename Store<ST>::T;
-        constexpr bool F = sizeof(T) == 4;
-        T a[15];
-        thermal_moments<T>(rho, ux, uy, Tt - (F ? T(ccs2_37f) : T(ccs2_37)), 4, a);
-#pragma unroll
-        for (int i = 0; i < 37; ++i) {
-            T s = 0;
-#pragma unroll
-            for (int k = 0; k < 15; ++k) s += (F ? T(cH37f[i][k]) : T(cH37[i][k])) * a[k];
-            f[i] = (F ? T(cw37f[i]) : T(cw37[i])) * s;
-        }
-        *iters = 0;
-        *conv = 1;
-    }
-    __device__ static void init_guess(double, double, double, double*) {}
-};
 
 // ---------------------------------------------------------------- numerical equilibrium
 // The max-entropy equilibrium of Eq. exponential on D2Q37 (the paper's lattice for Mach 1.75 to

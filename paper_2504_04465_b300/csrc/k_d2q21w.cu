@@ -17,7 +17,8 @@ static __constant__ float cH21wf[21][10];
 template <bool RR_>
 struct D2Q21W {
     static constexpr int D = 2, Q = 21;
-    // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
+    // occupancy targets of the step kernels (simple / other blocks) in units of 128 resident
+    // threads per SM: 4 is two resident 16x16 blocks (512 threads, at most 128 registers each)
     static constexpr int MINB_FAST = 4, MINB_GEN = 2;
     static constexpr bool TUNE = false, BATCH = false, DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;
@@ -33,15 +34,38 @@ struct D2Q21W {
     template <typename T>
     __device__ static T wq(int q) { return sizeof(T) == 4 ? T(cw21wf[q]) : T(cw21w[q]); }
 
-    // deviations f_i - w_i rho_ref of the expansion with coefficients a (a[0] = rho - rho_ref)
+    // 25920 w_i H[i][k] as an integer (exact in FP32 and FP64): 25920 w_i is 7280, 2160, 1920, 504,
+    // 60, 16 for the velocity classes (0,0), (1,0), (1,1), (2,0), (2,2), (3,0); per axis the
+    // factor h_a(xi) / (a! c_s^2a) with c_s^2 = 2/3 is 1, 3 xi / 2, 3 (3 xi^2 - 2) / 8 and
+    // 9 (xi^3 - 2 xi) / 16 for a = 0..3, and every product divides exactly.
+    __host__ __device__ static constexpr int wint(int x, int y) {
+        const int a = x < 0 ? -x : x, b = y < 0 ? -y : y;
+        const int m = a > b ? a : b, n = a > b ? b : a;
+        return m == 0 ? 7280 : m == 1 ? (n == 0 ? 2160 : 1920) : m == 2 ? (n == 0 ? 504 : 60) : 16;
+    }
+    __host__ __device__ static constexpr int hnum(int a, int x) {
+        return a == 0 ? 1 : a == 1 ? 3 * x : a == 2 ? 3 * (3 * x * x - 2) : 9 * (x * x * x - 2 * x);
+    }
+    __host__ __device__ static constexpr int hden(int a) { return a == 0 ? 1 : a == 1 ? 2 : a == 2 ? 8 : 16; }
+    __host__ __device__ static constexpr int ka(int k) { return k == 0 ? 0 : k <= 2 ? 2 - k : k <= 5 ? 5 - k : 9 - k; }
+    __host__ __device__ static constexpr int kb(int k) { return k == 0 ? 0 : k <= 2 ? k - 1 : k <= 5 ? k - 3 : k - 6; }
+    __host__ __device__ static constexpr int G(int q, int k) {
+        return wint(cx(q), cy(q)) * hnum(ka(k), cx(q)) * hnum(kb(k), cy(q)) / (hden(ka(k)) * hden(kb(k)));
+    }
+    // deviations f_i - w_i rho_ref of the expansion with coefficients a (a[0] = rho - rho_ref):
+    // f_i = (sum_k G(i, k) a_k) / 25920, one correctly rounded division per population, so the
+    // reconstruction carries no rounded weight or Hermite constant (an FP32 table scaled the
+    // momentum by 1 + O(1e-8) every step, a drift that grows linearly with the step count)
     template <typename T>
     __device__ static void expand(const T* a, T* f) {
+        const T den = T(25920), rden = T(1) / den;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             T s = T(0);
 #pragma unroll
-            for (int k = 0; k < 10; ++k) s += Hk<T>(q, k) * a[k];
-            f[q] = wq<T>(q) * s;
+            for (int k = 0; k < 10; ++k)
+                if (G(q, k) != 0) s += T(G(q, k)) * a[k];
+            f[q] = div_den<T>(s, den, rden);
         }
     }
     // equilibrium coefficients rho u^alpha (athermal, T0 = c_s^2), the order-0 one as rho - rho_ref
@@ -109,6 +133,30 @@ struct D2Q21W {
     }
     __device__ static void init_guess(double, double, double, double*) {}
 };
+
+// the integer table reproduces the moments of the expansion: component k = (a, b) alone carries
+// exactly the monomial moment xi_x^a xi_y^b (sum_i xi^(a,b) G(i, k) = 25920, orthonormality of
+// the scaled Hermite basis under the weights) and no lower odd moment
+namespace {
+template <int K, int PX, int PY>
+constexpr long moment21() {
+    long s = 0;
+    for (int q = 0; q < 21; ++q) {
+        long t = D2Q21W<true>::G(q, K);
+        for (int i = 0; i < PX; ++i) t *= D2Q21W<true>::cx(q);
+        for (int i = 0; i < PY; ++i) t *= D2Q21W<true>::cy(q);
+        s += t;
+    }
+    return s;
+}
+static_assert(moment21<0, 0, 0>() == 25920 && moment21<1, 1, 0>() == 25920 && moment21<2, 0, 1>() == 25920,
+              "D2Q21 integer reconstruction table");
+static_assert(moment21<3, 2, 0>() == 25920 && moment21<4, 1, 1>() == 25920 && moment21<6, 3, 0>() == 25920,
+              "D2Q21 integer reconstruction table");
+static_assert(moment21<0, 1, 0>() == 0 && moment21<3, 1, 0>() == 0 && moment21<7, 2, 1>() == 25920 &&
+                  moment21<9, 0, 3>() == 25920,
+              "D2Q21 integer reconstruction table");
+}  // namespace
 
 bool find_kernels_d2q21w(int model, int storage, const int* blk, KernelSet& out) {
     if (blk[0] != 16 || blk[1] != 16 || blk[2] != 1) return false;

@@ -49,5 +49,8 @@ cudaError_t upload_tables_d2q21w(const double* w21, const double* H21);
 
 // weights.cpp: D2Q37 weights re-derived from isotropy, Hermite tables of both lattices
 void lattice_constants(double w37[37], double H37[37 * 15], double* cs2_37, double w21[21], double H21[21 * 10]);
+// D2Q37 thermal-equilibrium coefficients per velocity class (FP64, and FP32 rounded to conserve
+// mass, momentum and energy exactly); max_residual: largest moment error left in the FP32 table
+void d2q37_class_tables(double C64[13 * 15], float C32[13 * 15], double* th64, float* th32, double* max_residual);
 
 }  // namespace lbm

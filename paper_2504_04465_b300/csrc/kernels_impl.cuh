@@ -295,7 +295,7 @@ __device__ __forceinline__ int collide(const ModelDev& m, const LevelDev& L, Cel
             const T tiny = (sizeof(T) == 8) ? T(1e-300) : T(1e-30);
 #pragma unroll
             for (int q = 0; q < M::Q; ++q)
-                if (feq[q] > tiny) eps += r_fabs(c.f[q] - feq[q]) / feq[q];
+                if (feq[q] > tiny) eps += sensor_ratio(r_fabs(c.f[q] - feq[q]), feq[q]);
             eps /= T(M::Q);
             tau_eff = T(tau) * sensor_alpha<T>(eps, T(tau), T(m.sensor_A));
         }

@@ -84,6 +84,17 @@ LBM_HD constexpr bool tables_match() {
 }
 static_assert(tables_match(), "D2Q21/D2Q37 switch tables differ from the enumeration");
 
+// The 13 classes (X, Y) = (|xi_x|, |xi_y|) of the D2Q37 velocities, the centre first, then the
+// axis pairs (X, 0) and (0, Y), then the quadruples (+-X, +-Y)
+LBM_HD constexpr int d2q37_class_x(int c) {
+    constexpr int t[13] = {0, 1, 0, 2, 0, 3, 0, 1, 2, 1, 2, 3, 1};
+    return t[c];
+}
+LBM_HD constexpr int d2q37_class_y(int c) {
+    constexpr int t[13] = {0, 0, 1, 0, 2, 0, 3, 1, 1, 2, 2, 1, 3};
+    return t[c];
+}
+
 template <int Q> struct Lat;
 
 template <> struct Lat<9> {

@@ -52,6 +52,12 @@ __device__ __forceinline__ void thermal_moments(T rho, T ux, T uy, T dT, int ord
     }
 }
 
+// one term |f - f_eq| / f_eq of Eq. DeltaAvg: the FP32 kernels take the fast approximate
+// division (a reciprocal and a product, a few ulps); the sensor only compares the mean with
+// thresholds 0.01, 0.1 and 1, so a few ulps matter no more than the FP32 rounding of f itself
+__device__ __forceinline__ float sensor_ratio(float num, float den) { return __fdividef(num, den); }
+__device__ __forceinline__ double sensor_ratio(double num, double den) { return num / den; }
+
 // Eq. shock_function with alpha = 1 below 0.01
 template <typename T>
 __device__ __forceinline__ T sensor_alpha(T eps, T tau, T A) {

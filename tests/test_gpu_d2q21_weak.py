@@ -2,8 +2,9 @@
 basis is every tensor component up to order 3, c_s^2 = 2/3) against the FP64 oracle on a
 two-level periodic grid.
 
-Tolerances: FP64 populations agree to 1e-12 relative L2 (rounding order only); FP32 deviations
-to 1e-5 for rho and u over 20 fine iterations (FP32 rounding of 21-term sums on deviations)."""
+Tolerances: FP64 populations agree to 1e-12 relative L2 (rounding order only) and conserve mass
+and momentum across the refinement interface to round-off; FP32 deviations to 1e-5 for rho and u
+over 20 fine iterations here and over 1000 in tests/test_gpu_fp32_long.py."""
 from __future__ import annotations
 
 from functools import lru_cache
@@ -45,6 +46,7 @@ def test_d2q21_weak_f64(model):
     assert err["rho"] < 1e-12 and err["u"] < 1e-12, err
     t1 = ctx.conserved()
     assert abs(t1[0] - t0[0]) <= 1e-13 * abs(t0[0])       # mass, exactly conserved (R1, R3)
+    assert np.abs(t1[1:3] - t0[1:3]).max() <= 1e-13 * abs(t0[0])   # momentum across the interface
     ctx.close()
 
 
