@@ -37,18 +37,142 @@ from paper_2504_04465_b300 import inputs as I  # noqa: E402
 BYTES_PER_UPDATE = {"f64": 432, "f32": 216, "f16dev": 108}   # 27 populations read + written
 WORKLOAD = ("D3Q27 recursive-regularized, flow past a sphere (D = 64 finest cells), 4 levels, "
             "1024x512x512 finest-unit box, Ma 0.1, Re 3900")
-# DRAM bytes per cell update of both step kernels over one full-size coarse step (16 launches),
-# from the single-pass ncu capture summarised in profiles/k_step_d3q27_sphere.md
-NCU_TRAFFIC_PER_UPDATE = {"f32": 230.6, "f16dev": 115.6, "f64": None}
+CSRC = os.path.join(ROOT, "paper_2504_04465_b300", "csrc")
+
+# Figures taken from ncu captures of the step kernels (``--counters PATH`` runs the captured
+# case; the ncu command that took it is given with its summary in the repository).  Each entry records
+# the kernel sources it was taken on (``source_hash``); when those files have changed since,
+# the figure is reported as null instead of a stale number.
+#   dram: DRAM bytes (read + write) per cell update of both step kernels over one coarse step
+#         of the main workload at half extents
+#   flops: executed floating-point operations per cell update (fadd + fmul + 2 ffma, and the
+#          same for FP64), both step kernels, one coarse step of the captured case
+COUNTERS = {
+    ('d2q21n32:band', "flops"): {"value": 4005.8, "source_hash": 'fcc82851cbd13753',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.15 Newton iterations per update'},
+    ('d2q21n32:sqr', "flops"): {"value": 3778.0, "source_hash": 'fcc82851cbd13753',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.07 Newton iterations per update'},
+    ('d2q21n32:unif', "flops"): {"value": 2879.7, "source_hash": 'fcc82851cbd13753',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 0.68 Newton iterations per update'},
+    ('d2q21n64:poly', "flops"): {"value": 37858.4, "source_hash": '4259e8426781d31e',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256, Mach 1.5, after 3 coarse steps, 11.74 Newton iterations per update'},
+    ('d2q21n64:warm', "flops"): {"value": 8578.6, "source_hash": '4259e8426781d31e',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256, Mach 1.5, after 3 coarse steps, 2.66 Newton iterations per update'},
+    ('d2q21w:f32', "flops"): {"value": 546.0, "source_hash": '5fd9507b8f0dddb7',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 1024^2 shear layer'},
+    ('d2q37n32:band', "flops"): {"value": 6318.2, "source_hash": 'e5447dc299a01302',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.13 Newton iterations per update'},
+    ('d2q37n32:sqr', "flops"): {"value": 5964.2, "source_hash": 'e5447dc299a01302',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.04 Newton iterations per update'},
+    ('d2q37n32:unif', "flops"): {"value": 4487.4, "source_hash": 'e5447dc299a01302',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 0.63 Newton iterations per update'},
+    ('d2q37p:naca_f32', "flops"): {"value": 961.5, "source_hash": '9718653ac1016060',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256'},
+    ('d2q37p:naca_f64', "flops"): {"value": 1361.6, "source_hash": '9718653ac1016060',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256'},
+    ('d2q37p:sod_f32', "flops"): {"value": 1095.0, "source_hash": '9718653ac1016060',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 4096x64 Sod tube'},
+    ('d2q37p:sod_f64', "flops"): {"value": 1661.2, "source_hash": '9718653ac1016060',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 4096x64 Sod tube'},
+    ('d2q9:f32', "flops"): {"value": 243.0, "source_hash": '094fa9843a63ee4f',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 2048^2 Taylor-Green grid'},
+    ('d2q9:f64', "flops"): {"value": 253.0, "source_hash": '094fa9843a63ee4f',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 2048^2 Taylor-Green grid'},
+    ('d3q27:f16dev', "flops"): {"value": 539.5, "source_hash": 'ed1516518122ee10',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+    ('d3q27:f16dev', "dram"): {"value": 109.8, "source_hash": 'ed1516518122ee10',
+                  "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+    ('d3q27:f32', "flops"): {"value": 612.5, "source_hash": 'ed1516518122ee10',
+                   "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+    ('d3q27:f32', "dram"): {"value": 225.5, "source_hash": 'ed1516518122ee10',
+                  "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+    ('d3q27:f64', "flops"): {"value": 621.8, "source_hash": 'ed1516518122ee10',
+                   "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+    ('d3q27:f64', "dram"): {"value": 447.1, "source_hash": 'ed1516518122ee10',
+                  "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
+}
+
+
+def source_hash(files) -> str:
+    """sha256 (first 16 hex digits) of the listed kernel source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+# the files each kernel path is compiled from (its translation unit and the headers it includes)
+_COMMON = ["kernels_impl.cuh", "device_common.cuh", "device_types.h", "models.cuh", "models_comp.cuh",
+           "lattice_tables.h", "kernels.h", "mlp.cuh"]
+PATH_SOURCES = {
+    "d3q27": ["k_d3q27.cu"] + _COMMON,
+    "d2q9": ["k_d2q9.cu"] + _COMMON,
+    "d2q37p": ["k_d2q37.cu", "d2q37.cuh", "weights.cpp"] + _COMMON,
+    "d2q21w": ["k_d2q21w.cu"] + _COMMON,
+    "d2q21n32": ["k_d2q21_n32_f32.cu", "d2q21.cuh"] + _COMMON,
+    "d2q37n32": ["k_d2q37_n32_f32.cu", "d2q37.cuh"] + _COMMON,
+    "d2q21n64": ["k_d2q21.cu", "d2q21.cuh"] + _COMMON,
+}
+
+
+def counter(path: str, key: str):
+    """(value, note) of a captured figure, value None when missing or taken on other sources."""
+    e = COUNTERS.get((path, key))
+    if e is None:
+        return None, "not captured"
+    if e["source_hash"] != source_hash(PATH_SOURCES[path.split(":")[0]]):
+        return None, "kernel sources changed since the capture"
+    return e["value"], e["capture"]
 
 
 def peaks():
+    """Measured HBM copy bandwidth of the B300s (GB/s) and where it comes from."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+_PIPE = {}
+
+
+def pipe_peaks(device: int) -> dict:
+    """Measured FP32, packed-FP32 and FP64 FMA throughput of this GPU (TFLOP/s), once per run."""
+    if not _PIPE:
+        from paper_2504_04465_b300 import lbmtree as lt
+        for k in ("fp32", "fp32x2", "fp64"):
+            _PIPE[k] = lt.pipe_peak(k, device, 8192)[0] / 1e12
+        _PIPE["how"] = ("lbm_pipe_peak: one wave of 256-thread blocks, 8 independent FMA chains per thread, "
+                        "best of 5 launches; fp32x2 = packed fma.rn.f32x2, the FP32 lanes' limit")
+    return _PIPE
+
+
+def roofline(updates: float, ms: float, bytes_per_update: float, pipe: str | None, flops_path: str | None,
+             device: int) -> dict:
+    """HBM and pipe fractions of a timed path: achieved bytes (algorithmic, per update) and
+    executed flops (captured, per update) over the event-timed duration, against the measured
+    HBM copy bandwidth and the measured pipe peak; frac is the larger of the two (the roofline
+    is the slower of the two limits)."""
+    hbm, kind = peaks()
+    gbs = bytes_per_update * updates / (ms * 1e-3) / 1e9
+    out = {"bytes_per_update": bytes_per_update, "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_peak_kind": kind,
+           "hbm_frac": gbs / hbm}
+    frac, bound = gbs / hbm, "hbm"
+    if pipe:
+        fpu, note = counter(flops_path, "flops") if flops_path else (None, "not captured")
+        pk = pipe_peaks(device)["fp32x2" if pipe == "fp32" else "fp64"]
+        out.update({"pipe": pipe, "flops_per_update": fpu, "flops_source": note, "pipe_peak_tflops": pk})
+        if fpu is not None:
+            tf = fpu * updates / (ms * 1e-3) / 1e12
+            out.update({"achieved_tflops": tf, "pipe_frac": tf / pk})
+            if tf / pk > frac:
+                frac, bound = tf / pk, pipe
+    out.update({"frac": frac, "bound": bound})
+    return out
 
 
 class ClockSampler:
@@ -166,6 +290,50 @@ def oracle_updates(counts, t0, n):
     return sum(c for t in range(t0, t0 + n) for i, c in enumerate(counts) if t % (1 << i) == 0)
 
 
+def _cpu_worker(seconds: float):
+    """One oracle replica on the reduced sphere for about ``seconds``: (cell updates, seconds)."""
+    s, counts = cpu_sample(0)
+    t0 = time.perf_counter()
+    nf = 0
+    while time.perf_counter() - t0 < seconds:
+        s.fine_iteration()
+        nf += 1
+    return oracle_updates(counts, 0, nf), time.perf_counter() - t0, nf
+
+
+def cpu_baseline(seconds: float, max_workers: int = 32) -> dict:
+    """The oracle on the host cores: one process, then independent replicas in a process pool
+    (spawned, one single-threaded worker per core up to max_workers), whole-pool updates over
+    the pool's wall time."""
+    import multiprocessing as mp
+    upd, dt, nf = _cpu_worker(seconds)
+    one = {"value": upd / dt / 1e6, "unit": "MLUPS", "cores": 1,
+           "sample": f"{nf} fine iterations in {dt:.1f} s"}
+    n = max(1, min(os.cpu_count() or 1, max_workers))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_cpu_worker, [seconds] * n)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    tot = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": tot / busy / 1e6, "unit": "MLUPS", "cores": n, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, reduced sphere workload (256x128x128, D=16, 4 levels): {n} independent "
+                       f"single-threaded replicas in a spawned process pool ({os.cpu_count()} host cores, at most "
+                       f"{max_workers} workers), {sum(r[2] for r in res)} fine iterations in all, updates over the "
+                       f"slowest replica's {busy:.1f} s (pool wall time with start-up {wall:.1f} s)"),
+            "one_core": one}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -188,6 +356,117 @@ def run_reference(args, world, rank):
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ cases of the kernel paths
+def _init_ctx(ctx, fields):
+    """Initial fields from fields(level, coords) -> (rho, u[, T]) at every listed cell."""
+    lv, xyz, _ = ctx.cells()
+    n, D = lv.size, ctx.dim
+    rho, u, T = np.ones(n), np.zeros((D, n)), np.zeros(n)
+    comp = False
+    for L in np.unique(lv):
+        m = lv == L
+        r = fields(int(L), xyz[m, :D])
+        rho[m], u[:, m] = r[0], r[1]
+        if len(r) > 2:
+            T[m], comp = r[2], True
+    ctx.init_fields(rho, u, T if comp else None)
+
+
+def sod_numerical_case(lat, grid, L, stream, local):
+    """The Sec. 5 Sod benchmark case (numerical equilibrium, FP32 populations and FP32 Newton)."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    grids = {"unif": I.sod_spec(L, L), "band": I.sod_spec(L, L, 2, (L // 4, 3 * L // 4)),
+             "sqr": I.GridSpec(2, (L, L), 2, [(0, (L // 4, L // 4), (3 * L // 4, 3 * L // 4))], (False, True),
+                               {"x-": ("neumann",), "x+": ("neumann",)})}
+    T0 = {"D2Q21": 0.9, "D2Q37": 1.0}[lat]       # inviscid reference temperatures of Sec. 4.2
+    ctx = lt.Context(2, device=local, stream=stream)
+    ctx.configure(grids[grid], lat, "num_ddf", "f32", nu0=0.0, T0=T0, sensor_A=1.5, newton_fp32=True)
+    _init_ctx(ctx, lambda lev, c: I.sod_fields(I.cell_centres(c, lev), L, T0))
+    # the timed window starts once the three waves have formed: t = 0.1 L / c_s (finest units)
+    fine = int(0.1 * L / np.sqrt(1.4 * T0))
+    return ctx, T0, fine
+
+
+def naca37_case(chord, storage, stream, local, n_levels=5):
+    """BASELINE configuration 3b: D2Q37 polynomial DDF around a NACA0012 at zero incidence,
+    Mach 0.8 subsonic inlet (density extrapolated), Re 1e4 on the chord, sensor A = 1.35."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    mach, T0, gamma = 0.8, lt.lattice_cs2("D2Q37"), 1.4
+    spec = I.naca_spec(chord, mach, T0, gamma, n_levels=n_levels, supersonic=False)
+    ctx = lt.Context(2, device=local, stream=stream)
+    ctx.configure(spec, "D2Q37", "poly_ddf", storage, nu0=mach * np.sqrt(gamma * T0) * chord / 1e4, gamma=gamma,
+                  sensor_A=1.35)
+    _init_ctx(ctx, lambda lev, c: I.naca_fields(lev, c, mach, T0, gamma))
+    return ctx
+
+
+def counters_case(path, stream, local):
+    """(context, coarse steps before the counted step) of a captured kernel path."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    fam, case = path.split(":")
+    if fam == "d3q27":
+        ctx = make_context(I.sphere_spec(2), case, local, stream, False, 2, DEFAULT_BLOCK[case], DEFAULT_VARIANT[case])
+        ctx.init_fields(*host_fields(ctx))
+        return ctx, 3
+    if fam == "d2q9":
+        ctx = lt.Context(2, device=local, stream=stream)
+        ctx.configure(I.taylor_green_spec(2048, 0, 0, 1), "D2Q9", "rr", case, nu0=0.01)
+        _init_ctx(ctx, lambda lev, c: I.taylor_green_fields(I.cell_centres(c, lev), 2048, 1, 0.05, 1.0 / 3.0))
+        return ctx, 3
+    if fam == "d2q37p":
+        geom, st = case.split("_")
+        if geom == "sod":
+            ctx = lt.Context(2, device=local, stream=stream)
+            ctx.configure(I.sod_spec(4096, 64), "D2Q37", "poly_ddf", st, nu0=0.0, sensor_A=1.5)
+            T0 = lt.lattice_cs2("D2Q37")
+            _init_ctx(ctx, lambda lev, c: I.sod_fields(I.cell_centres(c, lev), 4096, T0))
+            return ctx, 3
+        return naca37_case(256, st, stream, local), 3
+    if fam == "d2q21w":
+        n = 1024
+        ctx = lt.Context(2, device=local, stream=stream)
+        ctx.configure(I.GridSpec(2, (n, n), 1, [], (True, True)), "D2Q21", "rr", case, nu0=0.01)
+        _init_ctx(ctx, lambda lev, c: (np.ones(c.shape[0]), np.stack(
+            [0.05 * np.sin(2 * np.pi * I.cell_centres(c, lev)[:, 1] / n), np.zeros(c.shape[0])])))
+        return ctx, 3
+    if fam in ("d2q21n32", "d2q37n32"):
+        lat = "D2Q21" if fam == "d2q21n32" else "D2Q37"
+        ctx, _, fine = sod_numerical_case(lat, case, 2048, stream, local)
+        return ctx, max(3, fine // (2 ** (ctx.stats().n_levels - 1)))
+    if fam == "d2q21n64":
+        P = dict(LEARNED, chord=256)
+        spec = I.naca_spec(P["chord"], P["mach"], P["T0"], P["gamma"])
+        u_in = P["mach"] * np.sqrt(P["gamma"] * P["T0"])
+        ctx = lt.Context(2, device=local, stream=stream)
+        ctx.configure(spec, "D2Q21", "num_ddf", "f32", nu0=u_in * P["chord"] / P["Re"], T0=P["T0"], gamma=P["gamma"],
+                      sensor_A=P["sensor_A"], guess=case)
+        _init_ctx(ctx, lambda lev, c: I.naca_fields(lev, c, P["mach"], P["T0"], P["gamma"]))
+        return ctx, 3
+    raise ValueError(path)
+
+
+def run_counters(args, local):
+    """Run one captured kernel path: warm-up coarse steps, then one coarse step inside the NVTX
+    range "timed" (no graph, so an ncu capture filtered on that range sees each launch)."""
+    import torch
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx, pre = counters_case(args.counters, stream.cuda_stream, local)
+    ctx.step(pre)
+    ctx.sync()
+    s0 = ctx.stats()
+    torch.cuda.nvtx.range_push("timed")
+    ctx.step(1)
+    ctx.sync()
+    torch.cuda.nvtx.range_pop()
+    s1 = ctx.stats()
+    it = (s1.newton_iter_sum - s0.newton_iter_sum) / max(1, s1.newton_updates - s0.newton_updates)
+    print(json.dumps({"counters": args.counters, "cell_updates": int(s1.cell_updates),
+                      "launches": int(s1.kernel_launches - s0.kernel_launches), "newton_iterations": it,
+                      "source_hash": source_hash(PATH_SOURCES[args.counters.split(":")[0]])}), flush=True)
+    ctx.close()
 
 
 # ------------------------------------------------------------------ forms beside the plain FP32 method
@@ -237,12 +516,9 @@ def form_fp16(args, stream, local, f32_ms):
         errs[st] = _moment_err(c, ref, types)
         c.close()
     ref.close()
-    bpu = BYTES_PER_UPDATE["f16dev"]
-    peak, kind = peaks()
     return {"workload": "same as the main line, populations stored as binary16 deviations from w rho_ref",
             "ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS", "speedup_vs_f32": f32_ms / ms,
-            "roofline": {"bound": "hbm", "bytes_per_update": bpu, "achieved": bpu * upd / ms / 1e6, "peak": peak,
-                         "frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind},
+            "roofline": roofline(upd, ms, BYTES_PER_UPDATE["f16dev"], "fp32", "d3q27:f16dev", local),
             "err_vs_f64": errs,
             "err_case": "reduced sphere (256x128x128, D=16, 4 levels), 20 coarse steps, relative L2 over bulk and "
                         "boundary cells against the FP64 path"}
@@ -303,7 +579,7 @@ def form_learned(args, stream, local):
         held[g] = {"mean_iters": float(it[it >= 0].mean()) if (it >= 0).any() else None,
                    "nonconverged": int((it < 0).sum()),
                    "max_abs_dlambda_vs_zero_guess": float(np.abs(d_l.cpu().numpy() - lam_ref[ntr:]).max())}
-    def timed_runs(K, tune):
+    def timed_runs(K, tune, fp64):
         out = {}
         for g in ("poly", "mlp", "warm"):
             ctx.set_guess(g)
@@ -317,14 +593,16 @@ def form_learned(args, stream, local):
                       "mean_newton_iters": (s1.newton_iter_sum - s0.newton_iter_sum) /
                       max(1, s1.newton_updates - s0.newton_updates),
                       "nonconverged": s1.newton_nonconverged - s0.newton_nonconverged,
-                      "variant_min_blocks": ctx.variants()[v]}
+                      "variant_min_blocks": ctx.variants()[v],
+                      "roofline": roofline(s1.cell_updates, ms, 464, "fp64" if fp64 else "fp32",
+                                           f"d2q21n64:{g}" if fp64 else None, local)}
         return out
 
-    runs = timed_runs(1, False)
+    runs = timed_runs(1, False, True)
     # the same comparison with the solve on the FP32 pipe (tolerance 1e-5)
     ctx.set_newton_precision(True, 1e-5)
     try:
-        runs32 = timed_runs(3, True)
+        runs32 = timed_runs(3, True, False)
         fp32 = {"tol": 1e-5, "by_guess": runs32,
                 "speedup_mlp_vs_poly": runs32["poly"]["ms_per_step"] / runs32["mlp"]["ms_per_step"],
                 "speedup_vs_fp64_warm": runs["warm"]["ms_per_step"] / runs32["warm"]["ms_per_step"]}
@@ -351,8 +629,8 @@ def form_d2q37(args, stream, local):
     from paper_2504_04465_b300 import lbmtree as lt
     out = {"workload": "Sod shock tube (rho, p) = (1, 1) | (0.125, 0.1), T = T0 p / rho, T0 = c_s^2 of D2Q37, "
                        "Neumann ends, periodic across, inviscid with the kinetic sensor (A = 1.5)",
-           "bytes_per_update": {"f32": 592, "f64": 1184}}
-    peak, kind = peaks()
+           "bytes_per_update": {"f32": 592, "f64": 1184},
+           "flops_note": "flops per update captured on the 4096x64 tube"}
     cases = {"4096x64": I.sod_spec(4096, 64), "4096x64_band": I.sod_spec(4096, 64, 2, (1024, 3072)),
              "16384x512": I.sod_spec(16384, 512)}
     for name, spec in cases.items():
@@ -372,7 +650,8 @@ def form_d2q37(args, stream, local):
             ctx.sync()
             bpu = 592 if st == "f32" else 1184
             out[f"{name}_{st}"] = {"ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS",
-                                   "hbm_frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind}
+                                   "roofline": roofline(upd, ms, bpu, "fp32" if st == "f32" else "fp64",
+                                                        f"d2q37p:sod_{st}", local)}
             ctx.close()
     return out
 
@@ -384,8 +663,8 @@ def form_d2q21_weak(args, stream, local):
     n = 4096 // args.scale
     spec = I.GridSpec(2, (n, n), 1, [], (True, True))
     out = {"workload": f"D2Q21 weakly compressible, periodic {n}x{n}, u_x = 0.05 sin(2 pi y / L), rho = 1, "
-                       "nu0 = 0.01", "bytes_per_update": 168, "unit": "MLUPS"}
-    peak, kind = peaks()
+                       "nu0 = 0.01", "bytes_per_update": 168, "unit": "MLUPS",
+           "flops_note": "flops per update captured on the RR model at 1024^2"}
     for model in ("rr", "bgk"):
         ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
         ctx.configure(spec, "D2Q21", model, "f32", nu0=0.01)
@@ -399,8 +678,8 @@ def form_d2q21_weak(args, stream, local):
         ms = _event_ms(stream, lambda: ctx.step(K)) / K
         ctx.sync()
         upd = ctx.stats().cell_updates
-        out[model] = {"ms_per_step": ms, "value": upd / ms / 1e3, "hbm_frac": 168 * upd / ms / 1e6 / peak,
-                      "peak_kind": kind}
+        out[model] = {"ms_per_step": ms, "value": upd / ms / 1e3,
+                      "roofline": roofline(upd, ms, 168, "fp32", "d2q21w:f32" if model == "rr" else None, local)}
         ctx.close()
     return out
 
@@ -411,30 +690,23 @@ def form_sod_numerical(args, stream, local):
     populations and FP32 Newton (tolerance 1e-5, warm start), inviscid with the kinetic sensor
     (A = 1.5), on the L x L domain uniform and with the refinement patches of Sec. 4.2 (band:
     x/L in [1/4, 3/4); sqr: a centred square of side L/2; hori: the half y/L < 1/2, whose
-    interface meets the Neumann faces, which the grid builder refuses); L counts finest cells."""
-    from paper_2504_04465_b300 import lbmtree as lt
+    interface meets the Neumann faces, which the grid builder refuses); L counts finest cells.
+    The timed window starts after t = 0.1 L / c_s, once the rarefaction, contact and shock have
+    formed (the paper times whole runs; the first steps of the tube, nearly at rest, need almost
+    no Newton iterations and would flatter the solver)."""
     L = 8192 // args.scale                        # --scale 4: the 2048^2 profiling case
-    grids = {"unif": I.sod_spec(L, L), "band": I.sod_spec(L, L, 2, (L // 4, 3 * L // 4)),
-             "sqr": I.GridSpec(2, (L, L), 2, [(0, (L // 4, L // 4), (3 * L // 4, 3 * L // 4))], (False, True),
-                               {"x-": ("neumann",), "x+": ("neumann",)}),
-             "hori": I.GridSpec(2, (L, L), 2, [(0, (0, 0), (L, L // 2))], (False, True),
-                                {"x-": ("neumann",), "x+": ("neumann",)})}
-    T0s = {"D2Q21": 0.9, "D2Q37": 1.0}           # inviscid reference temperatures of Sec. 4.2
     out = {"workload": f"Sod shock tube on {L}x{L} (finest cells), (rho, p) = (1, 1) | (0.125, 0.1), "
                        "T = T0 p / rho, Neumann ends, periodic across, inviscid, kinetic sensor A = 1.5",
-           "storage": "f32", "newton": "fp32, tol 1e-5, warm start", "unit": "MLUPS (cell updates per second)"}
+           "storage": "f32", "newton": "fp32, tol 1e-5, warm start", "unit": "MLUPS (cell updates per second)",
+           "bytes_per_update": {"D2Q21": 464, "D2Q37": 720},
+           "bytes_note": "f and g FP32 read and written, the eight FP64 multipliers read and written",
+           "flops_note": "flops per update captured on the 2048^2 tube in the same window"}
     for lat in (("D2Q21", "D2Q37") if args.sod_lattices == "all" else args.sod_lattices.split(",")):
         for gname in (args.sod_grids.split(",")):
-            spec = grids[gname]
-            ctx = lt.Context(2, device=local, stream=stream.cuda_stream)
-            ctx.configure(spec, lat, "num_ddf", "f32", nu0=0.0, T0=T0s[lat], sensor_A=1.5, newton_fp32=True)
+            ctx, T0, fine = sod_numerical_case(lat, gname, L, stream.cuda_stream, local)
             ctx.use_graph(True)
-            lv, xyz, _ = ctx.cells()
-            rho, u, T = I.sod_fields(I.cell_centres(xyz[:, :2], lv), L, T0s[lat])
-            del xyz
-            ctx.init_fields(rho, u, T)
-            del rho, u, T
-            ctx.step(2)
+            nl = ctx.stats().n_levels
+            ctx.step(max(1, fine // 2 ** (nl - 1)))     # to t = 0.1 L / c_s
             v, tune_ms = ctx.autotune(2)                # occupancy variant of the step kernels
             st0 = ctx.stats()
             K = 4
@@ -443,14 +715,45 @@ def form_sod_numerical(args, stream, local):
             st1 = ctx.stats()
             upd = st1.cell_updates
             it = (st1.newton_iter_sum - st0.newton_iter_sum) / max(1, st1.newton_updates - st0.newton_updates)
-            out[f"{lat}_{gname}"] = {"cells": int(lv.size), "ms_per_step": ms, "value": upd / ms / 1e3,
+            fam = "d2q21n32" if lat == "D2Q21" else "d2q37n32"
+            out[f"{lat}_{gname}"] = {"cells": int(sum(st1.n_cells[:nl])), "ms_per_step": ms, "value": upd / ms / 1e3,
+                                     "window_start_fine_iteration": int(st0.fine_iterations),
                                      "newton_iterations": it, "nonconverged": int(st1.newton_nonconverged),
                                      "variant_min_blocks": ctx.variants()[v],
-                                     "autotune_ms": dict(zip(map(str, ctx.variants()), tune_ms))}
+                                     "autotune_ms": dict(zip(map(str, ctx.variants()), tune_ms)),
+                                     "roofline": roofline(upd, ms, 464 if lat == "D2Q21" else 720, "fp32",
+                                                          f"{fam}:{gname}", local)}
             ctx.close()
     out["paper_a100"] = {"note": "Sec. 5 table, A100-SXM4, other machine: context only",
                          "D2Q21": {"unif": 618.5, "hori": 555.9, "band": 588.2, "sqr": 544.4},
                          "D2Q37": {"unif (L = 2^12)": 286.9, "hori": 263.0, "band": 307.4, "sqr": 266.1}}
+    return out
+
+
+def form_naca37(args, stream, local):
+    """BASELINE configuration 3b: D2Q37 polynomial DDF with the sensor around a NACA0012 at
+    Mach 0.8 and Re 1e4 on 5 levels (chord 2048 finest cells, Sec. 6.3's transonic airfoil),
+    FP32 against FP64 populations."""
+    chord = 2048 // args.scale
+    out = {"workload": f"D2Q37 polynomial DDF, NACA0012 chord {chord} finest cells, zero incidence, Mach 0.8 "
+                       "(density extrapolated at the inlet), Re 1e4, sensor A = 1.35, 5 levels in [-15C, 15C]^2",
+           "step": "one coarse step = 16 fine iterations", "bytes_per_update": {"f32": 592, "f64": 1184},
+           "flops_note": "flops per update captured on the same grid at chord 256"}
+    for st in ("f32", "f64"):
+        ctx = naca37_case(chord, st, stream.cuda_stream, local)
+        ctx.use_graph(True)
+        ctx.step(2)
+        st0 = ctx.stats()
+        K = 4 if st == "f32" else 2
+        ms = _event_ms(stream, lambda: ctx.step(K)) / K
+        ctx.sync()
+        upd = st0.cell_updates
+        out[st] = {"cells": int(sum(st0.n_cells[:st0.n_levels])), "n_eq": st0.n_eq, "ms_per_step": ms,
+                   "value": upd / ms / 1e3, "unit": "MLUPS",
+                   "roofline": roofline(upd, ms, 592 if st == "f32" else 1184, "fp32" if st == "f32" else "fp64",
+                                        f"d2q37p:naca_{st}", local)}
+        ctx.close()
+    out["speedup_f32_vs_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
     return out
 
 
@@ -459,8 +762,7 @@ def form_d2q9(args, stream, local):
     benchmarks are D2Q9 at 2^13 x 2^13): a uniform 8192^2 grid and a 4096^2 coarse grid with its
     central half refined once; FP32 and FP64 populations."""
     from paper_2504_04465_b300 import lbmtree as lt
-    out = {"bytes_per_update": {"f32": 72, "f64": 144}}
-    peak, kind = peaks()
+    out = {"bytes_per_update": {"f32": 72, "f64": 144}, "flops_note": "flops per update captured on a uniform 2048^2 grid"}
     s = 1 if args.scale == 1 else 4
     cases = {f"uniform_{8192 // s}": (I.taylor_green_spec(8192 // s, 0, 0, 1), 8192 // s, 1),
              f"two_level_{4096 // s}": (I.taylor_green_spec(4096 // s, 1024 // s, 3072 // s, 2), 4096 // s, 2)}
@@ -479,7 +781,8 @@ def form_d2q9(args, stream, local):
             ctx.sync()
             bpu = 72 if st == "f32" else 144
             out[f"{name}_{st}"] = {"cells": int(lv.size), "ms_per_step": ms, "value": upd / ms / 1e3, "unit": "MLUPS",
-                                   "hbm_frac": bpu * upd / ms / 1e6 / peak, "peak_kind": kind}
+                                   "roofline": roofline(upd, ms, bpu, "fp32" if st == "f32" else "fp64", f"d2q9:{st}",
+                                                        local)}
             ctx.close()
     return out
 
@@ -584,12 +887,13 @@ def run_ours(args, world, rank, local):
     bpu = BYTES_PER_UPDATE[args.storage]
     achieved = bpu * updates_per_step * args.steps / (ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = NCU_TRAFFIC_PER_UPDATE.get(args.storage)
+    traffic, tnote = counter(f"d3q27:{args.storage}", "dram")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "bytes_per_update": bpu,
             "per": "coarse step: the interior and general step kernels of 8 fine iterations (event-timed together)",
-            "traffic": None if (traffic is None or args.scale != 1) else traffic * updates_per_step,
-            "traffic_per_update": traffic if args.scale == 1 else None}
+            "traffic": None if traffic is None else traffic * updates_per_step, "traffic_per_update": traffic,
+            "traffic_source": tnote + ("" if traffic is None else
+                                       " (DRAM bytes per update at half extents, times this step's updates)")}
     # end to end through the public API with host buffers: upload the fields, step, read the
     # conserved totals every step and the moments at the end
     e2e = None
@@ -622,16 +926,7 @@ def run_ours(args, world, rank, local):
         return
     cpu = None
     if not args.no_cpu:
-        s, counts = cpu_sample(0)
-        t0 = time.perf_counter()
-        nf = 0
-        while time.perf_counter() - t0 < args.cpu_seconds:
-            s.fine_iteration()
-            nf += 1
-        dt = time.perf_counter() - t0
-        cpu = {"value": oracle_updates(counts, 0, nf) / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, reduced sphere workload (256x128x128, D=16, 4 levels), {nf} fine "
-                         f"iterations in {dt:.1f} s"}
+        cpu = cpu_baseline(args.cpu_seconds)
     forms = None
     if not args.no_forms and args.storage == "f32":
         forms = {}
@@ -641,7 +936,8 @@ def run_ours(args, world, rank, local):
                          ("d2q37_sod", lambda: form_d2q37(args, stream, local)),
                          ("d2q9_tg", lambda: form_d2q9(args, stream, local)),
                          ("sod_numerical", lambda: form_sod_numerical(args, stream, local)),
-                         ("d2q21_weak", lambda: form_d2q21_weak(args, stream, local))):
+                         ("d2q21_weak", lambda: form_d2q21_weak(args, stream, local)),
+                         ("naca37", lambda: form_naca37(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -659,7 +955,8 @@ def run_ours(args, world, rank, local):
                        "autotune_ms_per_step": tuned,
                        "l2": "inputs larger than L2 (9.7 GB of populations at f32)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "pipe_peaks": pipe_peaks(local), "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clk.summary(), "forms": forms}
     print(json.dumps(line), flush=True)
     if dist:
@@ -677,7 +974,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak",
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37",
                     help="which forms to run (comma list; sod_numerical is the paper's Sec. 5 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",
@@ -688,10 +985,14 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--scale", type=int, default=1, choices=[1, 2, 4],
                     help="1: the full workload; 2, 4: copies with extents divided by 2, 4 (profiling, tests)")
+    ap.add_argument("--counters", default=None,
+                    help="run one kernel path's captured case (e.g. d3q27:f32) for an ncu capture and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.counters:
+        run_counters(args, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

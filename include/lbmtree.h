@@ -247,14 +247,14 @@ int lbm_stats(lbm_ctx* ctx, lbm_stats_t* out);
 int lbm_conserved_noalloc(lbm_ctx* ctx, double* d_out);
 
 /* ---------------------------------------------------------------- measurement */
-/* Floating-point throughput of the FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add pipe of
- * `device`, the compute denominator of the roofline of compute-bound step kernels (no
- * counterpart in the paper).  One wave of resident 256-thread blocks runs 8 independent FMA
- * chains per thread for `iters` rounds (16 flops per round per thread); the best of 5 timed
- * launches after one warm-up gives *flop_per_s (FMA counted as 2 operations) and *ms.  The
- * result is at whatever SM clock the GPU runs at: sample the clock beside it.  Allocates a small
- * output buffer; synchronous. */
-int lbm_pipe_peak(int device, int fp64, int iters, double* flop_per_s, float* ms);
+/* Floating-point throughput of a fused multiply-add pipe of `device`, the compute denominator
+ * of the roofline of compute-bound step kernels (no counterpart in the paper): kind 0 FP32 FMA,
+ * 1 FP64 FMA, 2 packed FP32-pair FMA (fma.rn.f32x2, two FMAs per instruction).  One wave of
+ * resident 256-thread blocks runs 8 independent FMA chains per thread for `iters` rounds; the
+ * best of 5 timed launches after one warm-up gives *flop_per_s (an FMA counts 2 operations) and
+ * *ms.  The result is at whatever SM clock the GPU runs at: sample the clock beside it.
+ * Allocates a small output buffer; synchronous.  LBM_ERR_ARG for another kind. */
+int lbm_pipe_peak(int device, int kind, int iters, double* flop_per_s, float* ms);
 
 /* ---------------------------------------------------------------- checkpoint / restart */
 /* Write the state (populations of both buffers, multipliers, fine iteration counter, device

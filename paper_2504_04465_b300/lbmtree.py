@@ -192,10 +192,14 @@ def lattice_cs2(name: str) -> float:
     return lattice_info(name)["cs2"]
 
 
-def pipe_peak(fp64: bool, device: int = 0, iters: int = 8192) -> tuple[float, float]:
-    """(flop/s, ms) of the FP32 or FP64 fused multiply-add pipe of ``device`` (lbm_pipe_peak)."""
+PIPE_KIND = {"fp32": 0, "fp64": 1, "fp32x2": 2}
+
+
+def pipe_peak(kind: str, device: int = 0, iters: int = 8192) -> tuple[float, float]:
+    """(flop/s, ms) of a fused multiply-add pipe of ``device`` (lbm_pipe_peak): "fp32", "fp64"
+    or "fp32x2" (packed FP32 pairs)."""
     out, ms = C.c_double(), C.c_float()
-    _check(_lib.lbm_pipe_peak(device, int(fp64), iters, C.byref(out), C.byref(ms)), "lbm_pipe_peak")
+    _check(_lib.lbm_pipe_peak(device, PIPE_KIND[kind], iters, C.byref(out), C.byref(ms)), "lbm_pipe_peak")
     return out.value, ms.value
 
 
