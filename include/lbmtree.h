@@ -45,15 +45,17 @@ extern "C" {
 /* ---------------------------------------------------------------- enums */
 /* Velocity sets of Appendix A, Tab. lattices_structure (D3Q27: tensor product of D1Q3). */
 #define LBM_D2Q9   9
+#define LBM_D2Q13 13
 #define LBM_D2Q21 21
 #define LBM_D2Q37 37
 #define LBM_D3Q27 27
 
 /* Collision models (Appendix A): BGK and recursive regularization with the Hermite equilibrium
  * of Eq. GenEq (weakly compressible: D2Q9 and D3Q27 on their tensor-product bases, all storage
- * formats; D2Q21 on every component up to order 3, FP64 and FP32); compressible polyatomic DDF (Eqs. gEq, polyTemp) with the
- * thermal polynomial equilibrium (D2Q37) or with the numerical max-entropy equilibrium of
- * Eq. exponential solved by Newton-Raphson in FP64 or FP32 (D2Q21 and D2Q37, Sec. 4.2). */
+ * formats; D2Q13 and D2Q21 on every component up to order 3, FP64 and FP32); compressible
+ * polyatomic DDF (Eqs. gEq, polyTemp) with the thermal polynomial equilibrium (D2Q37) or with the
+ * numerical max-entropy equilibrium of Eq. exponential solved by Newton-Raphson in FP64 or FP32
+ * (D2Q13, D2Q21 and D2Q37, Sec. 4.2; on D2Q13 the FP32 solve with FP32 populations only). */
 #define LBM_BGK             1
 #define LBM_RR              2
 #define LBM_COMP_POLY       3

@@ -23,7 +23,7 @@ OBJDIR = os.path.join(HERE, "_build")
 SOURCES = [
     "k_d2q37_n32_f32.cu", "k_d2q37_n32_f16.cu", "k_d2q37_n32_f64.cu", "k_d2q37_n64.cu",
     "k_d2q21_n32_f32.cu", "k_d2q21_n32_f16.cu", "k_d2q21_n32_f64.cu", "k_d2q21.cu",
-    "k_d2q37.cu", "k_d3q27.cu", "k_d2q9.cu", "k_d2q21w.cu",
+    "k_d2q37.cu", "k_d2q13.cu", "k_d3q27.cu", "k_d2q9.cu", "k_d2q21w.cu",
     "noalloc.cu", "k_peak.cu", "k_mlp.cu", "k_io.cu", "api.cpp", "builder.cpp", "weights.cpp",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

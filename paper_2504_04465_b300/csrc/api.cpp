@@ -67,6 +67,7 @@ bool find_kernels(int lattice, int model, int storage, const int* blk, bool newt
         case LBM_D2Q9: return find_kernels_d2q9(model, storage, blk, out);
         case LBM_D3Q27: return find_kernels_d3q27(model, storage, blk, out);
         case LBM_D2Q37: return find_kernels_d2q37(model, storage, blk, newton_fp32, out);
+        case LBM_D2Q13: return find_kernels_d2q13(model, storage, blk, newton_fp32, out);
         case LBM_D2Q21:
             return (model == LBM_BGK || model == LBM_RR) ? find_kernels_d2q21w(model, storage, blk, out)
                                                           : find_kernels_d2q21(model, storage, blk, newton_fp32, out);
@@ -158,6 +159,7 @@ struct lbm_ctx {
     double T0() const {
         if (params.T0 > 0) return params.T0;
         if (lattice == LBM_D2Q21) return 2.0 / 3.0;
+        if (lattice == LBM_D2Q13) return 0.5;
         if (lattice == LBM_D2Q37) return constants().cs2_37;
         return 1.0 / 3.0;
     }
@@ -176,9 +178,10 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     a.n_levels = L;
     const int BS = c->grid.BS;
     // tau = nu / theta + 1/2 in each level's units, nu_i = nu_0 / 2^i (Eq. tau_fine_to_coarse);
-    // theta = c_s^2 for the weakly compressible models (1/3, or 2/3 on D2Q21) and T0 for the
-    // compressible ones
-    const double theta = c->comp() ? c->T0() : (c->lattice == LBM_D2Q21 ? 2.0 / 3.0 : 1.0 / 3.0);
+    // theta = c_s^2 for the weakly compressible models (1/3, 1/2 on D2Q13, 2/3 on D2Q21) and T0
+    // for the compressible ones
+    const double theta = c->comp() ? c->T0()
+                                   : (c->lattice == LBM_D2Q21 ? 2.0 / 3.0 : c->lattice == LBM_D2Q13 ? 0.5 : 1.0 / 3.0);
     for (int i = 0; i < L; ++i) {
         const BuiltLevel& bl = c->grid.levels[i];
         LevelDev& d = a.lv[i];
@@ -400,6 +403,7 @@ int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2) {
     switch (lattice) {
         case LBM_D2Q9: q = 9; break;
         case LBM_D3Q27: q = 27; d = 3; break;
+        case LBM_D2Q13: q = 13; r = 2; c2 = 0.5; break;
         case LBM_D2Q21: q = 21; r = 3; c2 = 2.0 / 3.0; break;
         case LBM_D2Q37: q = 37; r = 3; c2 = constants().cs2_37; break;
         default: return fail(LBM_ERR_ARG, "unknown lattice");
@@ -461,7 +465,6 @@ int lbm_create(lbm_ctx** out, int dim, int device, void* stream) {
             const Constants& k = constants();
             e = upload_tables_d2q37(k.w37, k.H37, k.cs2_37);
             if (e == cudaSuccess) e = upload_tables_d2q21(k.w21, k.H21);
-            if (e == cudaSuccess) e = upload_tables_d2q21w(k.w21, k.H21);
             if (e != cudaSuccess) {
                 delete c;
                 return fail(LBM_ERR_CUDA, std::string("constant upload: ") + cudaGetErrorString(e));
@@ -491,7 +494,8 @@ int lbm_destroy(lbm_ctx* c) {
 
 int lbm_set_lattice(lbm_ctx* c, int lattice) {
     if (check_ctx(c)) return LBM_ERR_ARG;
-    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q21 && lattice != LBM_D2Q37 && lattice != LBM_D3Q27)
+    if (lattice != LBM_D2Q9 && lattice != LBM_D2Q13 && lattice != LBM_D2Q21 && lattice != LBM_D2Q37 &&
+        lattice != LBM_D3Q27)
         return fail(LBM_ERR_ARG, "unknown lattice");
     if ((lattice == LBM_D3Q27) != (c->dim == 3)) return fail(LBM_ERR_ARG, "lattice dimension differs from the context");
     if (c->built) return fail(LBM_ERR_STATE, "lattice must be set before lbm_build_grid");
@@ -580,9 +584,11 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     if (!c->lattice || !c->params_set) return fail(LBM_ERR_STATE, "set lattice and collision model first");
     if (c->built) return fail(LBM_ERR_STATE, "grid already built");
     const bool weak = c->model == LBM_BGK || c->model == LBM_RR;
-    if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27 || c->lattice == LBM_D2Q21)) ||
+    if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27 || c->lattice == LBM_D2Q21 ||
+                   c->lattice == LBM_D2Q13)) ||
         (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
-        (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q21 && c->lattice != LBM_D2Q37))
+        (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q13 && c->lattice != LBM_D2Q21 &&
+         c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
     if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
@@ -891,6 +897,7 @@ int lbm_newton_batch(lbm_ctx* c, const double* d_uT, int64_t n, int guess, doubl
     ModelDev m = a.m;
     m.guess = guess;
     if (c->lattice == LBM_D2Q37) launch_newton_batch_d2q37(d_uT, n, m, d_lambda, d_iters, c->stream);
+    else if (c->lattice == LBM_D2Q13) launch_newton_batch_d2q13(d_uT, n, m, d_lambda, d_iters, c->stream);
     else launch_newton_batch_d2q21(d_uT, n, m, d_lambda, d_iters, c->stream);
     CU(cudaGetLastError());
     return LBM_OK;

@@ -32,6 +32,7 @@ bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out
 bool find_kernels_d2q37(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
 bool find_kernels_d2q21(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
 bool find_kernels_d2q21w(int model, int storage, const int* block, KernelSet& out);
+bool find_kernels_d2q13(int model, int storage, const int* block, bool newton_fp32, KernelSet& out);
 
 int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
                      float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);
@@ -40,12 +41,12 @@ void launch_scatter(const int* slot, long long count, const double* src, long lo
 void launch_gather(const int* slot, long long count, const double* src, long long src_stride, int ncomp, double* dst,
                    long long dst_stride, cudaStream_t s);
 void launch_newton_batch_d2q21(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s);
+void launch_newton_batch_d2q13(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s);
 void launch_newton_batch_d2q37(const double* uT, long long n, const ModelDev& m, double* lam, int* iters, cudaStream_t s);
 
 // Constant tables of the D2Q37 and D2Q21 translation units (current device).
 cudaError_t upload_tables_d2q37(const double* w37, const double* H37, double cs2_37);
 cudaError_t upload_tables_d2q21(const double* w21, const double* H21);
-cudaError_t upload_tables_d2q21w(const double* w21, const double* H21);
 
 // weights.cpp: D2Q37 weights re-derived from isotropy, Hermite tables of both lattices
 void lattice_constants(double w37[37], double H37[37 * 15], double* cs2_37, double w21[21], double H21[21 * 10]);

@@ -1,7 +1,7 @@
 // Velocity sets and cell types of the CUDA path (host and device).
 //
 // Appendix A, Tab. lattices_structure of arXiv 2504.04465 gives the symmetry groups of D2Q9,
-// D2Q21 and D2Q37; D3Q27 is the tensor product of the 1D three-velocity set.  The CUDA path
+// D2Q13, D2Q21 and D2Q37; D3Q27 is the tensor product of the 1D three-velocity set.  The CUDA path
 // orders every 2D set row-major over (y, x) in [-r, r]^2 and D3Q27 as x + 3y + 9z with
 // components in {-1, 0, 1}.  Both orders are point-symmetric, so the opposite of velocity q is
 // Q - 1 - q.  Weights are not stored here: D2Q9/D2Q21/D3Q27 use the printed fractions and D2Q37
@@ -20,9 +20,13 @@ namespace lbm {
 // cell types of the layout (host builder and kernels)
 enum CellType : unsigned char { C_ABSENT = 0, C_FLUID = 1, C_CGHOST = 2, C_FGHOST = 3, C_BC = 4, C_SOLID = 5 };
 
-enum LatticeId { L_D2Q9 = 9, L_D2Q21 = 21, L_D2Q37 = 37, L_D3Q27 = 27 };
+enum LatticeId { L_D2Q9 = 9, L_D2Q13 = 13, L_D2Q21 = 21, L_D2Q37 = 37, L_D3Q27 = 27 };
 
 // membership of (x, y) in the 2D sets (|x|, |y| <= 3)
+LBM_HD constexpr bool in_d2q13(int x, int y) {
+    const int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+    return ax + ay <= 2;                                // (0,0) (1,0) (1,1) (2,0)
+}
 LBM_HD constexpr bool in_d2q21(int x, int y) {
     int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
     if (ax > 3 || ay > 3) return false;
@@ -38,6 +42,16 @@ LBM_HD constexpr bool in_d2q37(int x, int y) {
 }
 
 // component (x if want_y == 0, else y) of velocity q of a 2D set enumerated row-major over (y, x)
+LBM_HD constexpr int enum13(int q, int want_y) {
+    int k = 0;
+    for (int y = -2; y <= 2; ++y)
+        for (int x = -2; x <= 2; ++x)
+            if (in_d2q13(x, y)) {
+                if (k == q) return want_y ? y : x;
+                ++k;
+            }
+    return 0;
+}
 LBM_HD constexpr int enum21(int q, int want_y) {
     int k = 0;
     for (int y = -3; y <= 3; ++y)
@@ -61,6 +75,12 @@ LBM_HD constexpr int enum37(int q, int want_y) {
 
 // the same enumerations as switch tables: folded to constants where q is known at compile time
 // (unrolled loops), a jump table otherwise
+LBM_HD constexpr int d2q13_x(int q) {
+    switch (q) { case 1: return -1; case 3: return 1; case 4: return -2; case 5: return -1; case 7: return 1; case 8: return 2; case 9: return -1; case 11: return 1; default: return 0; }
+}
+LBM_HD constexpr int d2q13_y(int q) {
+    switch (q) { case 0: return -2; case 1: return -1; case 2: return -1; case 3: return -1; case 9: return 1; case 10: return 1; case 11: return 1; case 12: return 2; default: return 0; }
+}
 LBM_HD constexpr int d2q21_x(int q) {
     switch (q) { case 0: return 0; case 1: return -2; case 2: return 0; case 3: return 2; case 4: return -1; case 5: return 0; case 6: return 1; case 7: return -3; case 8: return -2; case 9: return -1; case 10: return 0; case 11: return 1; case 12: return 2; case 13: return 3; case 14: return -1; case 15: return 0; case 16: return 1; case 17: return -2; case 18: return 0; case 19: return 2; case 20: return 0; default: return 0; }
 }
@@ -76,13 +96,15 @@ LBM_HD constexpr int d2q37_y(int q) {
 
 // the switch tables agree with the enumeration for every velocity (checked at compile time)
 LBM_HD constexpr bool tables_match() {
+    for (int q = 0; q < 13; ++q)
+        if (d2q13_x(q) != enum13(q, 0) || d2q13_y(q) != enum13(q, 1)) return false;
     for (int q = 0; q < 21; ++q)
         if (d2q21_x(q) != enum21(q, 0) || d2q21_y(q) != enum21(q, 1)) return false;
     for (int q = 0; q < 37; ++q)
         if (d2q37_x(q) != enum37(q, 0) || d2q37_y(q) != enum37(q, 1)) return false;
     return true;
 }
-static_assert(tables_match(), "D2Q21/D2Q37 switch tables differ from the enumeration");
+static_assert(tables_match(), "D2Q13/D2Q21/D2Q37 switch tables differ from the enumeration");
 
 // The 13 classes (X, Y) = (|xi_x|, |xi_y|) of the D2Q37 velocities, the centre first, then the
 // axis pairs (X, 0) and (0, Y), then the quadruples (+-X, +-Y)
@@ -109,6 +131,13 @@ template <> struct Lat<27> {
     LBM_HD static constexpr int cx(int q) { return q % 3 - 1; }
     LBM_HD static constexpr int cy(int q) { return (q / 3) % 3 - 1; }
     LBM_HD static constexpr int cz(int q) { return q / 9 - 1; }
+};
+
+template <> struct Lat<13> {
+    static constexpr int Q = 13, D = 2, R = 2;
+    LBM_HD static constexpr int cx(int q) { return d2q13_x(q); }
+    LBM_HD static constexpr int cy(int q) { return d2q13_y(q); }
+    LBM_HD static constexpr int cz(int) { return 0; }
 };
 
 template <> struct Lat<21> {
@@ -141,6 +170,7 @@ inline LatticeDesc lattice_desc(int id) {
     LatticeDesc d{};
     switch (id) {
         case L_D2Q9: fill_desc<Lat<9>>(d); break;
+        case L_D2Q13: fill_desc<Lat<13>>(d); break;
         case L_D2Q21: fill_desc<Lat<21>>(d); break;
         case L_D2Q37: fill_desc<Lat<37>>(d); break;
         case L_D3Q27: fill_desc<Lat<27>>(d); break;

@@ -23,7 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 OK = 0
 ERR = {-1: "ARG", -2: "STATE", -3: "CUDA", -4: "OOM", -5: "GRID", -6: "NEWTON", -7: "NONFINITE",
        -10: "UNSUPPORTED"}
-LATTICE = {"D2Q9": 9, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
+LATTICE = {"D2Q9": 9, "D2Q13": 13, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
 MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4}
 STORAGE = {"f64": 1, "f32": 2, "f16dev": 3}
 FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}

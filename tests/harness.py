@@ -147,6 +147,14 @@ def compare_near(sol, ctx, width=None):
     return worst
 
 
+# Element-wise bound of FP64 populations for the Newton-solved (numerical) equilibria: both sides
+# stop the solve at the first iterate whose largest constraint residual is below 1e-12, and a
+# residual right at that threshold can stop one side an iteration earlier than the other, which
+# leaves individual populations apart by up to about the tolerance (the moments, averaged over
+# the grid, still agree to 1e-15).  Ten times the tolerance.
+POP_TOL_NEWTON = 1e-11
+
+
 def population_map(sol, ctx):
     """perm such that gpu population perm[q] is oracle population q."""
     xi_g = ctx.velocities()[:, : sol.g.D]

@@ -90,6 +90,10 @@ SPECS = [
     ("three_levels", lambda: I.GridSpec(2, (128, 128), 3, [(1, (32, 32), (96, 96)), (0, (48, 48), (80, 80))], (True, True)), "D2Q9", "bgk", None),
     ("reach3_q37", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q37", "poly_ddf", None),
     ("reach3_q21", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q21", "num_ddf", None),
+    ("reach2_q13", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q13", "rr", None),
+    ("reach2_q13_sod", lambda: I.sod_spec(256, 32, 2, (64, 192)), "D2Q13", "num_ddf", None),
+    ("reach2_q13_naca", lambda: I.naca_spec(64, 0.8, 0.35, n_levels=3, supersonic=False, half_domain=3.0,
+                                            level_boxes=I.NACA_BOXES_SMALL), "D2Q13", "num_ddf", None),
     ("sod_band", lambda: I.sod_spec(256, 32, 2, (64, 192)), "D2Q37", "poly_ddf", None),
     ("solid", lambda: I.GridSpec(2, (64, 64), 2, [(0, (16, 16), (48, 48))], (True, True),
                                  solids=[{"kind": "sphere", "center": (32.0, 32.0), "radius": 5.0}]), "D2Q9", "rr", None),
@@ -111,7 +115,8 @@ def test_host_builder_matches_oracle(lt, name, mk, latname, model, block):
 
 
 def test_velocity_sets_match_oracle(lt):
-    for latname, dim, model in (("D2Q9", 2, "rr"), ("D2Q21", 2, "num_ddf"), ("D2Q37", 2, "poly_ddf"), ("D3Q27", 3, "rr")):
+    for latname, dim, model in (("D2Q9", 2, "rr"), ("D2Q13", 2, "rr"), ("D2Q21", 2, "num_ddf"), ("D2Q37", 2, "poly_ddf"),
+                                ("D3Q27", 3, "rr")):
         c = lt.Context(dim, device=-1)
         c.set_lattice(latname)
         c.set_collision(model)
@@ -125,9 +130,11 @@ def test_velocity_sets_match_oracle(lt):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_numerical_equilibrium_lattices(lt, storage, fp32):
-    """The numerical equilibrium is built on D2Q21 and D2Q37 (Sec. 4.2), for either Newton
-    precision; the weakly compressible lattices refuse it."""
-    for latname in ("D2Q21", "D2Q37"):
+    """The numerical equilibrium is built on D2Q13, D2Q21 and D2Q37 (Sec. 4.2), for either Newton
+    precision (D2Q13: the FP32 solve with FP32 populations only); D2Q9 refuses it."""
+    for latname in ("D2Q13", "D2Q21", "D2Q37"):
+        if latname == "D2Q13" and fp32 and storage != "f32":
+            continue
         c = lt.Context(2, device=-1)
         c.configure(I.GridSpec(2, (32, 32), 1, [], (True, True)), latname, "num_ddf", storage, T0=0.9,
                     newton_fp32=fp32)
@@ -167,13 +174,13 @@ def test_batch_case_recipe_builds(lt):
 
 
 def test_lattice_info_matches_the_oracle_lattices(lt):
-    for name in ("D2Q9", "D2Q21", "D2Q37", "D3Q27"):
+    for name in ("D2Q9", "D2Q13", "D2Q21", "D2Q37", "D3Q27"):
         info = lt.lattice_info(name)
         ref = L.LATTICES[name]
         assert info["Q"] == ref.Q and info["D"] == ref.D
         assert abs(info["cs2"] - ref.cs2) < 1e-14
     with pytest.raises(lt.LbmError):
-        lt._check(lt._lib.lbm_lattice_info(13, None, None, None, None), "lbm_lattice_info")
+        lt._check(lt._lib.lbm_lattice_info(15, None, None, None, None), "lbm_lattice_info")
 
 
 def test_checkpoint_calls_check_their_arguments(lt, tmp_path):

@@ -62,6 +62,21 @@ def test_d3q27_sphere_f32():
 
 
 @pytest.mark.parametrize("model", ["bgk", "rr"])
+def test_d2q13_weak_f32(model):
+    _, ctx, err = _run("d2q13w-" + model, W21_SPEC, "D2Q13", model, "f32", weak_fields, nu0=NU0)
+    _check(err, {"rho": 1e-5, "u": 1e-5, "near_rho": 1e-5, "near_u": 1e-5})
+    ctx.close()
+
+
+def test_d2q13_numerical_f32_populations():
+    """Sensor off, T0 = 0.35."""
+    _, ctx, err = _run("d2q13n", N21_SPEC, "D2Q13", "num_ddf", "f32", H.smooth_comp_fields((96, 64), 0.35),
+                       nu0=0.01, T0=0.35)
+    _check(err, {"rho": 1e-5, "u": 1e-5, "T": 1e-5, "near_rho": 3e-5, "near_u": 3e-5, "near_T": 3e-5})
+    ctx.close()
+
+
+@pytest.mark.parametrize("model", ["bgk", "rr"])
 def test_d2q21_weak_f32(model):
     _, ctx, err = _run("d2q21w-" + model, W21_SPEC, "D2Q21", model, "f32", weak_fields, nu0=NU0)
     _check(err, {"rho": 1e-5, "u": 1e-5, "near_rho": 1e-5, "near_u": 1e-5})

@@ -186,8 +186,8 @@ def test_d2q21_numerical_two_level_f64():
     assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
     near = H.compare_near(sol, ctx)
     assert near["n"] > 0 and max(near["rho"], near["u"], near["T"]) < 1e-12, near
-    assert H.compare_populations(sol, ctx, "f") < 1e-12
-    assert H.compare_populations(sol, ctx, "g") < 1e-12
+    assert H.compare_populations(sol, ctx, "f") < H.POP_TOL_NEWTON
+    assert H.compare_populations(sol, ctx, "g") < H.POP_TOL_NEWTON
     s = ctx.stats()
     assert s.newton_updates > 0 and s.newton_nonconverged == 0
     assert s.newton_iter_sum / s.newton_updates < 4
@@ -210,8 +210,8 @@ def test_d2q21_supersonic_inlet_f64(guess):
     ctx.step_fine(30)
     err = H.compare_moments(sol, ctx)
     assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
-    assert H.compare_populations(sol, ctx, "f") < 1e-12
-    assert H.compare_populations(sol, ctx, "g") < 1e-12
+    assert H.compare_populations(sol, ctx, "f") < H.POP_TOL_NEWTON
+    assert H.compare_populations(sol, ctx, "g") < H.POP_TOL_NEWTON
 
 
 def test_d2q21_f32_populations_fp64_newton():

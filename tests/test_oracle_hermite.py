@@ -71,7 +71,7 @@ def test_thermal_moments_are_gaussian_hermite_coefficients():
     assert hm.a_eq((0, 1), rho, u, dT)[0] == pytest.approx(0.0)       # u_y = 0, no delta_xy
 
 
-@pytest.mark.parametrize("name", ["D2Q9", "D3Q27", "D2Q21", "D2Q37"])
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27", "D2Q13", "D2Q21", "D2Q37"])
 def test_athermal_equilibrium_moments(name):
     lat = L.LATTICES[name]
     n = 40
@@ -105,7 +105,7 @@ def test_thermal_equilibrium_moments_d2q37():
     assert np.allclose((xi[:, 0] * r2) @ feq, rho * u[0] * (u2 + 4 * T), atol=1e-12, rtol=0)
 
 
-@pytest.mark.parametrize("name", ["D2Q9", "D3Q27", "D2Q21"])
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27", "D2Q13", "D2Q21"])
 def test_rr_invariants(name):
     lat = L.LATTICES[name]
     n = 25
