@@ -309,6 +309,14 @@ int lbm_mlp_forward(const float* d_params, const double* d_x, int64_t n, float* 
  * (both overwritten; t[n*8] FP32 targets in normalised units). */
 int lbm_mlp_grad(const float* d_params, const double* d_x, const float* d_t, int64_t n, float* d_grad,
                  float* d_loss, void* stream);
+/* The same forward pass and gradient with the 64-wide products (layers 2 and 3 and their
+ * gradients) on the BF16 tensor cores (warp-level mma.sync m16n8k16, FP32 accumulation): the
+ * operands of those products -- the hidden activations, dL/dy and the layer-2 delta -- are
+ * rounded to bfloat16 as the weights are; layer 1, tanh, the biases and dW1 stay FP32.
+ * Same arguments and outputs as lbm_mlp_forward / lbm_mlp_grad. */
+int lbm_mlp_forward_tc(const float* d_params, const double* d_x, int64_t n, float* d_y, void* stream);
+int lbm_mlp_grad_tc(const float* d_params, const double* d_x, const float* d_t, int64_t n, float* d_grad,
+                    float* d_loss, void* stream);
 /* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8) of d_params with moments d_m, d_v;
  * step counts from 1. */
 int lbm_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step, float lr, void* stream);
@@ -324,6 +332,7 @@ typedef struct {
     double lr, lr_final;    /* learning rate, decayed linearly from lr to lr_final */
     uint64_t seed;          /* initial weights and minibatches (counter-based hash) */
     float final_loss;       /* out: loss of the trained network over all n samples */
+    int tensor_cores;       /* 1: gradients by lbm_mlp_grad_tc (BF16 tensor cores), 0: FP32 cores */
 } lbm_mlp_train_params;
 
 /* Train the context's network on n device samples: uT[n*3] = (u_x, u_y, T) and the converged

@@ -11,6 +11,13 @@ with a fixed per-output offset m and scale s (taken from the training targets). 
 used rounded to bfloat16 (round to nearest even), arithmetic here is FP64.  Loss: half the mean
 over samples of ||y - (lambda_target - m)/s||^2.  Optimiser: Adam (beta1 0.9, beta2 0.999,
 eps 1e-8) on FP32-representable master weights.
+
+Tensor-core form (``bf16_act=True``): the kernels that run the matrix products of 64-wide
+layers on BF16 tensor cores round the operands of those products to bfloat16 and accumulate in
+FP32.  This form rounds exactly those operands: the layer-1 output h1 entering layer 2, h2
+entering layer 3; in the backward pass dL/dy entering dW3 and dL/dh2, h2 entering dW3, the
+layer-2 delta d2 entering dW2 and dL/dh1, and h1 entering dW2.  Layer 1 (three inputs), its
+gradient dW1, the biases, tanh and its derivative 1 - h^2 use unrounded values.
 """
 from __future__ import annotations
 
@@ -38,26 +45,31 @@ def compute_weights(params: dict, rounded: bool = True) -> dict:
     return out
 
 
-def forward(params: dict, x: np.ndarray, rounded: bool = True):
+def _op(a, bf16_act: bool):
+    """A matrix-product operand as the tensor cores see it (bfloat16 of its FP32 value)."""
+    return bf16_round(a).astype(np.float64) if bf16_act else a
+
+
+def forward(params: dict, x: np.ndarray, rounded: bool = True, bf16_act: bool = False):
     """x (n, 3) -> (y (n, 8), cache)."""
     W = compute_weights(params, rounded)
     x = np.asarray(x, dtype=np.float64)
     h1 = np.tanh(x @ W["w1"].T + W["b1"])
-    h2 = np.tanh(h1 @ W["w2"].T + W["b2"])
-    y = h2 @ W["w3"].T + W["b3"]
+    h2 = np.tanh(_op(h1, bf16_act) @ W["w2"].T + W["b2"])
+    y = _op(h2, bf16_act) @ W["w3"].T + W["b3"]
     return y, (W, x, h1, h2)
 
 
-def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray, rounded: bool = True):
+def loss_and_grads(params: dict, x: np.ndarray, t: np.ndarray, rounded: bool = True, bf16_act: bool = False):
     """Loss 1/(2n) sum ||y - t||^2 and its gradients with respect to every parameter."""
-    y, (W, x, h1, h2) = forward(params, x, rounded)
+    y, (W, x, h1, h2) = forward(params, x, rounded, bf16_act)
     n = x.shape[0]
     d3 = (y - t) / n                                   # dL/dy
-    g = {"w3": d3.T @ h2, "b3": d3.sum(axis=0)}
-    d2 = (d3 @ W["w3"]) * (1.0 - h2 * h2)
-    g["w2"] = d2.T @ h1
+    g = {"w3": _op(d3, bf16_act).T @ _op(h2, bf16_act), "b3": d3.sum(axis=0)}
+    d2 = (_op(d3, bf16_act) @ W["w3"]) * (1.0 - h2 * h2)
+    g["w2"] = _op(d2, bf16_act).T @ _op(h1, bf16_act)
     g["b2"] = d2.sum(axis=0)
-    d1 = (d2 @ W["w2"]) * (1.0 - h1 * h1)
+    d1 = (_op(d2, bf16_act) @ W["w2"]) * (1.0 - h1 * h1)
     g["w1"] = d1.T @ x
     g["b1"] = d1.sum(axis=0)
     loss = 0.5 * ((y - t) ** 2).sum() / n

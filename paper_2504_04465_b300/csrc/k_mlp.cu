@@ -133,6 +133,307 @@ __global__ void __launch_bounds__(GS) k_mlp_grad(const float* __restrict__ P, co
     }
 }
 
+// ---------------------------------------------------------------- BF16 tensor-core form
+// The 64-wide products (layers 2 and 3 and their gradients) on the tensor cores: warp-level
+// mma.sync m16n8k16 with bfloat16 operands and FP32 accumulation.  A warp carries 16 samples
+// (the M dimension); layer 1 (three inputs), tanh, the biases and dW1 stay on the FP32 cores.
+// Fragments (g = lane / 4, t = lane % 4): A (16 x 16, row-major) holds (g, 2t..2t+1),
+// (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..); B (16 x 8, k x n) holds (2t..2t+1, g) and
+// (2t+8..2t+9, g); the FP32 accumulator (16 x 8) holds (g, 2t..2t+1) and (g+8, 2t..2t+1).
+// Two adjacent accumulator tiles (columns 0-7 and 8-15) are therefore exactly one A fragment of
+// k = 16, so a layer's output feeds the next product from registers.
+constexpr int TCW = 4;                       // warps per block
+constexpr int TCS = 16 * TCW;                // samples per block
+
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// two values as one register of bfloat16 (the first in the low half)
+__device__ __forceinline__ unsigned pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned*>(&v);
+}
+__device__ __forceinline__ unsigned pack2h(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+// A fragments of k-block kb from an accumulator-layout array v[8][4] (64 columns)
+__device__ __forceinline__ void a_frag(const float (*v)[4], int kb, unsigned* a) {
+    a[0] = pack2(v[2 * kb][0], v[2 * kb][1]);
+    a[1] = pack2(v[2 * kb][2], v[2 * kb][3]);
+    a[2] = pack2(v[2 * kb + 1][0], v[2 * kb + 1][1]);
+    a[3] = pack2(v[2 * kb + 1][2], v[2 * kb + 1][3]);
+}
+
+struct TcSmem {
+    __nv_bfloat16 w2[MLP_H * MLP_H];         // W2[j][i], rounded
+    __nv_bfloat16 w3[MLP_OUT * MLP_H];       // W3[o][i], rounded
+    float p1[MLP_W2];                        // W1 (rounded), b1
+    float b2[MLP_H], b3[MLP_OUT];
+};
+
+__device__ __forceinline__ void tc_load(const float* __restrict__ P, TcSmem& S) {
+    for (int k = threadIdx.x; k < MLP_H * MLP_H; k += blockDim.x) S.w2[k] = __float2bfloat16_rn(P[MLP_W2 + k]);
+    for (int k = threadIdx.x; k < MLP_OUT * MLP_H; k += blockDim.x) S.w3[k] = __float2bfloat16_rn(P[MLP_W3 + k]);
+    for (int k = threadIdx.x; k < MLP_W2; k += blockDim.x) S.p1[k] = k < MLP_B1 ? bf16r(P[k]) : P[k];
+    for (int k = threadIdx.x; k < MLP_H; k += blockDim.x) S.b2[k] = P[MLP_B2 + k];
+    if (threadIdx.x < MLP_OUT) S.b3[threadIdx.x] = P[MLP_B3 + threadIdx.x];
+}
+
+// forward pass of the warp's 16 samples (rows g and g+8 are samples s0 + g, s0 + g + 8):
+// h1, h2 (FP32, accumulator layout) and y (accumulator layout, 8 outputs)
+__device__ __forceinline__ void tc_forward(const TcSmem& S, const float* x /* [2][3] rows g, g+8 */,
+                                           float (*h1)[4], float (*h2)[4], float* y) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int j = 8 * nt + 2 * t + (r & 1);
+            const float* xs = x + 3 * (r >> 1);
+            h1[nt][r] = tanhf(fmaf(S.p1[MLP_W1 + 3 * j], xs[0], fmaf(S.p1[MLP_W1 + 3 * j + 1], xs[1],
+                              fmaf(S.p1[MLP_W1 + 3 * j + 2], xs[2], S.p1[MLP_B1 + j]))));
+        }
+    // layer 2: h2 = tanh(h1 W2^T + b2)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int j0 = 8 * nt + 2 * t;
+        float c[4] = {S.b2[j0], S.b2[j0 + 1], S.b2[j0], S.b2[j0 + 1]};
+        const int jn = 8 * nt + g;            // this lane's column of B
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+            unsigned a[4];
+            a_frag(h1, kb, a);
+            const unsigned b0 = *reinterpret_cast<const unsigned*>(S.w2 + jn * MLP_H + 16 * kb + 2 * t);
+            const unsigned b1 = *reinterpret_cast<const unsigned*>(S.w2 + jn * MLP_H + 16 * kb + 2 * t + 8);
+            mma_bf16(c, a, b0, b1);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h2[nt][r] = tanhf(c[r]);
+    }
+    // layer 3: y = h2 W3^T + b3
+    y[0] = S.b3[2 * t]; y[1] = S.b3[2 * t + 1]; y[2] = y[0]; y[3] = y[1];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        unsigned a[4];
+        a_frag(h2, kb, a);
+        const unsigned b0 = *reinterpret_cast<const unsigned*>(S.w3 + g * MLP_H + 16 * kb + 2 * t);
+        const unsigned b1 = *reinterpret_cast<const unsigned*>(S.w3 + g * MLP_H + 16 * kb + 2 * t + 8);
+        mma_bf16(y, a, b0, b1);
+    }
+}
+
+__device__ __forceinline__ void tc_inputs(const double* __restrict__ X, long long n, long long s0, float* x, bool* live) {
+    const int g = (threadIdx.x & 31) >> 2;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long i = s0 + g + 8 * h;
+        live[h] = i < n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[3 * h + c] = live[h] ? (float)X[3 * i + c] : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(32 * TCW) k_mlp_forward_tc(const float* __restrict__ P, const double* __restrict__ X,
+                                                            long long n, float* __restrict__ Y) {
+    __shared__ TcSmem S;
+    tc_load(P, S);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long s0 = (long long)blockIdx.x * TCS + 16 * w;
+    float x[6];
+    bool live[2];
+    tc_inputs(X, n, s0, x, live);
+    float h1[8][4], h2[8][4], y[4];
+    tc_forward(S, x, h1, h2, y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (live[h]) {
+            const long long i = s0 + g + 8 * h;
+            Y[MLP_OUT * i + 2 * t] = y[2 * h];
+            Y[MLP_OUT * i + 2 * t + 1] = y[2 * h + 1];
+        }
+}
+
+// per-block staging of the backward pass, samples of the whole block
+struct TcBack {
+    __nv_bfloat16 d2[TCS * MLP_H];           // d2[s][j], rounded
+    __nv_bfloat16 h1[TCS * MLP_H];           // h1[s][i], rounded
+    __nv_bfloat16 h2[TCS * MLP_H];           // h2[s][i], rounded
+    __nv_bfloat16 d3[TCS * MLP_OUT];         // d3[s][o], rounded
+    float d2f[TCS * MLP_H], d1f[TCS * MLP_H], d3f[TCS * MLP_OUT], x[TCS * 3], loss[TCW];
+};
+
+__global__ void __launch_bounds__(32 * TCW) k_mlp_grad_tc(const float* __restrict__ P, const double* __restrict__ X,
+                                                         const float* __restrict__ Tg, long long n,
+                                                         float* __restrict__ G, float* __restrict__ loss) {
+    extern __shared__ unsigned char tc_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
+    TcBack& B = *reinterpret_cast<TcBack*>(tc_raw + ((sizeof(TcSmem) + 15) / 16) * 16);
+    tc_load(P, S);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long s0 = (long long)blockIdx.x * TCS + 16 * w;
+    const int ls0 = 16 * w;                  // block-local sample of row 0
+    float x[6];
+    bool live[2];
+    tc_inputs(X, n, s0, x, live);
+    float h1[8][4], h2[8][4], y[4];
+    tc_forward(S, x, h1, h2, y);
+    const float inv_n = 1.0f / (float)n;
+    // d3 = (y - t) / n, loss
+    float d3[4], l = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int h = r >> 1, o = 2 * t + (r & 1);
+        const long long i = s0 + g + 8 * h;
+        const float e = live[h] ? y[r] - Tg[MLP_OUT * i + o] : 0.0f;
+        l = fmaf(e, e, l);
+        d3[r] = e * inv_n;
+        const int ls = ls0 + g + 8 * h;
+        B.d3[MLP_OUT * ls + o] = __float2bfloat16_rn(d3[r]);
+        B.d3f[MLP_OUT * ls + o] = d3[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) B.loss[w] = 0.5f * l * inv_n;
+    // d2 = (d3 W3) * (1 - h2^2): k = 8 outputs, padded to 16 with zeros
+    float d2[8][4];
+    {
+        const unsigned a[4] = {pack2(d3[0], d3[1]), pack2(d3[2], d3[3]), 0u, 0u};
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int in = 8 * nt + g;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            const unsigned b0 = pack2h(S.w3[(2 * t) * MLP_H + in], S.w3[(2 * t + 1) * MLP_H + in]);
+            mma_bf16(c, a, b0, 0u);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                d2[nt][r] = c[r] * (1.0f - h2[nt][r] * h2[nt][r]);
+                const int ls = ls0 + g + 8 * (r >> 1), j = 8 * nt + 2 * t + (r & 1);
+                B.d2[MLP_H * ls + j] = __float2bfloat16_rn(d2[nt][r]);
+                B.h2[MLP_H * ls + j] = __float2bfloat16_rn(h2[nt][r]);
+                B.d2f[MLP_H * ls + j] = d2[nt][r];
+            }
+        }
+    }
+    // d1 = (d2 W2) * (1 - h1^2)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int in = 8 * nt + g;
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+            unsigned a[4];
+            a_frag(d2, kb, a);
+            const int j0 = 16 * kb + 2 * t;
+            const unsigned b0 = pack2h(S.w2[j0 * MLP_H + in], S.w2[(j0 + 1) * MLP_H + in]);
+            const unsigned b1 = pack2h(S.w2[(j0 + 8) * MLP_H + in], S.w2[(j0 + 9) * MLP_H + in]);
+            mma_bf16(c, a, b0, b1);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float d1v = c[r] * (1.0f - h1[nt][r] * h1[nt][r]);
+            const int ls = ls0 + g + 8 * (r >> 1), j = 8 * nt + 2 * t + (r & 1);
+            B.h1[MLP_H * ls + j] = __float2bfloat16_rn(h1[nt][r]);
+            B.d1f[MLP_H * ls + j] = d1v;
+        }
+    }
+    // the block's samples are staged for the products over samples
+    if (t == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) B.x[3 * (ls0 + g + 8 * h) + c] = x[3 * h + c];
+    }
+    __syncthreads();
+    // dW2[j][i] = sum_s d2[s][j] h1[s][i]: warp w takes rows j = 16w .. 16w + 15
+    {
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[nt][r] = 0.0f;
+        const int jr = 16 * w + g;
+#pragma unroll
+        for (int ks = 0; ks < TCS / 16; ++ks) {
+            const int sa = 16 * ks + 2 * t;
+            const unsigned a[4] = {pack2h(B.d2[MLP_H * sa + jr], B.d2[MLP_H * (sa + 1) + jr]),
+                                   pack2h(B.d2[MLP_H * sa + jr + 8], B.d2[MLP_H * (sa + 1) + jr + 8]),
+                                   pack2h(B.d2[MLP_H * (sa + 8) + jr], B.d2[MLP_H * (sa + 9) + jr]),
+                                   pack2h(B.d2[MLP_H * (sa + 8) + jr + 8], B.d2[MLP_H * (sa + 9) + jr + 8])};
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int in = 8 * nt + g;
+                const unsigned b0 = pack2h(B.h1[MLP_H * sa + in], B.h1[MLP_H * (sa + 1) + in]);
+                const unsigned b1 = pack2h(B.h1[MLP_H * (sa + 8) + in], B.h1[MLP_H * (sa + 9) + in]);
+                mma_bf16(acc[nt], a, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int j = 16 * w + g + 8 * (r >> 1), i = 8 * nt + 2 * t + (r & 1);
+                atomicAdd(&G[MLP_W2 + MLP_H * j + i], acc[nt][r]);
+            }
+    }
+    // dW3[o][i] = sum_s d3[s][o] h2[s][i]: rows o = 0..7 (padded to 16), warp w takes i = 16w .. 16w + 15
+    {
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int ks = 0; ks < TCS / 16; ++ks) {
+            const int sa = 16 * ks + 2 * t;
+            const unsigned a[4] = {pack2h(B.d3[MLP_OUT * sa + g], B.d3[MLP_OUT * (sa + 1) + g]), 0u,
+                                   pack2h(B.d3[MLP_OUT * (sa + 8) + g], B.d3[MLP_OUT * (sa + 9) + g]), 0u};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int in = 16 * w + 8 * q + g;
+                const unsigned b0 = pack2h(B.h2[MLP_H * sa + in], B.h2[MLP_H * (sa + 1) + in]);
+                const unsigned b1 = pack2h(B.h2[MLP_H * (sa + 8) + in], B.h2[MLP_H * (sa + 9) + in]);
+                mma_bf16(acc[q], a, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                atomicAdd(&G[MLP_W3 + MLP_H * g + 16 * w + 8 * q + 2 * t + r], acc[q][r]);
+    }
+    // FP32 cores: dW1, b1, b2 (threads 0..63: unit j), b3 (threads 64..71), the loss
+    const int tid = threadIdx.x;
+    if (tid < MLP_H) {
+        float g1[3] = {0.f, 0.f, 0.f}, gb1 = 0.f, gb2 = 0.f;
+        for (int s2 = 0; s2 < TCS; ++s2) {
+            const float dd1 = B.d1f[MLP_H * s2 + tid];
+            g1[0] = fmaf(dd1, B.x[3 * s2], g1[0]);
+            g1[1] = fmaf(dd1, B.x[3 * s2 + 1], g1[1]);
+            g1[2] = fmaf(dd1, B.x[3 * s2 + 2], g1[2]);
+            gb1 += dd1;
+            gb2 += B.d2f[MLP_H * s2 + tid];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(&G[MLP_W1 + 3 * tid + c], g1[c]);
+        atomicAdd(&G[MLP_B1 + tid], gb1);
+        atomicAdd(&G[MLP_B2 + tid], gb2);
+    } else if (tid < MLP_H + MLP_OUT) {
+        const int o = tid - MLP_H;
+        float gb3 = 0.f;
+        for (int s2 = 0; s2 < TCS; ++s2) gb3 += B.d3f[MLP_OUT * s2 + o];
+        atomicAdd(&G[MLP_B3 + o], gb3);
+    } else if (tid == MLP_H + MLP_OUT) {
+        float ls = 0.f;
+#pragma unroll
+        for (int k = 0; k < TCW; ++k) ls += B.loss[k];
+        atomicAdd(loss, ls);
+    }
+}
+
+size_t grad_tc_smem() { return ((sizeof(TcSmem) + 15) / 16) * 16 + sizeof(TcBack); }
+
 __global__ void k_mlp_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ Mo,
                            float* __restrict__ Vo, float lr, float c1, float c2) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,8 +549,16 @@ int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double 
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+        cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_tc_smem());
         attr = true;
     }
+    // the gradient of a batch: FP32 cores, or the BF16 tensor-core form
+    auto grad = [&](const double* Xg, const float* Tgg, long long m) {
+        if (p.tensor_cores)
+            k_mlp_grad_tc<<<(unsigned)((m + TCS - 1) / TCS), 32 * TCW, grad_tc_smem(), s>>>(d_master, Xg, Tgg, m, G, L);
+        else
+            k_mlp_grad<<<(unsigned)((m + GS - 1) / GS), GS, grad_smem(), s>>>(d_master, Xg, Tgg, m, G, L);
+    };
     k_lambda_stats<<<MLP_OUT, 256, 0, s>>>(d_lam, n, ms);
     k_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_uT, d_lam, n, T0, ms, X, Tg);
     k_init_params<<<(MLP_NP + 255) / 256, 256, 0, s>>>(d_master, p.seed);
@@ -262,7 +571,7 @@ int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double 
         k_gather_batch<<<(B + 255) / 256, 256, 0, s>>>(X, Tg, n, B, p.seed, step, Xb, Tb);
         cudaMemsetAsync(G, 0, sizeof(float) * MLP_NP, s);
         cudaMemsetAsync(L, 0, sizeof(float), s);
-        k_mlp_grad<<<(B + GS - 1) / GS, GS, grad_smem(), s>>>(d_master, Xb, Tb, B, G, L);
+        grad(Xb, Tb, B);
         const double c1 = 1.0 - std::pow(0.9, step), c2 = 1.0 - std::pow(0.999, step);
         k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, s>>>(d_master, G, Mo, Vo, lr, (float)c1, (float)c2);
     }
@@ -270,7 +579,7 @@ int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double 
     // loss of the final parameters over the whole sample set
     cudaMemsetAsync(G, 0, sizeof(float) * MLP_NP, s);
     cudaMemsetAsync(L, 0, sizeof(float), s);
-    k_mlp_grad<<<(unsigned)((n + GS - 1) / GS), GS, grad_smem(), s>>>(d_master, X, Tg, n, G, L);
+    grad(X, Tg, n);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_ms, ms, sizeof(double) * 2 * MLP_OUT, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_loss, L, sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -305,6 +614,30 @@ int lbm_mlp_grad(const float* d_params, const double* d_x, const float* d_t, int
     cudaMemsetAsync(d_grad, 0, sizeof(float) * MLP_NP, s);
     cudaMemsetAsync(d_loss, 0, sizeof(float), s);
     k_mlp_grad<<<(unsigned)((n + GS - 1) / GS), GS, grad_smem(), s>>>(d_params, d_x, d_t, n, d_grad, d_loss);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int lbm_mlp_forward_tc(const float* d_params, const double* d_x, int64_t n, float* d_y, void* stream) {
+    if (!d_params || !d_x || !d_y || n < 0) return set_error(LBM_ERR_ARG, "bad arguments");
+    if (n == 0) return LBM_OK;
+    k_mlp_forward_tc<<<(unsigned)((n + TCS - 1) / TCS), 32 * TCW, 0, (cudaStream_t)stream>>>(d_params, d_x, n, d_y);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int lbm_mlp_grad_tc(const float* d_params, const double* d_x, const float* d_t, int64_t n, float* d_grad,
+                    float* d_loss, void* stream) {
+    if (!d_params || !d_x || !d_t || !d_grad || !d_loss || n <= 0) return set_error(LBM_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_tc_smem());
+        attr = true;
+    }
+    cudaMemsetAsync(d_grad, 0, sizeof(float) * MLP_NP, s);
+    cudaMemsetAsync(d_loss, 0, sizeof(float), s);
+    k_mlp_grad_tc<<<(unsigned)((n + TCS - 1) / TCS), 32 * TCW, grad_tc_smem(), s>>>(d_params, d_x, d_t, n, d_grad, d_loss);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
 }

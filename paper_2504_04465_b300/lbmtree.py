@@ -84,6 +84,8 @@ _sig = {
     "lbm_mlp_forward": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
     "lbm_mlp_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "lbm_mlp_adam": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p],
+    "lbm_mlp_forward_tc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "lbm_mlp_grad_tc": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "lbm_mlp_set": [_P, C.POINTER(C.c_float), _D, _D],
     "lbm_newton_batch": [_P, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p],
     "lbm_mlp_nparams": [],
@@ -179,7 +181,7 @@ class Batch:
 
 class MlpTrainParams(C.Structure):
     _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
-                ("seed", C.c_uint64), ("final_loss", C.c_float)]
+                ("seed", C.c_uint64), ("final_loss", C.c_float), ("tensor_cores", C.c_int)]
 
 
 def lattice_info(name: str) -> dict:
@@ -207,14 +209,16 @@ def mlp_nparams() -> int:
     return _lib.lbm_mlp_nparams()
 
 
-def mlp_forward(d_params: int, d_x: int, n: int, d_y: int, stream: int = 0) -> None:
-    _check(_lib.lbm_mlp_forward(C.c_void_p(d_params), C.c_void_p(d_x), n, C.c_void_p(d_y), C.c_void_p(stream)),
-           "lbm_mlp_forward")
+def mlp_forward(d_params: int, d_x: int, n: int, d_y: int, stream: int = 0, tensor_cores: bool = False) -> None:
+    f = _lib.lbm_mlp_forward_tc if tensor_cores else _lib.lbm_mlp_forward
+    _check(f(C.c_void_p(d_params), C.c_void_p(d_x), n, C.c_void_p(d_y), C.c_void_p(stream)), "lbm_mlp_forward")
 
 
-def mlp_grad(d_params: int, d_x: int, d_t: int, n: int, d_grad: int, d_loss: int, stream: int = 0) -> None:
-    _check(_lib.lbm_mlp_grad(C.c_void_p(d_params), C.c_void_p(d_x), C.c_void_p(d_t), n, C.c_void_p(d_grad),
-                             C.c_void_p(d_loss), C.c_void_p(stream)), "lbm_mlp_grad")
+def mlp_grad(d_params: int, d_x: int, d_t: int, n: int, d_grad: int, d_loss: int, stream: int = 0,
+             tensor_cores: bool = False) -> None:
+    f = _lib.lbm_mlp_grad_tc if tensor_cores else _lib.lbm_mlp_grad
+    _check(f(C.c_void_p(d_params), C.c_void_p(d_x), C.c_void_p(d_t), n, C.c_void_p(d_grad), C.c_void_p(d_loss),
+             C.c_void_p(stream)), "lbm_mlp_grad")
 
 
 def mlp_adam(d_params: int, d_grad: int, d_m: int, d_v: int, step: int, lr: float, stream: int = 0) -> None:
@@ -454,9 +458,9 @@ class Context:
         return p, m, s
 
     def mlp_train(self, d_uT: int, d_lambda: int, n: int, steps: int = 3000, batch: int = 1024, lr: float = 3e-3,
-                  lr_final: float = 3e-4, seed: int = 1504) -> float:
+                  lr_final: float = 3e-4, seed: int = 1504, tensor_cores: bool = False) -> float:
         """Train the context's Newton-guess network; returns the final loss over the n samples."""
-        p = MlpTrainParams(steps, batch, lr, lr_final, seed, 0.0)
+        p = MlpTrainParams(steps, batch, lr, lr_final, seed, 0.0, int(tensor_cores))
         _check(_lib.lbm_mlp_train(self._h, C.c_void_p(d_uT), C.c_void_p(d_lambda), n, C.byref(p)), "lbm_mlp_train")
         return float(p.final_loss)
 

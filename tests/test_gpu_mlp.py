@@ -6,7 +6,8 @@ solver run with the network guess against the oracle.
 Tolerances: the kernels compute in FP32 with the same bf16-rounded weight matrices as the
 oracle, so the forward pass agrees to FP32 rounding of 64-term sums (relative 1e-5 of the output
 scale) and the gradients, accumulated in FP32 over the batch with atomics, to 1e-4 relative L2
-per parameter tensor."""
+per parameter tensor.  The BF16 tensor-core kernels are compared with the oracle's tensor-core
+form (the same operands rounded to bfloat16); see their tests for the bounds."""
 from __future__ import annotations
 
 import numpy as np
@@ -97,6 +98,48 @@ def test_gradients_and_adam_match_oracle():
         assert np.abs(got[k] - q[k]).max() < 1e-6, k
 
 
+@pytest.mark.parametrize("n", [1, 100, 1000])
+def test_tensor_core_forward_matches_oracle(n):
+    """BF16 tensor-core forward pass against the oracle's tensor-core form (hidden activations
+    rounded to bfloat16 where the kernel rounds them).  An activation whose FP32 value lies
+    within FP32 rounding of a bfloat16 rounding boundary can round the other way on one side
+    (about 3e-5 of them), moving its outputs by one bfloat16 step of that term: every output
+    agrees to 2e-3 of the output scale, and all but a handful to 1e-5."""
+    p = random_params(11)
+    x = np.random.default_rng(12).uniform(-0.8, 0.8, (n, 3))
+    d_p, d_x = dev(flat(p), torch.float32), dev(x, torch.float64)
+    d_y = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    lt().mlp_forward(d_p.data_ptr(), d_x.data_ptr(), n, d_y.data_ptr(), tensor_cores=True)
+    torch.cuda.synchronize()
+    y, _ = mlp.forward(p, x, bf16_act=True)
+    err = np.abs(d_y.cpu().numpy() - y) / np.abs(y).max()
+    assert err.max() < 2e-3, err.max()
+    assert (err > 1e-5).sum() <= max(2, n // 100), (err > 1e-5).sum()
+
+
+def test_tensor_core_gradients_match_oracle():
+    n = 1000                                   # several blocks of 64 samples and a ragged tail
+    p = random_params(13)
+    rng = np.random.default_rng(14)
+    x = rng.uniform(-0.6, 0.6, (n, 3))
+    t = rng.standard_normal((n, 8)).astype(np.float32).astype(np.float64)
+    d_p, d_x, d_t = dev(flat(p), torch.float32), dev(x, torch.float64), dev(t, torch.float32)
+    npar = lt().mlp_nparams()
+    d_g = torch.empty(npar, dtype=torch.float32, device="cuda")
+    d_l = torch.empty(1, dtype=torch.float32, device="cuda")
+    lt().mlp_grad(d_p.data_ptr(), d_x.data_ptr(), d_t.data_ptr(), n, d_g.data_ptr(), d_l.data_ptr(),
+                  tensor_cores=True)
+    torch.cuda.synchronize()
+    loss, g = mlp.loss_and_grads(p, x, t, bf16_act=True)
+    _, g64 = mlp.loss_and_grads(p, x, t)
+    assert abs(float(d_l.item()) - loss) < 1e-4 * loss
+    gg = unflat(d_g.cpu().numpy())
+    for k in mlp.ORDER:
+        e = H.rel_l2(gg[k], g[k])
+        print(k, "tensor-core form %.2e, FP64 form %.2e" % (e, H.rel_l2(gg[k], g64[k])))
+        assert e < 1e-3, (k, e)
+
+
 def sup_fields(level, coords, c):
     """Ma ~0.6 inflow over a periodic channel with a density pulse and transverse waves."""
     x, y = c[:, 0], c[:, 1]
@@ -161,6 +204,38 @@ def test_batched_newton_matches_oracle_and_trained_guess_saves_iterations():
     lt().mlp_forward(d_p.data_ptr(), x.data_ptr(), 64, d_y.data_ptr())
     torch.cuda.synchronize()
     assert np.abs(d_y.cpu().numpy() - y).max() < 1e-5 * max(1.0, np.abs(y).max())
+    ctx.close()
+
+
+def test_tensor_core_training_saves_iterations():
+    """Training with the BF16 tensor-core gradient reaches the same quality as the FP32-core
+    training: loss below 0.1 and at least one Newton iteration saved against the polynomial
+    guess, Newton from it reaching the same root."""
+    import time
+    ctx, uT, _ = solver_samples()
+    n = uT.shape[0]
+    d_uT = dev(uT, torch.float64)
+    d_lam = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    d_it = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.newton_batch(d_uT.data_ptr(), n, "poly", d_lam.data_ptr(), d_it.data_ptr())
+    ctx.sync()
+    lam_poly, it_poly = d_lam.cpu().numpy(), d_it.cpu().numpy()
+    secs = {}
+    for tc in (False, True):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = ctx.mlp_train(d_uT.data_ptr(), d_lam.data_ptr(), n, steps=2000, batch=1024, lr=3e-3, lr_final=3e-4,
+                             tensor_cores=tc)
+        secs[tc] = time.perf_counter() - t0
+        assert loss < 0.1, (tc, loss)
+    ctx.newton_batch(d_uT.data_ptr(), n, "mlp", d_lam.data_ptr(), d_it.data_ptr())
+    ctx.sync()
+    it_mlp = d_it.cpu().numpy()
+    print(f"training 2000 steps of 1024: FP32 cores {secs[False]:.3f} s, tensor cores {secs[True]:.3f} s; "
+          f"Newton iterations poly {it_poly.mean():.3f} mlp(tc) {it_mlp.mean():.3f}")
+    assert (it_mlp >= 0).all()
+    assert np.abs(d_lam.cpu().numpy() - lam_poly).max() < 1e-9
+    assert it_mlp.mean() <= it_poly.mean() - 1.0
     ctx.close()
 
 

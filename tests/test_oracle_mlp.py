@@ -92,6 +92,55 @@ def test_gradients_match_autograd_with_rounded_weights():
         assert np.allclose(g[k], W[k].grad.numpy(), rtol=1e-12, atol=1e-15), k
 
 
+class _RoundFwd(torch.autograd.Function):
+    """bfloat16 of the value going forward (torch's own conversion), gradient passed unchanged."""
+    @staticmethod
+    def forward(ctx, a):
+        return a.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+class _RoundBwd(torch.autograd.Function):
+    """Value passed unchanged, bfloat16 of the gradient going back."""
+    @staticmethod
+    def forward(ctx, a):
+        return a.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def test_tensor_core_form_matches_autograd_with_bf16_operands():
+    """The bf16-operand gradients equal autograd of the network in which every operand of the
+    two 64-wide products is cast to bfloat16 by torch: activations on the way forward, the
+    gradient entering each product on the way back (biases and layer 1 unrounded)."""
+    p = random_params(15)
+    rng = np.random.default_rng(16)
+    x = rng.uniform(-0.6, 0.6, (40, 3))
+    t = rng.standard_normal((40, 8))
+    loss, g = mlp.loss_and_grads(p, x, t, rounded=True, bf16_act=True)
+    W = {k: torch.tensor(mlp.bf16_round(p[k]).astype(np.float64) if k.startswith("w") else p[k],
+                         dtype=torch.float64, requires_grad=True) for k in mlp.ORDER}
+    xt = torch.tensor(x)
+    h1 = torch.tanh(xt @ W["w1"].T + W["b1"])
+    h2 = torch.tanh(_RoundBwd.apply(_RoundFwd.apply(h1) @ W["w2"].T) + W["b2"])
+    y = _RoundBwd.apply(_RoundFwd.apply(h2) @ W["w3"].T) + W["b3"]
+    lt = 0.5 * ((y - torch.tensor(t)) ** 2).sum() / x.shape[0]
+    lt.backward()
+    assert abs(float(lt.detach()) - loss) < 1e-13
+    for k in mlp.ORDER:
+        assert np.allclose(g[k], W[k].grad.numpy(), rtol=1e-12, atol=1e-15), k
+    # and the rounding is real: the form differs from the FP64 one by about the bf16 unit roundoff
+    _, g64 = mlp.loss_and_grads(p, x, t, rounded=True)
+    for k in ("w2", "w3", "b2"):
+        d = np.linalg.norm(g[k] - g64[k]) / np.linalg.norm(g64[k])
+        assert 1e-5 < d < 2e-2, (k, d)
+
+
 def test_adam_first_step_closed_form():
     p = random_params(7)
     before = {k: v.copy() for k, v in p.items()}
