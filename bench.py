@@ -382,12 +382,12 @@ def _init_ctx(ctx, fields):
 
 
 def sod_numerical_case(lat, grid, L, stream, local):
-    """The Sec. 5 Sod benchmark case (numerical equilibrium, FP32 populations and FP32 Newton)."""
+    """The Sec. 7.6 Sod benchmark case (numerical equilibrium, FP32 populations and FP32 Newton)."""
     from paper_2504_04465_b300 import lbmtree as lt
     grids = {"unif": I.sod_spec(L, L), "band": I.sod_spec(L, L, 2, (L // 4, 3 * L // 4)),
              "sqr": I.GridSpec(2, (L, L), 2, [(0, (L // 4, L // 4), (3 * L // 4, 3 * L // 4))], (False, True),
                                {"x-": ("neumann",), "x+": ("neumann",)})}
-    T0 = {"D2Q13": 0.35, "D2Q21": 0.9, "D2Q37": 1.0}[lat]   # inviscid reference temperatures of Sec. 4.2
+    T0 = {"D2Q13": 0.35, "D2Q21": 0.9, "D2Q37": 1.0}[lat]   # inviscid reference temperatures of Sec. 6
     ctx = lt.Context(2, device=local, stream=stream)
     ctx.configure(grids[grid], lat, "num_ddf", "f32", nu0=0.0, T0=T0, sensor_A=1.5, newton_fp32=True)
     _init_ctx(ctx, lambda lev, c: I.sod_fields(I.cell_centres(c, lev), L, T0))
@@ -705,10 +705,10 @@ def form_d2q21_weak(args, stream, local):
 
 
 def form_sod_numerical(args, stream, local):
-    """The paper's compressible performance benchmark (Sec. 5, Sod tube, L = 2^13, single
+    """The paper's compressible performance benchmark (Sec. 7.6, Sod tube, L = 2^13, single
     precision): D2Q21 and D2Q37 DDF with the numerical equilibrium (8 constraints), FP32
     populations and FP32 Newton (tolerance 1e-5, warm start), inviscid with the kinetic sensor
-    (A = 1.5), on the L x L domain uniform and with the refinement patches of Sec. 4.2 (band:
+    (A = 1.5), on the L x L domain uniform and with the refinement patches of Sec. 6.1 (band:
     x/L in [1/4, 3/4); sqr: a centred square of side L/2; hori: the half y/L < 1/2, whose
     interface meets the Neumann faces, which the grid builder refuses); L counts finest cells.
     The timed window starts after t = 0.1 L / c_s, once the rarefaction, contact and shock have
@@ -754,7 +754,7 @@ def form_sod_numerical(args, stream, local):
                                      "roofline": roofline(upd, ms, {"D2Q13": 336, "D2Q21": 464, "D2Q37": 720}[lat],
                                                           "fp32", f"{fam}:{gname}", local)}
             ctx.close()
-    out["paper_a100"] = {"note": "Sec. 5 table, A100-SXM4, other machine: context only",
+    out["paper_a100"] = {"note": "Sec. 7.6 table, A100-SXM4, other machine: context only",
                          "D2Q13": {"unif": 1259.1, "hori": 1088.4, "band": 1244.8, "sqr": 1072.7},
                          "D2Q21": {"unif": 618.5, "hori": 555.9, "band": 588.2, "sqr": 544.4},
                          "D2Q37": {"unif (L = 2^12)": 286.9, "hori": 263.0, "band": 307.4, "sqr": 266.1}}
@@ -1006,7 +1006,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
     ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37",
-                    help="which forms to run (comma list; sod_numerical is the paper's Sec. 5 Sod benchmark)")
+                    help="which forms to run (comma list; sod_numerical is the paper's Sec. 7.6 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",
                     help="sod_numerical: grids (hori is refused: its interface meets the Neumann faces)")

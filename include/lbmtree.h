@@ -55,7 +55,7 @@ extern "C" {
  * formats; D2Q13 and D2Q21 on every component up to order 3, FP64 and FP32); compressible
  * polyatomic DDF (Eqs. gEq, polyTemp) with the thermal polynomial equilibrium (D2Q37) or with the
  * numerical max-entropy equilibrium of Eq. exponential solved by Newton-Raphson in FP64 or FP32
- * (D2Q13, D2Q21 and D2Q37, Sec. 4.2; on D2Q13 the FP32 solve with FP32 populations only). */
+ * (D2Q13, D2Q21 and D2Q37, Appendix A.2; on D2Q13 the FP32 solve with FP32 populations only). */
 #define LBM_BGK             1
 #define LBM_RR              2
 #define LBM_COMP_POLY       3
@@ -122,7 +122,7 @@ typedef struct { int kind; double p[8]; } lbm_shape;
 typedef struct {
     int64_t n_cells[8];          /* allocated non-absent cells per level                      */
     int64_t n_blocks[8];
-    double  n_eq;                /* sum_i n_i / 2^i over non-solid cells (Sec. 6.3)            */
+    double  n_eq;                /* sum_i n_i / 2^i over non-solid cells (Sec. 7.5)            */
     int     n_levels;
     int     block[3];            /* cell block shape                                          */
     int64_t newton_iter_sum;     /* Newton iterations summed over all collisions              */

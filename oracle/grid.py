@@ -76,7 +76,7 @@ class Grid:
     levels: list = field(default_factory=list)
 
     def n_eq(self) -> float:
-        """Equivalent fine cells N_eq = sum_i n_i / 2^i over non-solid cells (Sec. 6.3)."""
+        """Equivalent fine cells N_eq = sum_i n_i / 2^i over non-solid cells (Sec. 7.5)."""
         return sum(float((lv.ctype != SOLID).sum()) / 2 ** lv.level for lv in self.levels)
 
 

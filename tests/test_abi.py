@@ -130,7 +130,7 @@ def test_velocity_sets_match_oracle(lt):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_numerical_equilibrium_lattices(lt, storage, fp32):
-    """The numerical equilibrium is built on D2Q13, D2Q21 and D2Q37 (Sec. 4.2), for either Newton
+    """The numerical equilibrium is built on D2Q13, D2Q21 and D2Q37 (Appendix A.2), for either Newton
     precision (D2Q13: the FP32 solve with FP32 populations only); D2Q9 refuses it."""
     for latname in ("D2Q13", "D2Q21", "D2Q37"):
         if latname == "D2Q13" and fp32 and storage != "f32":

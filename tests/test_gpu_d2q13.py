@@ -2,7 +2,7 @@
 regularization on its order-3 Hermite basis (Appendix A, Tab. lattices_hermite; c_s^2 = 1/2,
 reach 2), and the compressible double distribution with the numerical equilibrium (Eq.
 exponential, eight constraints, Newton-Raphson) at the paper's reference temperature T0 = 0.35 for
-this lattice (Sec. 4.2): a smooth two-level case, the Sod tube with a refined band, and a
+this lattice (Sec. 6): a smooth two-level case, the Sod tube with a refined band, and a
 three-level NACA0012 at Mach 0.8 (the paper runs D2Q13 up to Mach 0.98).
 
 Tolerances: FP64 moments agree to 1e-12 (relative L2, and pointwise within twice the reach of
@@ -31,7 +31,7 @@ from tests.test_gpu_parity import N21_SPEC, SOD_SPEC
 
 pytestmark = pytest.mark.gpu
 
-T0 = 0.35           # Sec. 4.2: inviscid D2Q13 runs
+T0 = 0.35           # Sec. 6: inviscid D2Q13 runs
 NU0 = 0.02
 
 

@@ -1,6 +1,6 @@
 """D2Q37 compressible DDF with the numerical (max-entropy) equilibrium of Eq. exponential against
 the FP64 oracle: the lattice the paper pairs with that equilibrium for its supersonic airfoil
-runs (Sec. 4.2, Mach 1.75 to 2.5) and benchmarks on the Sod tube (Sec. 5).
+runs (Sec. 6.4, Mach 1.75 to 2.5) and benchmarks on the Sod tube (Sec. 7.6).
 
 Tolerances: FP64 populations with FP64 Newton agree to 1e-12 relative (rounding order only);
 FP32 populations with FP64 Newton to the FP32 rounding of 37-term moment sums accumulated over
@@ -23,7 +23,7 @@ from tests.test_gpu_parity import SOD_SPEC
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-# Sec. 4.2: T0 = 1.0 for inviscid runs on D2Q37, 0.4 for viscous ones
+# Sec. 6: T0 = 1.0 for inviscid runs on D2Q37, 0.4 for viscous ones
 T0_INV, T0_VISC = 1.0, 0.4
 N37_SPEC = I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True))
 

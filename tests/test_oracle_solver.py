@@ -278,3 +278,38 @@ def test_sod_refined_band_close_to_uniform():
     e_band = _sod_l1("D2Q37", "poly_ddf", None, 256, nl=2, band=(64, 192))
     e_fine = _sod_l1("D2Q37", "poly_ddf", None, 256)
     assert e_band < 2.5 * e_fine and e_band < 0.03
+
+
+def test_literal_unknown_rule_loses_mass():
+    """Reading R1 against the literal one.  Sec. 3.2 calls a coarse-ghost population unknown when
+    no neighbouring coarse cell supplied it; read literally, a population streamed from another
+    coarse ghost counts as supplied.  With that rule the ledger drifts at the convex corners of a
+    refined patch (a diagonal fine population leaving the fine bulk into a ghost whose coarse
+    counterpart another ghost feeds is never returned); with R1 (only coarse bulk sources count)
+    it is constant to round-off."""
+    lat = L.D2Q9
+    spec = I.taylor_green_spec(32, 8, 24, 2)
+    drift = {}
+    for rule in ("r1", "literal"):
+        g = G.build(spec, lat)
+        if rule == "literal":
+            lv = g.levels[1]
+            s = lv.src[:, lv.cg_cells]
+            rest = ~np.any(lat.xi != 0, axis=1)
+            unknown = s < 0                      # no coarse source of any kind
+            unknown[rest, :] = False
+            lv.cg_unknown = unknown
+        sol = S.Solver(g, "rr", nu0=0.04)
+        fields = []
+        for lv in g.levels:
+            c = I.cell_centres(lv.coords, lv.level)
+            rho, u = I.taylor_green_fields(c, 32, 2, 0.05, lat.cs2)
+            u = u + 0.01 * np.stack([I.uniform_at(5, lv.level, lv.coords, k) for k in range(2)])
+            fields.append((rho, u, None))
+        sol.init_fields(fields)
+        m0 = sol.ledger()[0]
+        sol.step_coarse(20)
+        drift[rule] = abs(sol.ledger()[0] - m0) / m0
+    print("relative mass drift over 20 coarse steps:", drift)
+    assert drift["r1"] < 1e-14
+    assert drift["literal"] > 1e-9, drift
