@@ -396,6 +396,19 @@ def sod_numerical_case(lat, grid, L, stream, local):
     return ctx, T0, fine
 
 
+def riemann12_case(grid, nc, stream, local):
+    """Sec. 6.2's 2D Riemann problem, configuration 12: D2Q21 DDF with the numerical equilibrium,
+    FP32 populations and FP32 Newton, inviscid with the kinetic sensor (A = 1.5), periodic, on the
+    diag, axes or optim grid with nc coarse cells per half side L."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    T0 = 0.9
+    ctx = lt.Context(2, device=local, stream=stream)
+    ctx.configure(I.riemann12_spec(nc, grid), "D2Q21", "num_ddf", "f32", nu0=0.0, T0=T0, sensor_A=1.5,
+                  newton_fp32=True)
+    _init_ctx(ctx, lambda lev, c: I.riemann12_fields(I.cell_centres(c, lev), nc, T0))
+    return ctx
+
+
 def naca37_case(chord, storage, stream, local, n_levels=5):
     """BASELINE configuration 3b: D2Q37 polynomial DDF around a NACA0012 at zero incidence,
     Mach 0.8 subsonic inlet (density extrapolated), Re 1e4 on the chord, sensor A = 1.35."""
@@ -438,6 +451,8 @@ def counters_case(path, stream, local):
         _init_ctx(ctx, lambda lev, c: (np.ones(c.shape[0]), np.stack(
             [0.05 * np.sin(2 * np.pi * I.cell_centres(c, lev)[:, 1] / n), np.zeros(c.shape[0])])))
         return ctx, 3
+    if fam == "d2q21n32" and case.startswith("riemann_"):
+        return riemann12_case(case[len("riemann_"):], 256, stream, local), 8
     if fam in ("d2q13n32", "d2q21n32", "d2q37n32"):
         lat = {"d2q13n32": "D2Q13", "d2q21n32": "D2Q21", "d2q37n32": "D2Q37"}[fam]
         ctx, _, fine = sod_numerical_case(lat, case, 2048, stream, local)
@@ -761,6 +776,39 @@ def form_sod_numerical(args, stream, local):
     return out
 
 
+def form_riemann12(args, stream, local):
+    """Sec. 6.2's 2D Riemann problem (configuration 12) at the paper's finest resolution, N_c = 512
+    coarse cells per L on [-L, L]^2 (2048^2 finest cells), D2Q21 numerical DDF in FP32 with the
+    FP32 Newton, on the three grids; the timed window starts at t = 0.05 t_c (t_c = L / u_0),
+    once the four shocks and contacts have left the quadrant edges."""
+    nc = 512 // args.scale
+    T0 = 0.9
+    out = {"workload": f"2D Riemann configuration 12 on [-L, L]^2, N_c = {nc} (finest {4 * nc}^2), periodic, "
+                       "inviscid, kinetic sensor A = 1.5",
+           "storage": "f32", "newton": "fp32, tol 1e-5, warm start", "unit": "MLUPS (cell updates per second)",
+           "bytes_per_update": 464, "step": "one coarse step = 2 fine iterations"}
+    from paper_2504_04465_b300 import lbmtree as lt
+    for gname in ("diag", "axes", "optim"):
+        ctx = riemann12_case(gname, nc, stream.cuda_stream, local)
+        ctx.use_graph(True)
+        ctx.step(max(1, int(0.05 * nc / np.sqrt(1.4 * T0))))     # coarse steps to t = 0.05 t_c
+        v, tune_ms = ctx.autotune(2)
+        st0 = ctx.stats()
+        K = 4
+        ms = _event_ms(stream, lambda: ctx.step(K)) / K
+        ctx.sync()
+        st1 = ctx.stats()
+        upd = st1.cell_updates
+        it = (st1.newton_iter_sum - st0.newton_iter_sum) / max(1, st1.newton_updates - st0.newton_updates)
+        out[gname] = {"cells": [int(n) for n in st1.n_cells[:st1.n_levels]], "ms_per_step": ms,
+                      "value": upd / ms / 1e3, "window_start_fine_iteration": int(st0.fine_iterations),
+                      "newton_iterations": it, "nonconverged": int(st1.newton_nonconverged),
+                      "variant_min_blocks": ctx.variants()[v],
+                      "roofline": roofline(upd, ms, 464, "fp32", f"d2q21n32:riemann_{gname}", local)}
+        ctx.close()
+    return out
+
+
 def form_naca37(args, stream, local):
     """BASELINE configuration 3b: D2Q37 polynomial DDF with the sensor around a NACA0012 at
     Mach 0.8 and Re 1e4 on 5 levels (chord 2048 finest cells, Sec. 6.3's transonic airfoil),
@@ -968,7 +1016,8 @@ def run_ours(args, world, rank, local):
                          ("d2q9_tg", lambda: form_d2q9(args, stream, local)),
                          ("sod_numerical", lambda: form_sod_numerical(args, stream, local)),
                          ("d2q21_weak", lambda: form_d2q21_weak(args, stream, local)),
-                         ("naca37", lambda: form_naca37(args, stream, local))):
+                         ("naca37", lambda: form_naca37(args, stream, local)),
+                         ("riemann12", lambda: form_riemann12(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -1005,7 +1054,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37",
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37,riemann12",
                     help="which forms to run (comma list; sod_numerical is the paper's Sec. 7.6 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",

@@ -18,7 +18,9 @@ finest units.  Region_i is the union of the level-i boxes of the spec (the whole
 the coarsest level).  Readings used here (design notes): R1 coarse unknowns are the
 populations that were not streamed from a coarse bulk cell (no source, or a source that is
 itself a coarse ghost) -- the literal "no coarse source" rule loses mass at patch corners,
-where diagonal links cut through the fine bulk; R11 a link is blocked when
+where diagonal links cut through the fine bulk; R33 at the concave corners of the finer region a
+child whose two-step streaming history leaves the finer level enters the coalescence with the
+coarse ghost's own streamed population (see ``_coupling``); R11 a link is blocked when
 any cell of the lattice segment between the two cells is solid (both roundings taken where
 the segment passes between cells); R12 a boundary cell's interior partner is the cell
 obtained by clamping its coordinates into the interior along every non-periodic axis.
@@ -54,6 +56,7 @@ class Level:
     cg_cells: np.ndarray = None   # (nc,) indices of coarse ghosts
     cg_unknown: np.ndarray = None  # (Q, nc) bool
     cg_children: np.ndarray = None  # (nc, 2^D) indices in the finer level
+    cg_broken: np.ndarray = None  # (Q, nc, 2^D) bool: child histories that leave the finer level
     # boundary cells
     bc_cells: np.ndarray = None
     bc_kind: np.ndarray = None
@@ -340,6 +343,45 @@ def _coupling(g: Grid, i: int) -> None:
         raise GridError("coarse ghost without its fine children")
     if cg.size and not (fine.ctype[lv.cg_children] == FGHOST).all():
         raise GridError("children of a coarse ghost are not fine ghosts")
+    # reading R33 (concave corners of the finer region): over one coarse step a fine ghost only
+    # streams, so a child's population q at the coalescence left the fine cell ch - 2 xi_q two
+    # fine iterations earlier through ch - xi_q.  Where that history leaves the finer level
+    # (ch - xi_q is no fine cell, or is a fine ghost and ch - 2 xi_q is none) the packet came
+    # from the coarse side and is the coarse ghost's own streamed population instead (the
+    # post-collision population of ch's coarse cell minus xi_q, which is the coarse cell
+    # holding ch - 2 xi_q).  Only unknown populations are marked; along straight interfaces and
+    # at convex corners no history leaves the finer level.
+    nk = lv.cg_children.shape[1]
+    brk = np.zeros((g.lat.Q, cg.size, nk), dtype=bool)
+    for k in range(nk):
+        ch = fine.coords[lv.cg_children[:, k]]
+        for q in range(g.lat.Q):
+            xi = g.lat.xi[q][None, :]
+            if not xi.any():
+                continue
+            i1 = _lookup(fine, ch - xi, g.periodic)
+            i2 = _lookup(fine, ch - 2 * xi, g.periodic)
+            t1 = np.where(i1 >= 0, fine.ctype[np.maximum(i1, 0)], 0)
+            brk[q, :, k] = (i1 < 0) | ((t1 == FGHOST) & (i2 < 0))
+    brk &= lv.cg_unknown[:, :, None]
+    if (brk.any(axis=2) & (s < 0)).any():
+        raise GridError("a coarse ghost stands in for a fine history but has no coarse source")
+    lv.cg_broken = brk
+
+
+def _lookup(lv: Level, c: np.ndarray, periodic) -> np.ndarray:
+    """Index of the cell of ``lv`` at level coordinates c (wrapped across periodic faces), -1 where
+    there is none."""
+    c = c.copy()
+    ok = np.ones(c.shape[0], dtype=bool)
+    for ax in range(c.shape[1]):
+        if periodic[ax]:
+            c[:, ax] %= lv.shape[ax]
+        else:
+            ok &= (c[:, ax] >= 0) & (c[:, ax] < lv.shape[ax])
+    out = np.full(c.shape[0], -1, dtype=np.int64)
+    out[ok] = lv.index[tuple(c[ok].T)]
+    return out
 
 
 def _bc_partners(g: Grid, i: int) -> None:

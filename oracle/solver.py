@@ -159,16 +159,20 @@ class Solver:
 
     # ------------------------------------------------------------------ phases
     def _coalesced(self, lev: int):
-        """Pre-collision populations of the coarse ghosts of ``lev`` with unknowns coalesced."""
+        """Pre-collision populations of the coarse ghosts of ``lev`` with unknowns coalesced: the
+        mean over the children of their streamed populations, a child whose history left the
+        finer level standing in with the ghost's own streamed population (reading R33)."""
         lv = self.g.levels[lev]
         C, kids, unk = lv.cg_cells, lv.cg_children, lv.cg_unknown
+        brk = lv.cg_broken
         f = self.f[lev][:, C].copy()
-        fine_f = self.f[lev - 1][:, kids]                       # (Q, nc, nk)
+        fine_f = np.where(brk, f[:, :, None], self.f[lev - 1][:, kids])        # (Q, nc, nk), R33
         f[unk] = fine_f.mean(axis=2)[unk]
         g = lam = None
         if self.comp:
             g = self.g_[lev][:, C].copy()
-            g[unk] = self.g_[lev - 1][:, kids].mean(axis=2)[unk]
+            fine_g = np.where(brk, g[:, :, None], self.g_[lev - 1][:, kids])
+            g[unk] = fine_g.mean(axis=2)[unk]
         if self.lam is not None:
             lam = self.lam[lev - 1][:, kids].mean(axis=2)
         return f, g, lam

@@ -8,7 +8,9 @@
 // A coarse-ghost population is supplied by coalescence unless it was streamed from a coarse
 // bulk or boundary cell (the rest population always stays); with that rule the coupling is
 // exactly conservative, including at patch corners where diagonal links cut through the fine
-// bulk.  Boundary layers are the `reach` outer layers on non-periodic faces (Appendix A.3); a
+// bulk.  At concave corners of the finer region a child's two-step streaming history can leave
+// the finer level; such a child enters the coalescence with the ghost's own streamed
+// population, which keeps the coupling conservative there too (record flag b bit 0).  Boundary layers are the `reach` outer layers on non-periodic faces (Appendix A.3); a
 // boundary cell's partner is the cell obtained by clamping its coordinates into the interior.
 // A link is blocked by a solid when any cell met on the lattice segment is solid, taking both
 // roundings where the segment passes between cells.
@@ -455,6 +457,30 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                     uint8_t ct = locate(i - 1, ch, cc);
                     if (ct != C_FGHOST) errs[tid] = "coarse ghost whose children are not fine ghosts";
                     r.a = (int32_t)cc;
+                    // concave corner of the finer region: some child's two-step streaming history
+                    // of an unknown population leaves the finer level (b bit 0; the kernels then
+                    // test each child and let the ghost's own streamed population stand in)
+                    const int nk = g.D == 3 ? 8 : 4;
+                    for (int q = 0; q < Q && !(r.b & 1); ++q) {
+                        if (!(r.mask >> q & 1)) continue;
+                        for (int k = 0; k < nk; ++k) {
+                            int64_t x[3] = {ch[0] + (k & 1), ch[1] + ((k >> 1) & 1), ch[2] + ((k >> 2) & 1)};
+                            int64_t s1[3], s2[3], i1, i2;
+                            for (int d = 0; d < 3; ++d) {
+                                s1[d] = x[d] - g.lat.xi[q][d];
+                                s2[d] = x[d] - 2 * g.lat.xi[q][d];
+                            }
+                            const uint8_t t1 = locate(i - 1, s1, i1);
+                            if (t1 == C_ABSENT || (t1 == C_FGHOST && locate(i - 1, s2, i2) == C_ABSENT)) {
+                                r.b |= 1;
+                                int64_t sc[3] = {c[0] - g.lat.xi[q][0], c[1] - g.lat.xi[q][1], c[2] - g.lat.xi[q][2]};
+                                int64_t scc;
+                                if (locate(i, sc, scc) == C_ABSENT)
+                                    errs[tid] = "a coarse ghost stands in for a fine history but has no coarse source";
+                                break;
+                            }
+                        }
+                    }
                 }
                 if (t == C_FGHOST || t == C_BC) {
                     int rz = g.D == 3 ? g.R : 0;

@@ -34,6 +34,39 @@ struct hermite_weak<M, std::void_t<decltype(M::HERMITE_WEAK)>> : std::bool_const
 
 enum Mode { MODE_STEP = 0, MODE_READ = 1, MODE_LEDGER = 2 };
 
+// largest |xi_a| of the lattice (its reach)
+template <class M>
+__host__ __device__ constexpr int lattice_reach() {
+    int r = 0;
+    for (int q = 0; q < M::Q; ++q) {
+        const int a = M::cx(q) < 0 ? -M::cx(q) : M::cx(q), b = M::cy(q) < 0 ? -M::cy(q) : M::cy(q),
+                  c = M::cz(q) < 0 ? -M::cz(q) : M::cz(q);
+        r = a > r ? a : r;
+        r = b > r ? b : r;
+        r = c > r ? c : r;
+    }
+    return r;
+}
+
+// Concave corners of the finer region: over one coarse step a fine ghost only streams, so the
+// population xi of child ch at the coalescence left ch - 2 xi through ch - xi.  True when that
+// history leaves the finer level (ch - xi is no cell of it, or is a fine ghost and ch - 2 xi is
+// none): the packet came from the coarse side and the coarse ghost's own streamed population
+// stands in for it.  Two steps of the lattice reach stay within the neighbouring blocks.
+template <class M, int BX, int BY, int BZ>
+__device__ __forceinline__ bool history_leaves(const LevelDev& F, long long ch, int cx, int cy, int cz) {
+    static_assert(2 * lattice_reach<M>() <= BX && 2 * lattice_reach<M>() <= BY &&
+                      (M::D == 2 || 2 * lattice_reach<M>() <= BZ),
+                  "two lattice steps must stay within the neighbouring blocks");
+    const long long s1 = src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz);
+    if (s1 < 0) return true;
+    const int t1 = F.type[s1];
+    if (t1 == C_ABSENT) return true;
+    if (t1 != C_FGHOST) return false;
+    const long long s2 = src_cell_g<BX, BY, BZ>(F.nbr, ch, 2 * cx, 2 * cy, 2 * cz);
+    return s2 < 0 || F.type[s2] == C_ABSENT;
+}
+
 template <class M, int ST>
 struct Cell {
     using T = typename Store<ST>::T;
@@ -123,7 +156,9 @@ __device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c,
 // Pre-collision state of the cell (level lev, block b, local l) at the current iteration:
 //   FLUID : pull gather, bounce-back on blocked links
 //   CGHOST: pull gather; in STEP/LEDGER modes the unknown populations are the mean of the
-//           children's streamed populations (Eq. coalescence) and lambda the children's mean
+//           children's streamed populations (Eq. coalescence; at a concave corner a child whose
+//           history left the finer level counts with the ghost's own streamed population) and
+//           lambda the children's mean
 //   FGHOST: pull gather (pure streaming), lambda carried
 //   BC    : Neumann copies the partner's gathered state (and lambda); Dirichlet sets the
 //           equilibrium of (rho_bc or the partner's rho, u_bc, T_bc)
@@ -141,6 +176,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
     if (type != C_BC) {
         unsigned long long bmask = 0ull, umask = 0ull;
         long long child = -1;
+        bool corner = false;    // a coarse ghost at a concave corner of the finer region
         if (!simple && type != C_FGHOST) {
             const int r = L.rec_id[cell];
             if (r >= 0) {
@@ -150,6 +186,7 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
                 } else {
                     umask = rec.mask;
                     child = rec.a;
+                    corner = (rec.b & 1) != 0;
                 }
             }
         }
@@ -159,7 +196,9 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
             T gv = T(0);
             if (bmask & (1ull << q)) {
                 load_pop<M, ST, BX * BY * BZ>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
-            } else if (!(coal && (umask & (1ull << q)))) {
+            } else if (!(coal && (umask & (1ull << q))) || corner) {
+                // (a corner ghost keeps its own streamed unknowns: they stand in for the
+                // children whose history left the finer level)
                 const long long s = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(q), M::cy(q), M::cz(q));
                 load_pop<M, ST, BX * BY * BZ>(L, rd, s, q, a.m, c.f[q], gv);
             }
@@ -185,10 +224,23 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
 #pragma unroll
                 for (int qq = 0; qq < M::Q; ++qq)
                     if (qq == q) { cx = M::cx(qq); cy = M::cy(qq); cz = M::cz(qq); }
+                T own_f = T(0), own_g = T(0);
+#pragma unroll
+                for (int qq = 0; qq < M::Q; ++qq) {
+                    if (qq == q) {
+                        own_f = c.f[qq];
+                        if constexpr (M::HAS_G) own_g = c.g[qq];
+                    }
+                }
                 T vf[NK], vg[NK];
 #pragma unroll
                 for (int k = 0; k < NK; ++k) {
                     const long long ch = child + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
+                    if (corner && history_leaves<M, BX, BY, BZ>(F, ch, cx, cy, cz)) {
+                        vf[k] = own_f;
+                        vg[k] = own_g;
+                        continue;
+                    }
                     const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz);
                     load_pop<M, ST, BX * BY * BZ>(F, rdf, s, q, a.m, vf[k], vg[k]);
                 }
@@ -363,15 +415,17 @@ __device__ __forceinline__ void gather_fast(const LevelDev& L, int rd, int l, co
 // a block prefix sum and thread t takes pairs t, t + BS, ...; each pair's 2^D children are
 // loaded together and summed in child order.  Result: out[q * BS + cell].
 template <class M, int ST, int BX, int BY, int BZ>
-__device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l, unsigned long long umask,
-                                               long long child, typename Store<ST>::T* out, int* s_cnt,
-                                               unsigned long long* s_um, int* s_child, int* s_warp) {
+__device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, long long b, int l, unsigned long long umask,
+                                               long long child, bool corner, typename Store<ST>::T* out, int* s_cnt,
+                                               unsigned long long* s_um, int* s_child, unsigned char* s_corner,
+                                               int* s_warp) {
     using T = typename Store<ST>::T;
     constexpr int BS = BX * BY * BZ;
     constexpr int NW = BS / 32;
     constexpr int NK = (M::D == 3) ? 8 : 4;
     s_um[l] = umask;
     s_child[l] = (int)child;
+    s_corner[l] = corner ? 1 : 0;
     // block exclusive prefix sum of the pair counts
     const int n = __popcll(umask);
     const int lane = l & 31, w = l >> 5;
@@ -413,12 +467,23 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, int l
         const int q = (r < c0 ? 0 : 32) + __ffs((int)w) - 1;
         const int cx = M::cx(q), cy = M::cy(q), cz = M::cz(q);
         const long long ch0 = s_child[lo];
+        const bool cor = s_corner[lo] != 0;
+        T own = T(0), vg;
+        if (cor) {
+            // the ghost's own streamed population, for children whose history left the finer level
+            const LevelDev& C = a.lv[lev];
+            const long long sc = src_cell_g<BX, BY, BZ>(C.nbr, b * BS + lo, cx, cy, cz);
+            load_pop<M, ST, BS>(C, a.rd[lev], sc, q, a.m, own, vg);
+        }
         T v[NK];
 #pragma unroll
         for (int kk = 0; kk < NK; ++kk) {
             const long long ch = ch0 + (kk & 1) + ((kk >> 1) & 1) * BX + ((kk >> 2) & 1) * BX * BY;
+            if (cor && history_leaves<M, BX, BY, BZ>(F, ch, cx, cy, cz)) {
+                v[kk] = own;
+                continue;
+            }
             const long long s = src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz);
-            T vg;
             load_pop<M, ST, BS>(F, rdf, s, q, a.m, v[kk], vg);
         }
         T sf = 0;
@@ -485,14 +550,18 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
     if constexpr (COOP) {
         __shared__ int s_cnt[BS + 1], s_child[BS], s_warp[BS / 32];
         __shared__ unsigned long long s_um[BS];
+        __shared__ unsigned char s_corner[BS];
         unsigned long long um = 0ull;
         long long child = 0;
+        bool corner = false;
         if (type == C_CGHOST) {
             const CellRecDev rec = L.recs[L.rec_id[cell]];
             um = rec.mask;
             child = rec.a;
+            corner = (rec.b & 1) != 0;
         }
-        coalesce_block<M, ST, BX, BY, BZ>(a, lev, l, um, child, sx.f, s_cnt, s_um, s_child, s_warp);
+        coalesce_block<M, ST, BX, BY, BZ>(a, lev, b, l, um, child, corner, sx.f, s_cnt, s_um, s_child, s_corner,
+                                          s_warp);
         __syncthreads();
     }
     int iters = -1;

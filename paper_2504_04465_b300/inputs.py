@@ -119,6 +119,50 @@ def sod_fields(centres: np.ndarray, nx: int, T0: float):
     return rho, np.zeros((2, rho.size)), T0 * p / rho
 
 
+# ------------------------------------------------------------------ 2D Riemann problem, configuration 12
+# Quadrant states of Sec. 6.2 (rho / rho0, u_x / u0, u_y / u0, p / p0), quadrants numbered
+# counter-clockwise from x > 0, y > 0; u0 = sqrt(gamma T0), p0 = rho0 T0, rho0 = 1.
+RIEMANN12 = {1: (0.513, 0.0, 0.0, 0.4), 2: (1.0, 0.7276, 0.0, 1.0), 3: (0.8, 0.0, 0.0, 1.0), 4: (1.0, 0.0, 0.7276, 1.0)}
+
+
+def riemann12_spec(nc: int, grid: str) -> GridSpec:
+    """The [-L, L]^2 domain of the 2D Riemann problem with N_c = nc coarse cells per L (2 nc per
+    side), two levels, periodic on every face, refined on one of the grids of Sec. 6.2:
+      diag   the half x > y (finest-level box per coarse row: a staircase along the diagonal, whose
+             interface is the symmetry line of the initial state);
+      axes   bands |x| < L/4 and |y| < L/4 along both axes;
+      optim  the axes bands and the central square |x|, |y| < L/2.
+    Positions in finest units: the domain is [0, 4 nc)^2 with its centre at 2 nc."""
+    ext = 4 * nc
+    c = 2 * nc
+    boxes = []
+    if grid == "diag":
+        for j in range(2 * nc - 1):            # coarse row j: coarse cells i > j refined
+            boxes.append((0, (2 * (j + 1), 2 * j), (ext, 2 * j + 2)))
+    elif grid in ("axes", "optim"):
+        w = nc // 2                             # L/4 in finest units (L = 2 nc)
+        boxes += [(0, (c - w, 0), (c + w, ext)), (0, (0, c - w), (ext, c + w))]
+        if grid == "optim":
+            boxes.append((0, (c - nc, c - nc), (c + nc, c + nc)))
+    elif grid != "uniform":
+        raise ValueError(grid)
+    return GridSpec(2, (ext, ext), 2 if boxes else 1, boxes, (True, True))
+
+
+def riemann12_fields(centres: np.ndarray, nc: int, T0: float, gamma: float = 1.4):
+    """rho, u, T of configuration 12 at cell centres (finest units): T = T0 (p/p0) / (rho/rho0)."""
+    c = 2 * nc
+    x = centres[:, 0] - c
+    y = centres[:, 1] - c
+    q = np.where(x > 0, np.where(y > 0, 1, 4), np.where(y > 0, 2, 3))
+    tab = np.array([RIEMANN12[k] for k in (1, 2, 3, 4)])
+    st = tab[q - 1]
+    u0 = np.sqrt(gamma * T0)
+    rho = st[:, 0]
+    u = np.stack([st[:, 1] * u0, st[:, 2] * u0])
+    return rho, u, T0 * st[:, 3] / rho
+
+
 # ------------------------------------------------------------------ 3D flow past a sphere
 def sphere_spec(scale: int = 1) -> GridSpec:
     """Four-level box around a sphere: 1024x512x512 finest units at scale 1, sphere diameter 64

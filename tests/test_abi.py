@@ -90,6 +90,8 @@ SPECS = [
     ("three_levels", lambda: I.GridSpec(2, (128, 128), 3, [(1, (32, 32), (96, 96)), (0, (48, 48), (80, 80))], (True, True)), "D2Q9", "bgk", None),
     ("reach3_q37", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q37", "poly_ddf", None),
     ("reach3_q21", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q21", "num_ddf", None),
+    ("riemann12_diag_q21", lambda: I.riemann12_spec(16, "diag"), "D2Q21", "num_ddf", None),
+    ("riemann12_optim_q37", lambda: I.riemann12_spec(16, "optim"), "D2Q37", "num_ddf", None),
     ("reach2_q13", lambda: I.GridSpec(2, (96, 64), 2, [(0, (32, 16), (64, 48))], (True, True)), "D2Q13", "rr", None),
     ("reach2_q13_sod", lambda: I.sod_spec(256, 32, 2, (64, 192)), "D2Q13", "num_ddf", None),
     ("reach2_q13_naca", lambda: I.naca_spec(64, 0.8, 0.35, n_levels=3, supersonic=False, half_domain=3.0,

@@ -313,3 +313,78 @@ def test_literal_unknown_rule_loses_mass():
     print("relative mass drift over 20 coarse steps:", drift)
     assert drift["r1"] < 1e-14
     assert drift["literal"] > 1e-9, drift
+
+
+def test_riemann12_keeps_the_diagonal_symmetry_on_a_uniform_grid():
+    """Configuration 12 is symmetric under the reflection x <-> y (quadrants 2 and 4 swap with
+    their velocities, Sec. 6.2); the oracle on a uniform periodic grid keeps that symmetry."""
+    lat = L.D2Q21
+    nc = 8
+    g = G.build(I.riemann12_spec(nc, "uniform"), lat)
+    s = S.Solver(g, "num_ddf", nu0=0.0, T0=0.9, sensor_A=1.5)
+    lv = g.levels[0]
+    s.init_fields([I.riemann12_fields(I.cell_centres(lv.coords, 0), nc, 0.9)])
+    s.step_fine(30)
+    rho, u, T = s.moments(0)
+    mirror = lv.index[lv.coords[:, 1], lv.coords[:, 0]]          # cell (y, x) of each (x, y)
+    assert abs(rho.max() - rho.min()) > 0.1                      # the flow is not trivial
+    assert np.abs(rho - rho[mirror]).max() < 1e-12
+    assert np.abs(u[0] - u[1, mirror]).max() < 1e-12
+    assert np.abs(T - T[mirror]).max() < 1e-12
+
+
+def _ledger_drift(spec, latname, model, disable_r33=False, steps=6, seed=5):
+    lat = L.LATTICES[latname]
+    g = G.build(spec, lat)
+    if disable_r33:
+        for lv in g.levels[1:]:
+            lv.cg_broken[:] = False
+    kw = {"nu0": 0.04} if model == "rr" else {"nu0": 0.02}
+    sol = S.Solver(g, model, **kw)
+    fields = []
+    for lv in g.levels:
+        n = lv.coords.shape[0]
+        rho = 1.0 + 0.05 * I.uniform_at(seed, lv.level, lv.coords, 0)
+        u = 0.05 * np.stack([I.uniform_at(seed + 1, lv.level, lv.coords, k) for k in range(lat.D)])
+        T = None if model == "rr" else lat.cs2 * (1.0 + 0.05 * I.uniform_at(seed + 2, lv.level, lv.coords, 0))
+        fields.append((rho, u, T))
+    sol.init_fields(fields)
+    m0 = sol.ledger()
+    sol.step_coarse(steps)
+    m1 = sol.ledger()
+    n = lat.D + 1 if model == "rr" else lat.D + 2          # energy only where collisions keep it
+    return float(np.abs(m1[:n] - m0[:n]).max() / m0[0])
+
+
+@pytest.mark.parametrize("latname,model,grid", [("D2Q9", "rr", "diag"), ("D2Q21", "rr", "axes"),
+                                                ("D2Q37", "poly_ddf", "diag")])
+def test_concave_corner_rule_keeps_the_ledger(latname, model, grid):
+    """Reading R33.  At the concave corners of the finer region (the diag staircase, the corners
+    of the axes cross) a fine ghost's two-step streaming history can start outside the finer
+    level, where a plain coalescence reads no population; with R33 the ghost's own streamed
+    population stands in and mass, momentum (and energy for the double distribution) stay
+    constant to round-off; without it they drift by 1e-4 and more within a few coarse steps."""
+    spec = I.riemann12_spec(8, grid)
+    with_rule = _ledger_drift(spec, latname, model)
+    without = _ledger_drift(spec, latname, model, disable_r33=True)
+    print(latname, grid, "drift with R33 %.1e, without %.1e" % (with_rule, without))
+    assert with_rule < 1e-13
+    assert without > 1e-5
+
+
+def test_concave_corner_rule_3d():
+    """The same ledger on an L-shaped refined region of a D3Q27 grid (three concave edges)."""
+    spec = I.GridSpec(3, (32, 32, 32), 2, [(0, (8, 8, 8), (24, 16, 24)), (0, (8, 16, 8), (16, 24, 24))],
+                      (True, True, True))
+    assert _ledger_drift(spec, "D3Q27", "rr", steps=3) < 1e-13
+    assert _ledger_drift(spec, "D3Q27", "rr", disable_r33=True, steps=3) > 1e-6
+
+
+def test_no_history_leaves_a_convex_patch():
+    """Along straight interfaces and at convex corners R33 marks nothing (the plain coalescence
+    of the earlier cases is unchanged)."""
+    for latname in ("D2Q9", "D2Q21", "D2Q37"):
+        g = G.build(I.taylor_green_spec(64, 16, 48, 2), L.LATTICES[latname])
+        assert not g.levels[1].cg_broken.any()
+    g = G.build(I.riemann12_spec(8, "diag"), L.D2Q21)
+    assert g.levels[1].cg_broken.any()
