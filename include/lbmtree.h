@@ -60,6 +60,10 @@ extern "C" {
 #define LBM_RR              2
 #define LBM_COMP_POLY       3
 #define LBM_COMP_NUMERICAL  4
+/* Two-relaxation-time collision (D2Q9, D3Q27; F64 and F32 storage): the parts of f - f_eq even
+ * and odd under xi -> -xi relax with 1/tau (tau from nu0, the shear viscosity) and with the rate
+ * fixed by Lambda = (tau - 1/2)(tau_odd - 1/2) (trt_magic below); needs nu0 > 0. */
+#define LBM_TRT             5
 
 /* Population storage.  F64/F32: plain values.  F16DEV: binary16 deviations
  * delta_i = f_i/(w_i rho_ref) - 1 (and for g: g_i/(w_i rho_ref (2Cv-D) T0) - 1), arithmetic in
@@ -114,6 +118,10 @@ typedef struct {
     int    newton_fp32;  /* 1: Newton of the numerical equilibrium in FP32 arithmetic (the
                             paper's single-precision threshold is 1e-5); multipliers kept in
                             FP64 between steps.  0 (default): FP64 Newton.                     */
+    int    trace_eq;     /* LBM_RR on D2Q9/D3Q27 (F64, F32 storage): equilibrate the trace of the
+                            second-order moments (Appendix A, after Eq. a1Rec; bulk relaxation
+                            time one): Pi is replaced by its deviatoric part in the recursion  */
+    double trt_magic;    /* LBM_TRT: Lambda = (tau - 1/2)(tau_odd - 1/2); <= 0: 1/4            */
 } lbm_collision_params;
 
 typedef struct { int level; int64_t lo[3]; int64_t hi[3]; } lbm_box;     /* finest units */
@@ -169,6 +177,14 @@ int lbm_set_guess(lbm_ctx* ctx, int guess);
  * the Newton solve, also on a built and running context. */
 int lbm_set_newton_precision(lbm_ctx* ctx, int fp32, double tol);
 int lbm_set_precision(lbm_ctx* ctx, int storage);
+/* Far-field relaxation of Eq. relaxation_pressure (weakly compressible models, p = rho c_s^2):
+ * before every collision, rho' = rho (1 - sigma) + sigma rho_inf with sigma = 0 for r < r0,
+ * sigma_max (r - r0)/(r1 - r0) for r0 <= r < r1 and sigma_max beyond, r the distance of the
+ * cell centre from `centre` (finest units; z ignored in 2D); the populations become
+ * f + f_eq(rho', u) - f_eq(rho, u) (velocity and non-equilibrium part kept).  sigma_max = 0
+ * switches it off (the default).  Errors: LBM_ERR_ARG for r1 <= r0, sigma_max outside [0, 1] or
+ * rho_inf <= 0; LBM_ERR_UNSUPPORTED with a compressible model.  Takes effect at the next step. */
+int lbm_set_sponge(lbm_ctx* ctx, const double centre[3], double r0, double r1, double sigma_max, double rho_inf);
 /* face 0..5; kind LBM_*; rho_u_T = {rho, ux, uy, uz, T} (ignored for PERIODIC/NEUMANN). */
 int lbm_set_boundary(lbm_ctx* ctx, int face, int kind, const double rho_u_T[5]);
 /* Block shape of the cell layout (x, y, z; z = 1 in 2D).  Defaults 16x16 (2D), 8x4x4 (3D).

@@ -211,20 +211,50 @@ def collide_bgk(f: np.ndarray, feq: np.ndarray, tau) -> np.ndarray:
     return f - (f - feq) / tau
 
 
-def collide_rr(lat: Lattice, f: np.ndarray, tau) -> np.ndarray:
-    """Recursive-regularized collision, Eq. GenRegCollision."""
+def collide_rr(lat: Lattice, f: np.ndarray, tau, trace_eq: bool = False) -> np.ndarray:
+    """Recursive-regularized collision, Eq. GenRegCollision.
+
+    trace_eq: equilibrate the trace of the second-order moments (Appendix A, after Eq. a1Rec;
+    the bulk relaxation time set to one): Pi is replaced by its deviatoric part
+    Pi - (tr Pi / D) I before the recursion, so no trace survives the collision (reading R35)."""
     rho, u = macroscopic(lat, f)
     feq = feq_athermal(lat, rho, u)
     Pi = pi_neq(lat, f, feq)
+    if trace_eq:
+        tr = sum(Pi[(a, a)] for a in range(lat.D)) / lat.D
+        Pi = {k: (v - tr if k[0] == k[1] else v) for k, v in Pi.items()}
     comps = basis_components(lat.name, lat.D)
     omega = 1.0 - 1.0 / np.asarray(tau, dtype=np.float64)
     return expand(lat, comps, lat.cs2,
                   lambda al: a_eq(al, rho, u) + omega * a_neq(al, Pi, u))
 
 
-def collide_weak(lat: Lattice, f: np.ndarray, tau, model: str) -> np.ndarray:
-    """Weakly compressible collision: model 'bgk' or 'rr' (same equilibrium, Sec. A.2)."""
+def trt_omega_minus(tau_plus: float, magic: float) -> float:
+    """Relaxation rate of the antisymmetric part of the two-relaxation-time collision from the
+    'magic' combination Lambda = (tau+ - 1/2)(tau- - 1/2) (reading R36)."""
+    if tau_plus <= 0.5:
+        raise ValueError("the two-relaxation-time collision needs tau+ > 1/2 (a positive viscosity)")
+    return 1.0 / (magic / (tau_plus - 0.5) + 0.5)
+
+
+def collide_trt(lat: Lattice, f: np.ndarray, feq: np.ndarray, tau, magic: float) -> np.ndarray:
+    """Two-relaxation-time collision: the parts of f - f_eq even and odd under xi -> -xi relax
+    with 1/tau+ (tau+ = tau, the viscosity) and with the rate of ``trt_omega_minus``."""
+    opp = lat.opp
+    wp = 1.0 / tau
+    wm = trt_omega_minus(tau, magic)
+    d = f - feq
+    even = 0.5 * (d + d[opp])
+    odd = 0.5 * (d - d[opp])
+    return f - wp * even - wm * odd
+
+
+def collide_weak(lat: Lattice, f: np.ndarray, tau, model: str, trace_eq: bool = False,
+                 magic: float = 0.25) -> np.ndarray:
+    """Weakly compressible collision: model 'bgk', 'trt' or 'rr' (same equilibrium, Sec. A.2)."""
     if model == "rr":
-        return collide_rr(lat, f, tau)
+        return collide_rr(lat, f, tau, trace_eq)
     rho, u = macroscopic(lat, f)
+    if model == "trt":
+        return collide_trt(lat, f, feq_athermal(lat, rho, u), tau, magic)
     return collide_bgk(f, feq_athermal(lat, rho, u), tau)

@@ -30,7 +30,7 @@ from . import hermite as hm
 from . import numerical as nm
 from .grid import BC, CGHOST, FGHOST, FLUID, SOLID, Grid
 
-WEAK_MODELS = ("bgk", "rr")
+WEAK_MODELS = ("bgk", "rr", "trt")
 COMP_MODELS = ("poly_ddf", "num_ddf")
 
 
@@ -56,7 +56,7 @@ class Solver:
     def __init__(self, grid: Grid, model: str, nu0: float = 0.0, T0: float | None = None,
                  gamma: float = 1.4, sensor_A: float | None = None, newton_tol: float = 1e-12,
                  newton_max_iter: int = 50, guess: str = "warm", poly_order: int | None = None,
-                 mlp=None):
+                 mlp=None, trace_eq: bool = False, trt_magic: float = 0.25, sponge=None):
         self.g = grid
         self.lat = grid.lat
         self.model = model
@@ -76,6 +76,13 @@ class Solver:
         self.guess = guess
         self.poly_order = poly_order if poly_order is not None else (4 if self.lat.Q >= 37 else 3)
         self.mlp = mlp
+        self.trace_eq = bool(trace_eq)
+        self.trt_magic = trt_magic
+        if trace_eq and model != "rr":
+            raise ValueError("trace equilibration applies to the recursive-regularized collision")
+        self.sponge = sponge
+        if sponge is not None and self.comp:
+            raise ValueError("the far-field relaxation is built for the weakly compressible models")
         self.t = 0
         Q = self.lat.Q
         self.f = [np.zeros((Q, lv.n)) for lv in grid.levels]
@@ -116,11 +123,31 @@ class Solver:
         return rho[None, :] * e, lam, it
 
     # ------------------------------------------------------------------ collision
-    def _collide(self, lev: int, f, g, lam):
-        """Post-collision state of cells with pre-collision (f, g, lam) at level ``lev``."""
+    def _relax_far_field(self, lev: int, cells, f):
+        """Eq. relaxation_pressure before the collision (weakly compressible, p = rho c_s^2):
+        rho' = rho (1 - sigma) + sigma rho_inf with sigma ramping linearly from 0 at distance r0
+        to sigma_max at r1 from the centre (finest units, cell centres) and sigma_max beyond; the
+        populations become f + f_eq(rho', u) - f_eq(rho, u), the velocity and the
+        non-equilibrium part kept (reading R37)."""
+        sp = self.sponge
+        lv = self.g.levels[lev]
+        x = (lv.coords[cells] + 0.5) * float(2 ** lev)
+        r = np.sqrt(((x - np.asarray(sp["centre"], float)[None, : self.lat.D]) ** 2).sum(axis=1))
+        sigma = np.clip((r - sp["r0"]) / (sp["r1"] - sp["r0"]), 0.0, 1.0) * sp["sigma_max"]
+        rho, u = hm.macroscopic(self.lat, f)
+        rho_new = rho * (1.0 - sigma) + sigma * sp["rho_inf"]
+        relaxed = f + hm.feq_athermal(self.lat, rho_new, u) - hm.feq_athermal(self.lat, rho, u)
+        return np.where(sigma[None, :] > 0.0, relaxed, f)
+
+    def _collide(self, lev: int, f, g, lam, cells=None):
+        """Post-collision state of cells with pre-collision (f, g, lam) at level ``lev``
+        (``cells``: their indices in the level, for position-dependent terms)."""
         tau = self.tau[lev]
         if not self.comp:
-            return hm.collide_weak(self.lat, f, tau, self.model), None, None, np.zeros(f.shape[1], np.int64)
+            if self.sponge is not None and cells is not None:
+                f = self._relax_far_field(lev, cells, f)
+            fs = hm.collide_weak(self.lat, f, tau, self.model, self.trace_eq, self.trt_magic)
+            return fs, None, None, np.zeros(f.shape[1], np.int64)
         rho, u, T = self._moments(f, g)
         lam0 = self._guess(u, T, lam) if lam is not None else None
         feq, lam_new, it = self._feq_comp(rho, u, T, lam0)
@@ -185,7 +212,7 @@ class Solver:
             self._cg_post[lev] = None
             return
         f, g, lam = self._coalesced(lev)
-        fs, gs, lam_new, it = self._collide(lev, f, g, lam)
+        fs, gs, lam_new, it = self._collide(lev, f, g, lam, C)
         self._cg_post[lev] = (fs, gs, lam_new, it)
         nk = kids.shape[1]
         for k in range(nk):
@@ -208,7 +235,7 @@ class Solver:
         if coll.size:
             g_in = self.g_[lev][:, coll] if self.comp else None
             l_in = lam[:, coll] if lam is not None else None
-            a, b, c, it = self._collide(lev, f[:, coll], g_in, l_in)
+            a, b, c, it = self._collide(lev, f[:, coll], g_in, l_in, coll)
             fs[:, coll] = a
             if self.comp:
                 gs[:, coll] = b

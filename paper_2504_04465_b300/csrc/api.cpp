@@ -48,6 +48,7 @@ struct DevLevel {
     double* lam = nullptr;
     int* blist[2] = {nullptr, nullptr};
     int64_t nlist[2] = {0, 0};
+    int* bxyz = nullptr;
 };
 
 struct Constants {
@@ -156,6 +157,11 @@ struct lbm_ctx {
     // buffer holding the current state of level i after tt iterations: ceil(tt / 2^i) steps done
     int cur(int i, int64_t tt) const { return int(((tt + (int64_t(1) << i) - 1) >> i) & 1); }
     bool comp() const { return model == LBM_COMP_POLY || model == LBM_COMP_NUMERICAL; }
+    bool weak() const { return model == LBM_BGK || model == LBM_RR || model == LBM_TRT; }
+    // kernel-set code of the collision: the public model, with the trace-equilibrated RR as 6
+    int kmodel() const { return (model == LBM_RR && params.trace_eq) ? KMODEL_RR_TRACE : model; }
+    // far-field relaxation (lbm_set_sponge)
+    double sp_c[3] = {0, 0, 0}, sp_r0 = 0, sp_r1 = 1, sp_smax = 0, sp_rho_inf = 1;
     double T0() const {
         if (params.T0 > 0) return params.T0;
         if (lattice == LBM_D2Q21) return 2.0 / 3.0;
@@ -203,6 +209,10 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
         d.tau = nu / theta + 0.5;
         d.omega = 1.0 / d.tau;
         d.omega_f = (float)d.omega;
+        // odd-part rate of the two-relaxation-time collision: (tau - 1/2)(tau_odd - 1/2) = Lambda
+        d.omega_m = nu > 0 ? 1.0 / (c->params.trt_magic / (d.tau - 0.5) + 0.5) : d.omega;
+        d.omega_m_f = (float)d.omega_m;
+        d.bxyz = c->dl[i].bxyz;
     }
     ModelDev& m = a.m;
     m.cs2 = theta;
@@ -222,6 +232,12 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     m.newton_max_iter = c->params.newton_max_iter > 0 ? c->params.newton_max_iter : 50;
     m.guess = c->params.guess;
     m.newton_fp32 = c->params.newton_fp32;
+    m.sponge_on = c->sp_smax > 0 ? 1 : 0;
+    for (int d = 0; d < 3; ++d) m.sp_c[d] = c->sp_c[d];
+    m.sp_r0 = c->sp_r0;
+    m.sp_r1 = c->sp_r1;
+    m.sp_smax = c->sp_smax;
+    m.sp_rho_inf = c->sp_rho_inf;
     m.mlp = c->d_mlp;
     for (int k = 0; k < 8; ++k) { m.mlp_m[k] = c->mlp_m[k]; m.mlp_s[k] = c->mlp_s[k]; }
     for (int f = 0; f < 6; ++f) {
@@ -505,10 +521,13 @@ int lbm_set_lattice(lbm_ctx* c, int lattice) {
 
 int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
     if (check_ctx(c)) return LBM_ERR_ARG;
-    if (model < LBM_BGK || model > LBM_COMP_NUMERICAL) return fail(LBM_ERR_ARG, "unknown collision model");
+    if (model < LBM_BGK || model > LBM_TRT) return fail(LBM_ERR_ARG, "unknown collision model");
     if (c->built) return fail(LBM_ERR_STATE, "collision model must be set before lbm_build_grid");
+    if (model == LBM_TRT && (!p || p->nu0 <= 0))
+        return fail(LBM_ERR_ARG, "the two-relaxation-time collision needs a positive viscosity");
     if (p) {
         if (p->nu0 < 0) return fail(LBM_ERR_ARG, "negative viscosity");
+        if (p->trace_eq && model != LBM_RR) return fail(LBM_ERR_ARG, "trace equilibration applies to LBM_RR");
         if (p->gamma <= 1.0 && model >= LBM_COMP_POLY) return fail(LBM_ERR_ARG, "gamma must exceed 1");
         if (p->guess < 0 || p->guess > LBM_GUESS_MLP) return fail(LBM_ERR_ARG, "unknown Newton guess");
         if (p->newton_fp32 && p->newton_tol > 0 && p->newton_tol < 1e-6)
@@ -516,6 +535,12 @@ int lbm_set_collision(lbm_ctx* c, int model, const lbm_collision_params* p) {
         c->params = *p;
         if (c->params.gamma <= 1.0) c->params.gamma = 1.4;
         if (c->params.rho_ref <= 0) c->params.rho_ref = 1.0;
+        if (c->params.trt_magic <= 0) c->params.trt_magic = 0.25;
+    } else {
+        c->params = lbm_collision_params{};
+        c->params.gamma = 1.4;
+        c->params.rho_ref = 1.0;
+        c->params.trt_magic = 0.25;
     }
     c->model = model;
     c->params_set = true;
@@ -539,11 +564,27 @@ int lbm_set_newton_precision(lbm_ctx* c, int fp32, double tol) {
     if (c->built) {
         // the two precisions are separate kernel sets (D2Q21); keep the variant in use
         KernelSet ks;
-        if (find_kernels(c->lattice, c->model, c->storage, c->block, fp32 != 0, ks)) {
+        if (find_kernels(c->lattice, c->kmodel(), c->storage, c->block, fp32 != 0, ks)) {
             ks.step = ks.variant[c->variant < ks.n_variants ? c->variant : 0];
             c->ks = ks;
         }
     }
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    return LBM_OK;
+}
+
+int lbm_set_sponge(lbm_ctx* c, const double centre[3], double r0, double r1, double sigma_max, double rho_inf) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!centre) return fail(LBM_ERR_ARG, "null centre");
+    if (!(r1 > r0) || !(sigma_max >= 0.0 && sigma_max <= 1.0) || !(rho_inf > 0.0))
+        return fail(LBM_ERR_ARG, "need r1 > r0, sigma_max in [0, 1] and rho_inf > 0");
+    if (c->params_set && c->comp() && sigma_max > 0)
+        return fail(LBM_ERR_UNSUPPORTED, "the far-field relaxation is built for the weakly compressible models");
+    for (int d = 0; d < 3; ++d) c->sp_c[d] = centre[d];
+    c->sp_r0 = r0;
+    c->sp_r1 = r1;
+    c->sp_smax = sigma_max;
+    c->sp_rho_inf = rho_inf;
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return LBM_OK;
 }
@@ -583,14 +624,17 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     if (!extent || (n_boxes > 0 && !boxes) || (n_solids > 0 && !solids)) return fail(LBM_ERR_ARG, "null array");
     if (!c->lattice || !c->params_set) return fail(LBM_ERR_STATE, "set lattice and collision model first");
     if (c->built) return fail(LBM_ERR_STATE, "grid already built");
-    const bool weak = c->model == LBM_BGK || c->model == LBM_RR;
+    const bool weak = c->weak();
     if ((weak && !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27 || c->lattice == LBM_D2Q21 ||
                    c->lattice == LBM_D2Q13)) ||
+        ((c->model == LBM_TRT || c->kmodel() == KMODEL_RR_TRACE) &&
+         !(c->lattice == LBM_D2Q9 || c->lattice == LBM_D3Q27)) ||
         (c->model == LBM_COMP_POLY && c->lattice != LBM_D2Q37) ||
         (c->model == LBM_COMP_NUMERICAL && c->lattice != LBM_D2Q13 && c->lattice != LBM_D2Q21 &&
          c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
-    if (!find_kernels(c->lattice, c->model, c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
+    if (c->sp_smax > 0 && !weak) return fail(LBM_ERR_UNSUPPORTED, "the far-field relaxation is built for the weakly compressible models");
+    if (!find_kernels(c->lattice, c->kmodel(), c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
     GridInput in;
     in.dim = c->dim;
@@ -681,6 +725,13 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         CU(cudaMemcpy(d.type, lv.type.data(), lv.type.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.bflag, lv.bflag.data(), lv.bflag.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d.rec_id, lv.rec_id.data(), lv.rec_id.size() * 4, cudaMemcpyHostToDevice));
+        d.bxyz = (int*)c->dalloc(lv.bxyz.size() * 4);
+        if (!d.bxyz) {
+            c->release();
+            c->built = false;
+            return fail(LBM_ERR_OOM, "device allocation of the block coordinates");
+        }
+        CU(cudaMemcpy(d.bxyz, lv.bxyz.data(), lv.bxyz.size() * 4, cudaMemcpyHostToDevice));
         // list 0 entries: 2 * block + 1 for streaming blocks (cell types read), 2 * block for
         // simple blocks; list 1: the general blocks
         std::vector<int32_t> lists[2];

@@ -27,6 +27,9 @@ struct LevelDev {
     double tau;
     double omega;            // 1 / tau
     float omega_f;           // 1 / tau in FP32 (no division in the kernels)
+    double omega_m;          // two-relaxation-time collision: rate of the odd part
+    float omega_m_f;
+    const int* bxyz;         // block coordinates (3 per block), for position-dependent terms
     const int* blist[2];     // [0] 2 * block + s: simple (s = 0) and streaming (s = 1) blocks, [1] the others
                              // (block nb of f/g holds zero populations: the missing-neighbour stand-in)
     long long nlist[2];
@@ -52,6 +55,8 @@ struct ModelDev {
     int guess;
     FaceDev faces[6];
     const float* mlp;        // Newton-guess network (bf16-rounded weights), guess == 3
+    int sponge_on;           // far-field relaxation (weakly compressible models)
+    double sp_c[3], sp_r0, sp_r1, sp_smax, sp_rho_inf;   // its centre, radii (finest units), sigma_max, rho_inf
     double mlp_m[8], mlp_s[8];
 };
 

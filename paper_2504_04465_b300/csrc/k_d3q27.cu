@@ -4,11 +4,14 @@
 
 namespace lbm {
 
-template <bool RR_> struct D3Q27M {
+// RR_: recursive regularization, else BGK; VAR_: WV_TRT (two relaxation times, with BGK's
+// equilibrium) or WV_TRACE (RR with the trace of Pi equilibrated), see models.cuh
+template <bool RR_, int VAR_ = WV_PLAIN> struct D3Q27M {
+    static constexpr int VAR = VAR_;
     static constexpr int D = 3, Q = 27;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = 6, MINB_GEN = 4;
-    static constexpr bool TUNE = true;      // compile occupancy variants for the autotuner
+    static constexpr bool TUNE = VAR_ == WV_PLAIN;   // compile occupancy variants for the autotuner
     static constexpr int TUNE_V[3] = {84, 86, 66};   // their targets, 10 * interior + general
     static constexpr bool BATCH = false; // compile the batched multi-case launch
     static constexpr bool DEV = true;
@@ -22,6 +25,12 @@ template <bool RR_> struct D3Q27M {
 };
 
 bool find_kernels_d3q27(int model, int storage, const int* blk, KernelSet& out) {
+    if (model == LBM_TRT || model == KMODEL_RR_TRACE) {
+        // FP64 and FP32 storage, 8 x 4 x 4 blocks
+        if (blk[0] != 8 || blk[1] != 4 || blk[2] != 4 || (storage != ST_F64 && storage != ST_F32)) return false;
+        return model == LBM_TRT ? pick_storage<D3Q27M<false, WV_TRT>, 8, 4, 4>(storage, out)
+                                : pick_storage<D3Q27M<true, WV_TRACE>, 8, 4, 4>(storage, out);
+    }
     if (blk[0] == 8 && blk[1] == 4 && blk[2] == 4) {
         if (model == 1) return pick_storage<D3Q27M<false>, 8, 4, 4>(storage, out);
         if (model == 2) return pick_storage<D3Q27M<true>, 8, 4, 4>(storage, out);

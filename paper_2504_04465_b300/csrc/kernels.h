@@ -26,6 +26,10 @@ struct KernelSet {
                      cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// Kernel-set code of the recursive-regularized collision with the trace of the second-order
+// moments equilibrated (public LBM_RR with trace_eq set); the other codes are the public models.
+constexpr int KMODEL_RR_TRACE = 6;
+
 // Kernels for (model, storage, block shape) of each lattice; false if that combination is not built.
 bool find_kernels_d2q9(int model, int storage, const int* block, KernelSet& out);
 bool find_kernels_d3q27(int model, int storage, const int* block, KernelSet& out);

@@ -32,6 +32,11 @@ template <class M>
 struct hermite_weak<M, std::void_t<decltype(M::HERMITE_WEAK)>> : std::bool_constant<M::HERMITE_WEAK> {};
 
 
+// collision variant of a weakly compressible tensor-product model (WV_*; 0 where not declared)
+template <class M, class = void> struct weak_var : std::integral_constant<int, 0> {};
+template <class M>
+struct weak_var<M, std::void_t<decltype(M::VAR)>> : std::integral_constant<int, M::VAR> {};
+
 enum Mode { MODE_STEP = 0, MODE_READ = 1, MODE_LEDGER = 2 };
 
 // largest |xi_a| of the lattice (its reach)
@@ -332,8 +337,9 @@ __device__ __forceinline__ int collide(const ModelDev& m, const LevelDev& L, Cel
             if constexpr (sizeof(T) == 4) M::template collide<T>(c.f, L.omega_f, m.rho_ref_f);
             else M::template collide<T>(c.f, T(L.omega), T(m.rho_ref));
         } else if constexpr (REL) weak_collide<M::D, true, T, true>(c.f, L.omega_f, m.rho_ref_f, m.inv_rho_ref_f);
-        else if constexpr (sizeof(T) == 4) weak_collide<M::D, M::RR, T>(c.f, L.omega_f, m.rho_ref_f);
-        else weak_collide<M::D, M::RR, T>(c.f, T(L.omega), T(m.rho_ref));
+        else if constexpr (sizeof(T) == 4)
+            weak_collide<M::D, M::RR, T, false, weak_var<M>::value>(c.f, L.omega_f, m.rho_ref_f, T(1), L.omega_m_f);
+        else weak_collide<M::D, M::RR, T, false, weak_var<M>::value>(c.f, T(L.omega), T(m.rho_ref), T(1), T(L.omega_m));
         return 0;
     } else {
         T rho, u[3], Tt;
@@ -493,6 +499,43 @@ __device__ __forceinline__ void coalesce_block(const StepArgs& a, int lev, long 
     }
 }
 
+// Far-field relaxation of Eq. relaxation_pressure, before the collision of a weakly compressible
+// cell (populations held as deviations from w rho_ref): rho' = rho (1 - sigma) + sigma rho_inf,
+// sigma ramping linearly from 0 at r0 to sigma_max at r1 (distance of the cell centre from the
+// centre, finest units).  The equilibrium is linear in rho at fixed u, so f_eq(rho', u) -
+// f_eq(rho, u) = (rho' - rho) E(u) with E the equilibrium of unit density: velocity and
+// non-equilibrium part are kept.
+template <class M, int ST, int BX, int BY, int BZ>
+__device__ __forceinline__ void relax_far_field(const ModelDev& m, const LevelDev& L, int lev, long long b, int l,
+                                                Cell<M, ST>& c) {
+    using T = typename Store<ST>::T;
+    static_assert(!M::HAS_G && M::DEV, "weakly compressible deviation models");
+    const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+    const double h = double(1 << lev);
+    const double x = (double(L.bxyz[3 * b] * BX + lx) + 0.5) * h - m.sp_c[0];
+    const double y = (double(L.bxyz[3 * b + 1] * BY + ly) + 0.5) * h - m.sp_c[1];
+    const double z = M::D == 3 ? (double(L.bxyz[3 * b + 2] * BZ + lz) + 0.5) * h - m.sp_c[2] : 0.0;
+    const double r = sqrt(x * x + y * y + z * z);
+    if (!(r > m.sp_r0)) return;
+    const double sigma = (r >= m.sp_r1 ? 1.0 : (r - m.sp_r0) / (m.sp_r1 - m.sp_r0)) * m.sp_smax;
+    T drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) {
+        drho += c.f[q];
+        if (M::cx(q)) jx += T(M::cx(q)) * c.f[q];
+        if (M::cy(q)) jy += T(M::cy(q)) * c.f[q];
+        if (M::cz(q)) jz += T(M::cz(q)) * c.f[q];
+    }
+    const T rho = T(m.rho_ref) + drho;
+    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const T dr = T(sigma * (m.sp_rho_inf - double(rho)));
+    T E[M::Q];
+    if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(T(1), ux, uy, T(0), E);
+    else weak_feq_dev<M::D, T>(T(1), ux, uy, uz, T(0), E);
+#pragma unroll
+    for (int q = 0; q < M::Q; ++q) c.f[q] += dr * E[q];
+}
+
 // Staging of a block's coarse-ghost post-collision states for the cooperative explosion:
 // populations [q][cell], the finer level's block under each octant of the block (-1: none)
 // and a coarse-ghost flag per cell.  Empty where the explosion is written per cell.
@@ -582,6 +625,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         // interior kernel, binary16 deviations, recursive regularization: the collision writes
         // the storage value directly (fine ghosts, which do not collide, are scaled instead)
         constexpr bool REL = FAST && ST == ST_F16DEV && !M::HAS_G && M::RR && M::DEV;
+        if constexpr (!M::HAS_G && M::DEV) {
+            if (a.m.sponge_on && type != C_FGHOST) relax_far_field<M, ST, BX, BY, BZ>(a.m, L, lev, b, l, c);
+        }
         if (type != C_FGHOST) {
             const int it = collide<M, ST, REL>(a.m, L, c, &conv2);
             if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
@@ -1029,7 +1075,12 @@ bool pick_storage(int storage, KernelSet& out) {
     switch (storage) {
         case ST_F64: out = make_set<M, ST_F64, BX, BY, BZ>(); return true;
         case ST_F32: out = make_set<M, ST_F32, BX, BY, BZ>(); return true;
-        case ST_F16DEV: out = make_set<M, ST_F16DEV, BX, BY, BZ>(); return true;
+        case ST_F16DEV:
+            if constexpr (weak_var<M>::value == 0) {       // the collision variants: FP64 and FP32 only
+                out = make_set<M, ST_F16DEV, BX, BY, BZ>();
+                return true;
+            }
+            return false;
     }
     return false;
 }

@@ -121,10 +121,20 @@ __host__ __device__ __forceinline__ void tp_moments(const T* d, T& drho, T* j, T
 // REL (recursive regularization only): the result is written relative to the reference,
 // f*_i / (w_i rho_ref) - 1, the binary16 storage value, with inv_rho_ref = 1 / rho_ref: the
 // division by 18^D and by w_i rho_ref fold into one product by 1 / (W_x W_y W_z).
-template <int D, bool RR, typename T, bool REL = false>
-__host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, T inv_rho_ref = T(1)) {
+// VAR = WV_TRT (with RR = false): two-relaxation-time collision, the parts of f - f_eq even and
+// odd under xi -> -xi relaxed with omega and omega_m (the opposite of q is Q - 1 - q).
+// VAR = WV_TRACE (with RR = true): the trace of Pi equilibrated (Pi replaced by its deviatoric
+// part, bulk relaxation time one; Appendix A, after Eq. a1Rec).
+enum : int { WV_PLAIN = 0, WV_TRT = 1, WV_TRACE = 2 };
+template <int D, bool RR, typename T, bool REL = false, int VAR = WV_PLAIN>
+__host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, T inv_rho_ref = T(1),
+                                                      T omega_m = T(0)) {
     constexpr int NZ = TP<D>::NZ;
+    constexpr int Q = TP<D>::Q;
     static_assert(!REL || RR, "relative output only for the regularized collision");
+    static_assert(VAR == WV_PLAIN || (VAR == WV_TRT && !RR && !REL) || (VAR == WV_TRACE && RR && !REL),
+                  "collision variant");
+    T fe[VAR == WV_TRT ? Q : 1];
     T drho, j[3], m2[6];
     tp_moments<D, T>(f, drho, j, m2);
     const T rho = rho_ref + drho;
@@ -137,11 +147,20 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, 
     if constexpr (RR) {
         // (1 - 1/tau) Pi_ab, Pi_ab = sum xi_a xi_b f - rho (u_a u_b + c_s^2 delta_ab)
         const T keep = REL ? (T(1) - omega) * inv_rho_ref : T(1) - omega;
-        kxx = keep * (m2[0] - drho / T(3) - rho * ux * ux);
-        kyy = keep * (m2[1] - drho / T(3) - rho * uy * uy);
+        T pxx = m2[0] - drho / T(3) - rho * ux * ux;
+        T pyy = m2[1] - drho / T(3) - rho * uy * uy;
+        T pzz = D == 3 ? m2[2] - drho / T(3) - rho * uz * uz : T(0);
+        if constexpr (VAR == WV_TRACE) {
+            const T tr = (pxx + pyy + pzz) / T(D);
+            pxx -= tr;
+            pyy -= tr;
+            if constexpr (D == 3) pzz -= tr;
+        }
+        kxx = keep * pxx;
+        kyy = keep * pyy;
         kxy = keep * (m2[3] - rho * ux * uy);
         if constexpr (D == 3) {
-            kzz = keep * (m2[2] - drho / T(3) - rho * uz * uz);
+            kzz = keep * pzz;
             kxz = keep * (m2[4] - rho * ux * uz);
             kyz = keep * (m2[5] - rho * uy * uz);
         }
@@ -170,6 +189,7 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, 
                 const T num = A0 + N0;
                 if constexpr (REL) f[q] = num * T(1.0 / (Wc(ix) * Wc(iy)));
                 else if constexpr (RR) f[q] = div_den<T>(num, den, rden);
+                else if constexpr (VAR == WV_TRT) fe[q] = div_den<T>(A0, den, rden);
                 else f[q] += omega * (div_den<T>(A0, den, rden) - f[q]);
             } else {
                 const T B0 = rho_ref * T(Wc(ix) * Wc(iy));
@@ -181,13 +201,27 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, 
                         const T num = eq + N0 * az.E[iz] + N1 * T(X2c(iz)) + N2 * az.X1[iz];
                         if constexpr (REL) f[q] = num * T(1.0 / (Wc(ix) * Wc(iy) * Wc(iz)));
                         else f[q] = div_den<T>(num, den, rden);
+                    } else if constexpr (VAR == WV_TRT) {
+                        fe[q] = div_den<T>(eq, den, rden);
                     } else {
                         f[q] += omega * (div_den<T>(eq, den, rden) - f[q]);
                     }
                 }
             }
         }
+    if constexpr (VAR == WV_TRT) {
+#pragma unroll
+        for (int q = 0; q < Q / 2; ++q) {
+            const int qb = Q - 1 - q;
+            const T dq = f[q] - fe[q], db = f[qb] - fe[qb];
+            const T ev = T(0.5) * (dq + db), od = T(0.5) * (dq - db);
+            f[q] -= omega * ev + omega_m * od;
+            f[qb] -= omega * ev - omega_m * od;
+        }
+        f[Q / 2] -= omega * (f[Q / 2] - fe[Q / 2]);
+    }
     (void)NZ;
+    (void)fe;
 }
 
 // Weakly compressible equilibrium as deviations f_eq,i - w_i rho_ref (boundary cells,

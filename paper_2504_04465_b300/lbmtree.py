@@ -24,7 +24,7 @@ OK = 0
 ERR = {-1: "ARG", -2: "STATE", -3: "CUDA", -4: "OOM", -5: "GRID", -6: "NEWTON", -7: "NONFINITE",
        -10: "UNSUPPORTED"}
 LATTICE = {"D2Q9": 9, "D2Q13": 13, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
-MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4}
+MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4, "trt": 5}
 STORAGE = {"f64": 1, "f32": 2, "f16dev": 3}
 FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}
 GUESS = {"warm": 0, "zero": 1, "poly": 2, "mlp": 3}
@@ -35,7 +35,8 @@ CELL_FLUID, CELL_CGHOST, CELL_FGHOST, CELL_BC, CELL_SOLID = 1, 2, 3, 4, 5
 class CollisionParams(C.Structure):
     _fields_ = [("nu0", C.c_double), ("T0", C.c_double), ("gamma", C.c_double), ("sensor_on", C.c_int),
                 ("sensor_A", C.c_double), ("newton_tol", C.c_double), ("newton_max_iter", C.c_int),
-                ("guess", C.c_int), ("rho_ref", C.c_double), ("newton_fp32", C.c_int)]
+                ("guess", C.c_int), ("rho_ref", C.c_double), ("newton_fp32", C.c_int), ("trace_eq", C.c_int),
+                ("trt_magic", C.c_double)]
 
 
 class Box(C.Structure):
@@ -63,6 +64,7 @@ _sig = {
     "lbm_set_lattice": [_P, C.c_int],
     "lbm_set_collision": [_P, C.c_int, C.POINTER(CollisionParams)],
     "lbm_set_precision": [_P, C.c_int],
+    "lbm_set_sponge": [_P, _D, C.c_double, C.c_double, C.c_double, C.c_double],
     "lbm_set_boundary": [_P, C.c_int, C.c_int, _D],
     "lbm_set_block": [_P, C.c_int, C.c_int, C.c_int],
     "lbm_build_grid": [_P, C.POINTER(C.c_int64), C.c_int, C.POINTER(Box), C.c_int, C.POINTER(Shape), C.c_int],
@@ -273,10 +275,17 @@ class Context:
 
     def set_collision(self, model: str, nu0: float = 0.0, T0: float = 0.0, gamma: float = 1.4,
                       sensor_A: float | None = None, newton_tol: float = 0.0, newton_max_iter: int = 50,
-                      guess: str = "warm", rho_ref: float = 1.0, newton_fp32: bool = False) -> None:
+                      guess: str = "warm", rho_ref: float = 1.0, newton_fp32: bool = False,
+                      trace_eq: bool = False, trt_magic: float = 0.25) -> None:
         p = CollisionParams(nu0, T0, gamma, int(sensor_A is not None), sensor_A or 0.0, newton_tol,
-                            newton_max_iter, GUESS[guess], rho_ref, int(newton_fp32))
+                            newton_max_iter, GUESS[guess], rho_ref, int(newton_fp32), int(trace_eq), trt_magic)
         _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
+
+    def set_sponge(self, centre, r0: float, r1: float, sigma_max: float, rho_inf: float = 1.0) -> None:
+        """Far-field relaxation (Eq. relaxation_pressure), finest units; sigma_max = 0 switches it off."""
+        c = np.zeros(3)
+        c[: len(centre)] = centre
+        _check(_lib.lbm_set_sponge(self._h, _dptr(c), r0, r1, sigma_max, rho_inf), "lbm_set_sponge")
 
     def save(self, path: str) -> None:
         _check(_lib.lbm_save(self._h, str(path).encode()), "lbm_save")
@@ -337,7 +346,10 @@ class Context:
     def configure(self, spec, lattice: str, model: str, storage: str = "f64", block=None, **coll) -> None:
         """Apply a grid specification (see paper_2504_04465_b300.inputs.GridSpec) and build."""
         self.set_lattice(lattice)
+        sponge = coll.pop("sponge", None)
         self.set_collision(model, **coll)
+        if sponge is not None:
+            self.set_sponge(sponge["centre"], sponge["r0"], sponge["r1"], sponge["sigma_max"], sponge["rho_inf"])
         self.set_precision(storage)
         for ax in range(spec.dim):
             for side in "-+":

@@ -9,7 +9,7 @@ from oracle import lattices as L
 from oracle import solver as S
 from paper_2504_04465_b300 import inputs as I
 
-ORACLE_PARAMS = ("nu0", "T0", "gamma", "sensor_A", "newton_tol", "guess")
+ORACLE_PARAMS = ("nu0", "T0", "gamma", "sensor_A", "newton_tol", "guess", "trace_eq", "trt_magic", "sponge")
 
 
 def fields_for(lat, fields_fn, level, coords):

@@ -192,3 +192,39 @@ def test_checkpoint_calls_check_their_arguments(lt, tmp_path):
         ctx.save(str(tmp_path / "a.ckpt"))          # host-only context: nothing to save
     with pytest.raises(lt.LbmError):
         ctx.load(str(tmp_path / "missing.ckpt"))
+
+
+def test_collision_variant_arguments(lt):
+    c = lt.Context(2, device=-1)
+    c.set_lattice("D2Q9")
+    with pytest.raises(lt.LbmError) as e:
+        c.set_collision("trt", nu0=0.0)                  # TRT needs a viscosity
+    assert e.value.code == -1
+    with pytest.raises(lt.LbmError):
+        c.set_collision("bgk", nu0=0.01, trace_eq=True)  # trace equilibration is an RR option
+    with pytest.raises(lt.LbmError):
+        c.set_sponge((0, 0, 0), 10.0, 5.0, 0.1)          # r1 <= r0
+    with pytest.raises(lt.LbmError):
+        c.set_sponge((0, 0, 0), 5.0, 10.0, 1.5)          # sigma_max > 1
+    c.set_collision("trt", nu0=0.01)
+    c.set_precision("f16dev")
+    with pytest.raises(lt.LbmError) as e:
+        c.build_grid((64, 64), 1)                        # TRT: FP64 and FP32 storage only
+    assert e.value.code == -10
+    c2 = lt.Context(2, device=-1)
+    c2.set_lattice("D2Q21")
+    c2.set_collision("trt", nu0=0.01)
+    with pytest.raises(lt.LbmError) as e:
+        c2.build_grid((64, 64), 1)                       # TRT built on D2Q9 and D3Q27
+    assert e.value.code == -10
+    c3 = lt.Context(2, device=-1)
+    c3.set_lattice("D2Q37")
+    c3.set_collision("poly_ddf", nu0=0.01)
+    with pytest.raises(lt.LbmError) as e:
+        c3.set_sponge((0, 0, 0), 5.0, 10.0, 0.1)         # weakly compressible models only
+    assert e.value.code == -10
+    c4 = lt.Context(2, device=-1)
+    c4.set_lattice("D2Q9")
+    c4.set_collision("rr", nu0=0.01, trace_eq=True)
+    c4.set_sponge((32, 32, 0), 5.0, 10.0, 0.1)
+    c4.build_grid((64, 64), 1)
