@@ -75,11 +75,18 @@ extern "C" {
 /* Boundary kinds for the six faces (Appendix A.3), applied on `reach` layers.  PERIODIC wraps.
  * EQ_DIRICHLET imposes rho, u, T through the equilibrium; EQ_DIRICHLET_RHO imposes u, T and
  * extrapolates rho from the nearest interior cell along the face normal; NEUMANN copies every
- * population of that interior cell.  Faces: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+. */
+ * population of that interior cell.  WALL: halfway bounce-back at the face plane (no boundary
+ * layer): a link whose source leaves the domain through wall faces only returns the cell's own
+ * opposite post-collision population plus Ladd's moving-wall term 2 w_i rho_w (xi_i . u_w)/c_s^2
+ * (rho_u_T = {rho_w, u_w}; a link leaving through several wall faces at once takes the mean of
+ * their rho_w u_w; moving walls with the weakly compressible models only).  No ghost layer may
+ * lie within the lattice reach of a wall face (LBM_ERR_GRID).
+ * Faces: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+. */
 #define LBM_PERIODIC          0
 #define LBM_EQ_DIRICHLET      1
 #define LBM_EQ_DIRICHLET_RHO  2
 #define LBM_NEUMANN           3
+#define LBM_WALL              4
 
 /* Initial guess of the Newton solve.  WARM: the multipliers stored in the cell (carried through
  * coalescence/explosion, Sec. 3.2).  ZERO: lambda = 0.  POLY: weighted least-squares fit of

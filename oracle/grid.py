@@ -37,6 +37,7 @@ from .lattices import Lattice
 FLUID, CGHOST, FGHOST, BC, SOLID = 1, 2, 3, 4, 5
 FACES = ["x-", "x+", "y-", "y+", "z-", "z+"]
 BC_KINDS = {"dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}
+WALL = "wall"     # face kind: halfway bounce-back at the face plane, Ladd's moving-wall term
 
 
 class GridError(ValueError):
@@ -62,6 +63,7 @@ class Level:
     bc_kind: np.ndarray = None
     bc_face: np.ndarray = None
     bc_partner: np.ndarray = None
+    wall_term: np.ndarray = None  # (Q, n) velocity term of links bounced at a wall face
 
     @property
     def n(self) -> int:
@@ -247,6 +249,14 @@ def build(spec, lat: Lattice) -> Grid:
                 layer = np.broadcast_to(sel.reshape(bshape), shape) & cells[i]
                 if FACES[face] not in g.faces:
                     raise GridError(f"non-periodic face {FACES[face]} has no boundary condition")
+                if g.faces[FACES[face]][0] == WALL:
+                    # a wall face has no boundary layer; its links bounce back (_links).  Ghost
+                    # layers within the reach of a wall would need bounce-back in pure-streaming
+                    # cells, which the method does not define: refused
+                    near = np.broadcast_to(sel.reshape(bshape), shape)
+                    if (near & ((ct == CGHOST) | (ct == FGHOST))).any():
+                        raise GridError(f"ghost layers of level {i} within the reach of wall face {FACES[face]}")
+                    continue
                 # priority: any Dirichlet face over Neumann; among equals, the first face
                 kind = BC_KINDS[g.faces[FACES[face]][0]]
                 cur = bc_face >= 0
@@ -310,8 +320,37 @@ def _links(g: Grid, i: int, solid0) -> None:
                 hit = np.zeros(n, dtype=bool)
                 hit[okc] = solid0[tuple(c[okc].T)]
                 blocked[q] |= hit
+    # wall faces (Appendix A.3, Ladd's velocity bounce-back): a link whose source lies outside
+    # the domain through wall faces only bounces back and gains 2 w_q (xi_q . rho_w u_w) / c_s^2,
+    # with rho_w u_w the mean over the faces the link crosses (reading R38)
+    wall_term = np.zeros((Q, n))
+    for q in range(Q):
+        s = lv.coords - lat.xi[q][None, :]
+        crossed = np.zeros(n, dtype=np.int64)
+        nonwall = np.zeros(n, dtype=bool)
+        mom = np.zeros((n, g.D))
+        for ax in range(g.D):
+            if g.periodic[ax]:
+                continue
+            for side, out in ((0, s[:, ax] < 0), (1, s[:, ax] >= shape[ax])):
+                if not out.any():
+                    continue
+                spec_f = g.faces.get(FACES[2 * ax + side])
+                if spec_f is None or spec_f[0] != WALL:
+                    nonwall |= out
+                    continue
+                rho_w = spec_f[1] if len(spec_f) > 1 else 1.0
+                u_w = np.asarray(spec_f[2] if len(spec_f) > 2 else (0.0,) * 3, float)[: g.D]
+                crossed += out
+                mom[out] += rho_w * u_w[None, :]
+        wall = (crossed > 0) & ~nonwall & (src[q] < 0)
+        blocked[q] |= wall
+        if wall.any():
+            mean = mom[wall] / crossed[wall][:, None]
+            wall_term[q, wall] = 2.0 * lat.w[q] * (mean @ lat.xi[q].astype(np.float64)) / lat.cs2
     blocked[:, solid_cells] = False
-    lv.src, lv.blocked = src, blocked
+    wall_term[:, solid_cells] = 0.0
+    lv.src, lv.blocked, lv.wall_term = src, blocked, wall_term
     # every bulk fluid cell must see a cell (or a solid) in every direction
     fl = lv.ctype == FLUID
     missing = (src < 0) & ~blocked & fl[None, :]

@@ -17,7 +17,7 @@ Sources (arXiv 2504.04465):
     each level's own units, theta = c_s^2 (weakly compressible) or T0 (compressible, R4).
   * Appendix A: polyatomic DDF (Eqs. gEq, polyTemp), kinetic shock sensor (Eqs. DeltaAvg,
     shock_function; reading R10: alpha = 1 below 0.01, terms with f_eq <= 1e-300 skipped),
-    boundary conditions (A.3; readings R11, R12).
+    boundary conditions (A.3; readings R11, R12; wall faces with Ladd's moving-wall term, R38).
   * Populations with no source (outside a non-periodic face, or a coarse cell covered by the
     finer level) are set to 0 by streaming; they are either overwritten (boundary layers,
     coalescence) or never reach a bulk cell.
@@ -81,6 +81,8 @@ class Solver:
         if trace_eq and model != "rr":
             raise ValueError("trace equilibration applies to the recursive-regularized collision")
         self.sponge = sponge
+        if self.comp and any(np.any(lv.wall_term != 0.0) for lv in grid.levels):
+            raise ValueError("moving walls are built for the weakly compressible models")
         if sponge is not None and self.comp:
             raise ValueError("the far-field relaxation is built for the weakly compressible models")
         self.t = 0
@@ -258,10 +260,10 @@ class Solver:
         # streaming: f_i(x, t+1) = f*_i(x - xi_i, t); blocked links bounce back
         self.f[lev] = self._stream(lv, fs)
         if self.comp:
-            self.g_[lev] = self._stream(lv, gs)
+            self.g_[lev] = self._stream(lv, gs, wall_terms=False)
         self._boundaries(lev)
 
-    def _stream(self, lv, fs):
+    def _stream(self, lv, fs, wall_terms: bool = True):
         lat = self.lat
         new = np.zeros_like(fs)
         opp = lat.opp
@@ -270,7 +272,7 @@ class Solver:
             ok = (src >= 0) & ~lv.blocked[q]
             new[q, ok] = fs[q, src[ok]]
             b = lv.blocked[q]
-            new[q, b] = fs[opp[q], b]
+            new[q, b] = fs[opp[q], b] + (lv.wall_term[q, b] if wall_terms else 0.0)
         new[:, lv.ctype == SOLID] = 0.0
         return new
 

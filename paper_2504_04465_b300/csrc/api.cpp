@@ -213,6 +213,7 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
         d.omega_m = nu > 0 ? 1.0 / (c->params.trt_magic / (d.tau - 0.5) + 0.5) : d.omega;
         d.omega_m_f = (float)d.omega_m;
         d.bxyz = c->dl[i].bxyz;
+        for (int k = 0; k < 3; ++k) d.shape[k] = (int)bl.shape[k];
     }
     ModelDev& m = a.m;
     m.cs2 = theta;
@@ -600,12 +601,14 @@ int lbm_set_precision(lbm_ctx* c, int storage) {
 int lbm_set_boundary(lbm_ctx* c, int face, int kind, const double* v) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (face < 0 || face > 5) return fail(LBM_ERR_ARG, "face out of range");
-    if (kind < LBM_PERIODIC || kind > LBM_NEUMANN) return fail(LBM_ERR_ARG, "unknown boundary kind");
+    if (kind < LBM_PERIODIC || kind > LBM_WALL) return fail(LBM_ERR_ARG, "unknown boundary kind");
     if ((kind == LBM_EQ_DIRICHLET || kind == LBM_EQ_DIRICHLET_RHO) && !v) return fail(LBM_ERR_ARG, "Dirichlet values missing");
     if (c->built) return fail(LBM_ERR_STATE, "boundaries must be set before lbm_build_grid");
     FaceSpec& f = c->faces[face];
     f.kind = kind;
     if (v) { f.rho = v[0]; f.u[0] = v[1]; f.u[1] = v[2]; f.u[2] = v[3]; f.T = v[4]; }
+    else { f.rho = 1.0; f.u[0] = f.u[1] = f.u[2] = 0.0; f.T = 0.0; }
+    if (kind == LBM_WALL && !(f.rho > 0)) return fail(LBM_ERR_ARG, "wall density must be positive");
     return LBM_OK;
 }
 
@@ -634,6 +637,10 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
          c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
     if (c->sp_smax > 0 && !weak) return fail(LBM_ERR_UNSUPPORTED, "the far-field relaxation is built for the weakly compressible models");
+    for (int f = 0; f < 6; ++f)
+        if (c->faces[f].kind == LBM_WALL && !weak &&
+            (c->faces[f].u[0] != 0.0 || c->faces[f].u[1] != 0.0 || c->faces[f].u[2] != 0.0))
+            return fail(LBM_ERR_UNSUPPORTED, "moving walls are built for the weakly compressible models");
     if (!find_kernels(c->lattice, c->kmodel(), c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
     GridInput in;

@@ -8,7 +8,9 @@
 // A coarse-ghost population is supplied by coalescence unless it was streamed from a coarse
 // bulk or boundary cell (the rest population always stays); with that rule the coupling is
 // exactly conservative, including at patch corners where diagonal links cut through the fine
-// bulk.  At concave corners of the finer region a child's two-step streaming history can leave
+// bulk.  Wall faces have no boundary layer: a link whose source leaves the domain through wall
+// faces only bounces back (record mask bit, b bit 1 for the moving-wall term).  At concave
+// corners of the finer region a child's two-step streaming history can leave
 // the finer level; such a child enters the coalescence with the ghost's own streamed
 // population, which keeps the coupling conservative there too (record flag b bit 0).  Boundary layers are the `reach` outer layers on non-periodic faces (Appendix A.3); a
 // boundary cell's partner is the cell obtained by clamping its coordinates into the interior.
@@ -81,6 +83,30 @@ struct Geo {
         return false;
     }
     bool is_cell(int i, const int64_t* c) const { return bulk(i, c) || cghost(i, c); }
+    // within the lattice reach of a wall face
+    bool near_wall(int i, const int64_t* c) const {
+        for (int d = 0; d < D; ++d) {
+            if (periodic[d]) continue;
+            if (in.faces[2 * d].kind == BCK_WALL && c[d] < R) return true;
+            if (in.faces[2 * d + 1].kind == BCK_WALL && c[d] >= shape[i][d] - R) return true;
+        }
+        return false;
+    }
+    // the pull source c - xi leaves the domain through wall faces only (periodic axes wrap)
+    bool wall_link(int i, const int64_t* c, const int* xi) const {
+        int walls = 0;
+        for (int d = 0; d < D; ++d) {
+            if (periodic[d]) continue;
+            const int64_t s = c[d] - xi[d];
+            int f = -1;
+            if (s < 0) f = 2 * d;
+            else if (s >= shape[i][d]) f = 2 * d + 1;
+            if (f < 0) continue;
+            if (in.faces[f].kind != BCK_WALL) return false;
+            ++walls;
+        }
+        return walls > 0;
+    }
     bool fghost(int i, const int64_t* c) const {
         if (i + 1 >= L) return false;
         int64_t p[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
@@ -125,6 +151,7 @@ struct Geo {
                 bool in_layer = side == 0 ? c[d] < R : c[d] >= shape[i][d] - R;
                 if (!in_layer) continue;
                 int f = 2 * d + side;
+                if (in.faces[f].kind == BCK_WALL) continue;      // walls have no boundary layer
                 if (best < 0) { best = f; continue; }
                 int kb = in.faces[best].kind, kf = in.faces[f].kind;
                 if (kb == BCK_NEUMANN && kf != BCK_NEUMANN) best = f;
@@ -319,6 +346,7 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                             if (fg && !g.bulk(i, c)) e = "fine ghosts overlap another ghost layer";
                             if (so && (cg || fg)) e = "solid inside a ghost layer";
                             if (bf >= 0 && (cg || fg)) e = "boundary layer overlaps a ghost layer";
+                            if ((cg || fg) && g.near_wall(i, c)) e = "ghost layer within the reach of a wall face";
                             if (cg) t = C_CGHOST;
                             else if (fg) t = C_FGHOST;
                             else if (so) t = C_SOLID;
@@ -432,6 +460,12 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                                 int64_t pc;
                                 if (locate(i, p, pc) == C_SOLID) { blocked = true; break; }
                             }
+                        }
+                        if (!blocked && st == C_ABSENT && g.wall_link(i, c, g.lat.xi[q])) {
+                            // halfway bounce-back at a wall face (record b bit 1: the kernels add
+                            // Ladd's moving-wall term to such links)
+                            blocked = true;
+                            r.b |= 2;
                         }
                         if (blocked) {
                             r.mask |= 1ull << q;

@@ -14,7 +14,7 @@
 
 namespace lbm {
 
-enum BcKind { BCK_PERIODIC = 0, BCK_DIR = 1, BCK_DIR_RHO = 2, BCK_NEUMANN = 3 };
+enum BcKind { BCK_PERIODIC = 0, BCK_DIR = 1, BCK_DIR_RHO = 2, BCK_NEUMANN = 3, BCK_WALL = 4 };
 
 // Per-cell record of the non-simple cells.
 //   FLUID : mask = bounce-back directions (link blocked by a solid)

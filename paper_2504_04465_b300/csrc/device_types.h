@@ -30,6 +30,7 @@ struct LevelDev {
     double omega_m;          // two-relaxation-time collision: rate of the odd part
     float omega_m_f;
     const int* bxyz;         // block coordinates (3 per block), for position-dependent terms
+    int shape[3];            // cells per axis of the level
     const int* blist[2];     // [0] 2 * block + s: simple (s = 0) and streaming (s = 1) blocks, [1] the others
                              // (block nb of f/g holds zero populations: the missing-neighbour stand-in)
     long long nlist[2];

@@ -157,6 +157,32 @@ __device__ __forceinline__ void moments(const ModelDev& m, const Cell<M, ST>& c,
     if constexpr (M::HAS_G) Tt = (e2 + gs - r * (u[0] * u[0] + u[1] * u[1])) / (T(2) * r * T(m.Cv));
 }
 
+// Ladd's moving-wall term of link q of cell l of block b (Appendix A.3): when the pull source
+// leaves the domain through wall faces only, 2 w_q (xi_q . rho_w u_w) / c_s^2 with rho_w u_w the
+// mean over the wall faces crossed (periodic axes wrap and are not crossings); 0 otherwise (a
+// link blocked by a solid).  Weakly compressible models (c_s^2 = m.cs2).
+template <class M, int BX, int BY, int BZ>
+__device__ __forceinline__ double wall_term(const ModelDev& m, const LevelDev& L, long long b, int l, int q) {
+    const int lc[3] = {L.bxyz[3 * b] * BX + l % BX, L.bxyz[3 * b + 1] * BY + (l / BX) % BY,
+                       L.bxyz[3 * b + 2] * BZ + l / (BX * BY)};
+    const int xi[3] = {M::cx(q), M::cy(q), M::cz(q)};
+    double mom[3] = {0.0, 0.0, 0.0};
+    int walls = 0;
+#pragma unroll
+    for (int d = 0; d < M::D; ++d) {
+        const int s = lc[d] - xi[d];
+        const int f = s < 0 ? 2 * d : (s >= L.shape[d] ? 2 * d + 1 : -1);
+        if (f < 0 || m.faces[f].kind == LBM_PERIODIC) continue;
+        if (m.faces[f].kind != LBM_WALL) return 0.0;
+        ++walls;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mom[k] += m.faces[f].rho * m.faces[f].u[k];
+    }
+    if (!walls) return 0.0;
+    const double dot = double(xi[0]) * mom[0] + double(xi[1]) * mom[1] + double(xi[2]) * mom[2];
+    return 2.0 * M::w(q) * dot / (double(walls) * m.cs2);
+}
+
 // ------------------------------------------------------------------ state assembly
 // Pre-collision state of the cell (level lev, block b, local l) at the current iteration:
 //   FLUID : pull gather, bounce-back on blocked links
@@ -182,12 +208,14 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
         unsigned long long bmask = 0ull, umask = 0ull;
         long long child = -1;
         bool corner = false;    // a coarse ghost at a concave corner of the finer region
+        bool walls = false;     // a fluid cell with links bounced at wall faces
         if (!simple && type != C_FGHOST) {
             const int r = L.rec_id[cell];
             if (r >= 0) {
                 const CellRecDev rec = L.recs[r];
                 if (type == C_FLUID) {
                     bmask = rec.mask;
+                    walls = (rec.b & 2) != 0;
                 } else {
                     umask = rec.mask;
                     child = rec.a;
@@ -201,6 +229,9 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
             T gv = T(0);
             if (bmask & (1ull << q)) {
                 load_pop<M, ST, BX * BY * BZ>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);      // f_q(x) = f*_qbar(x)
+                if constexpr (!M::HAS_G) {
+                    if (walls) c.f[q] += T(wall_term<M, BX, BY, BZ>(a.m, L, b, l, q));
+                }
             } else if (!(coal && (umask & (1ull << q))) || corner) {
                 // (a corner ghost keeps its own streamed unknowns: they stand in for the
                 // children whose history left the finer level)
@@ -969,9 +1000,13 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
     const int type = L.bflag[b] == 1 ? (int)C_FLUID : (int)L.type[cell];
     if (type == C_ABSENT || type == C_SOLID) return;
     unsigned long long bmask = 0ull;
+    bool walls = false;
     if (L.bflag[b] != 1 && type == C_FLUID) {
         const int r = L.rec_id[cell];
-        if (r >= 0) bmask = L.recs[r].mask;
+        if (r >= 0) {
+            bmask = L.recs[r].mask;
+            walls = (L.recs[r].b & 2) != 0;
+        }
     }
     const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
     const S* Ef = (const S*)L.f[1];
@@ -983,6 +1018,16 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
         const int qb = M::Q - 1 - q;
         long long src;
         int qs;
+        if constexpr (!M::HAS_G) {
+            if (walls && (bmask & (1ull << qb))) {
+                // a link bounced at a moving wall: the first gather adds the wall term back
+                using T = typename Store<ST>::T;
+                T e, dummy;
+                load_pop<M, ST, BS>(L, 1, cell, qb, a.m, e, dummy);
+                store_pop<M, ST, BS>(L, 0, cell, q, a.m, e - T(wall_term<M, BX, BY, BZ>(a.m, L, b, l, qb)), T(0));
+                continue;
+            }
+        }
         if (bmask & (1ull << qb)) {
             src = cell;
             qs = qb;

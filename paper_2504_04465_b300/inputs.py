@@ -163,6 +163,28 @@ def riemann12_fields(centres: np.ndarray, nc: int, T0: float, gamma: float = 1.4
     return rho, u, T0 * st[:, 3] / rho
 
 
+# ------------------------------------------------------------------ lid-driven cavity
+def cavity_spec(n: int, lid_u: float, n_levels: int = 1, patch: tuple | None = None, dim: int = 2) -> GridSpec:
+    """The L x L (x L) lid-driven cavity of Sec. 5.1 in finest units (n cells per side): wall faces
+    (halfway bounce-back) on every side, the lid y+ moving along x at lid_u (Ladd's velocity
+    bounce-back, Appendix A.3).  patch = (lo, hi): a centred refinement box (finest units, on
+    every axis) kept at least the lattice reach from the walls."""
+    faces = {f: ("wall", 1.0, (0.0, 0.0, 0.0)) for f in ("x-", "x+", "y-", "y+", "z-", "z+")[: 2 * dim]}
+    faces["y+"] = ("wall", 1.0, (lid_u, 0.0, 0.0))
+    boxes = []
+    if patch is not None:
+        lo, hi = patch
+        boxes.append((0, (lo,) * dim, (hi,) * dim))
+    return GridSpec(dim, (n,) * dim, n_levels, boxes, (False,) * dim, faces)
+
+
+def couette_spec(nx: int, ny: int, wall_u: float) -> GridSpec:
+    """Plane Couette flow: periodic along x, a resting wall at y- and a wall moving along x at
+    y+ (finest units, one level)."""
+    faces = {"y-": ("wall", 1.0, (0.0, 0.0, 0.0)), "y+": ("wall", 1.0, (wall_u, 0.0, 0.0))}
+    return GridSpec(2, (nx, ny), 1, [], (True, False), faces)
+
+
 # ------------------------------------------------------------------ 3D flow past a sphere
 def sphere_spec(scale: int = 1) -> GridSpec:
     """Four-level box around a sphere: 1024x512x512 finest units at scale 1, sphere diameter 64

@@ -26,7 +26,7 @@ ERR = {-1: "ARG", -2: "STATE", -3: "CUDA", -4: "OOM", -5: "GRID", -6: "NEWTON", 
 LATTICE = {"D2Q9": 9, "D2Q13": 13, "D2Q21": 21, "D2Q37": 37, "D3Q27": 27}
 MODEL = {"bgk": 1, "rr": 2, "poly_ddf": 3, "num_ddf": 4, "trt": 5}
 STORAGE = {"f64": 1, "f32": 2, "f16dev": 3}
-FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3}
+FACE_KIND = {"periodic": 0, "dirichlet": 1, "dirichlet_rho": 2, "neumann": 3, "wall": 4}
 GUESS = {"warm": 0, "zero": 1, "poly": 2, "mlp": 3}
 FACES = ["x-", "x+", "y-", "y+", "z-", "z+"]
 CELL_FLUID, CELL_CGHOST, CELL_FGHOST, CELL_BC, CELL_SOLID = 1, 2, 3, 4, 5

@@ -228,3 +228,30 @@ def test_collision_variant_arguments(lt):
     c4.set_collision("rr", nu0=0.01, trace_eq=True)
     c4.set_sponge((32, 32, 0), 5.0, 10.0, 0.1)
     c4.build_grid((64, 64), 1)
+
+
+WALL_SPECS = [
+    ("cavity_q9", lambda: I.cavity_spec(64, 0.1, 2, (16, 48)), "D2Q9", "rr"),
+    ("cavity_q27", lambda: I.cavity_spec(32, 0.05, 2, (8, 24), dim=3), "D3Q27", "rr"),
+    ("couette_q9", lambda: I.couette_spec(32, 16, 0.05), "D2Q9", "bgk"),
+    ("closed_q37", lambda: I.GridSpec(2, (128, 32), 1, [], (False, True),
+                                      {f: ("wall", 1.0, (0.0, 0.0, 0.0)) for f in ("x-", "x+")}), "D2Q37", "poly_ddf"),
+]
+
+
+@pytest.mark.parametrize("name,mk,latname,model", WALL_SPECS, ids=[s[0] for s in WALL_SPECS])
+def test_wall_grids_match_oracle(lt, name, mk, latname, model):
+    _compare(lt, mk(), latname, model)
+
+
+def test_wall_arguments(lt):
+    c = lt.Context(2, device=-1)
+    c.set_lattice("D2Q9")
+    c.set_collision("rr", nu0=0.01)
+    with pytest.raises(lt.LbmError):
+        c.configure(I.cavity_spec(64, 0.1, 2, (0, 32)), "D2Q9", "rr")      # ghosts next to a wall
+    c2 = lt.Context(2, device=-1)
+    with pytest.raises(lt.LbmError) as e:                                   # moving wall, compressible
+        c2.configure(I.GridSpec(2, (128, 32), 1, [], (False, True),
+                                {"x-": ("wall", 1.0, (0.0, 0.1, 0.0)), "x+": ("wall",)}), "D2Q37", "poly_ddf")
+    assert e.value.code == -10
