@@ -866,6 +866,44 @@ def form_d2q9(args, stream, local):
     return out
 
 
+def form_aa(args, stream, local):
+    """AA-pattern in-place streaming against the two-buffer path on the same single-level
+    workloads: a periodic D3Q27 RR box (512 x 256 x 256 at scale 1, perturbed uniform flow) and a
+    D2Q9 RR Taylor-Green square (8192^2), FP32; updates per second, HBM fraction and device
+    memory of each, and the largest D3Q27 FP32 box that fits the GPU's free memory with each."""
+    import torch
+    from paper_2504_04465_b300 import lbmtree as lt
+    s = 1 if args.scale == 1 else 2
+    cases = {"d3q27_box": (I.GridSpec(3, (512 // s, 256 // s, 256 // s), 1, [], (True, True, True)), "D3Q27", 216),
+             "d2q9_tg": (I.taylor_green_spec(8192 // s, 0, 0, 1), "D2Q9", 72)}
+    out = {"storage": "f32", "model": "rr", "note": "identical arithmetic (readouts bitwise equal, tests/test_gpu_aa.py)"}
+    for name, (spec, lat, bpu) in cases.items():
+        for mode in ("ab", "aa"):
+            ctx = lt.Context(spec.dim, device=local, stream=stream.cuda_stream)
+            ctx.configure(spec, lat, "rr", "f32", nu0=0.01, streaming=mode)
+            ctx.use_graph(True)
+            lv, xyz, _ = ctx.cells()
+            n = lv.size
+            rho = 1.0 + 1e-3 * I.uniform_at(71, 0, xyz[:, :spec.dim], 0)
+            u = 0.02 + 1e-3 * np.stack([I.uniform_at(72 + k, 0, xyz[:, :spec.dim], 0) for k in range(spec.dim)])
+            ctx.init_fields(rho, u)
+            ctx.step(4)
+            K = 20
+            ms = _event_ms(stream, lambda: ctx.step(K)) / K
+            ctx.sync()
+            st = ctx.stats()
+            out[f"{name}_{mode}"] = {"cells": int(n), "ms_per_step": ms, "value": n / ms / 1e3, "unit": "MLUPS",
+                                     "device_gb": st.device_bytes / 1e9,
+                                     "roofline": roofline(n, ms, bpu, None, None, local)}
+            ctx.close()
+    free, total = torch.cuda.mem_get_info(local)
+    # D3Q27 FP32: 27 x 4 bytes per population buffer and cell, plus tables (~ 8 bytes per cell)
+    for mode, nbuf in (("ab", 2), ("aa", 1)):
+        out[f"largest_d3q27_f32_cells_{mode}"] = int(0.95 * free / (nbuf * 108 + 8))
+    out["free_gb"] = free / 1e9
+    return out
+
+
 def form_batched(args, stream, local):
     """48 uneven 2D cases (D2Q9 Taylor-Green and D2Q37 Sod tubes, 2-4 levels): one batched
     launch per lattice group per fine iteration (CUDA graph of the schedule period) against
@@ -1017,7 +1055,8 @@ def run_ours(args, world, rank, local):
                          ("sod_numerical", lambda: form_sod_numerical(args, stream, local)),
                          ("d2q21_weak", lambda: form_d2q21_weak(args, stream, local)),
                          ("naca37", lambda: form_naca37(args, stream, local)),
-                         ("riemann12", lambda: form_riemann12(args, stream, local))):
+                         ("riemann12", lambda: form_riemann12(args, stream, local)),
+                         ("aa", lambda: form_aa(args, stream, local))):
             if name not in args.forms.split(","):
                 continue
             try:
@@ -1054,7 +1093,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / learned-guess / batched forms")
-    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37,riemann12",
+    ap.add_argument("--forms", default="fp16_store,learned,batched,d2q37_sod,d2q9_tg,sod_numerical,d2q21_weak,naca37,riemann12,aa",
                     help="which forms to run (comma list; sod_numerical is the paper's Sec. 7.6 Sod benchmark)")
     ap.add_argument("--sod-lattices", default="all", help="sod_numerical: lattices (D2Q21,D2Q37 or all)")
     ap.add_argument("--sod-grids", default="unif,band,sqr",

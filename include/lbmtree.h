@@ -184,6 +184,16 @@ int lbm_set_guess(lbm_ctx* ctx, int guess);
  * the Newton solve, also on a built and running context. */
 int lbm_set_newton_precision(lbm_ctx* ctx, int fp32, double tol);
 int lbm_set_precision(lbm_ctx* ctx, int storage);
+/* Streaming scheme (before lbm_build_grid).  AB (default): two population buffers, pull
+ * streaming.  AA: one buffer updated in place (the AA pattern; Sec. 9's outlook): even
+ * iterations read and write each cell's own slots (the read reversed), odd iterations gather from
+ * the neighbours and write each post-collision population back into the slot its opposite was
+ * read from.  Results are bitwise those of AB; population memory is halved.  Single-level grids
+ * with periodic, wall and imposed-equilibrium (EQ_DIRICHLET) faces, D2Q9/D3Q27 BGK and RR and
+ * D2Q37 polynomial DDF; otherwise lbm_build_grid returns LBM_ERR_UNSUPPORTED. */
+#define LBM_STREAM_AB 0
+#define LBM_STREAM_AA 1
+int lbm_set_streaming(lbm_ctx* ctx, int mode);
 /* Far-field relaxation of Eq. relaxation_pressure (weakly compressible models, p = rho c_s^2):
  * before every collision, rho' = rho (1 - sigma) + sigma rho_inf with sigma = 0 for r < r0,
  * sigma_max (r - r0)/(r1 - r0) for r0 <= r < r1 and sigma_max beyond, r the distance of the

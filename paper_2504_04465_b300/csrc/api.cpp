@@ -157,6 +157,7 @@ struct lbm_ctx {
     // buffer holding the current state of level i after tt iterations: ceil(tt / 2^i) steps done
     int cur(int i, int64_t tt) const { return int(((tt + (int64_t(1) << i) - 1) >> i) & 1); }
     bool comp() const { return model == LBM_COMP_POLY || model == LBM_COMP_NUMERICAL; }
+    int streaming = LBM_STREAM_AB;   // lbm_set_streaming
     bool weak() const { return model == LBM_BGK || model == LBM_RR || model == LBM_TRT; }
     // kernel-set code of the collision: the public model, with the trace-equilibrated RR as 6
     int kmodel() const { return (model == LBM_RR && params.trace_eq) ? KMODEL_RR_TRACE : model; }
@@ -233,6 +234,7 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
     m.newton_max_iter = c->params.newton_max_iter > 0 ? c->params.newton_max_iter : 50;
     m.guess = c->params.guess;
     m.newton_fp32 = c->params.newton_fp32;
+    a.aa = c->streaming == LBM_STREAM_AA ? 1 : 0;
     m.sponge_on = c->sp_smax > 0 ? 1 : 0;
     for (int d = 0; d < 3; ++d) m.sp_c[d] = c->sp_c[d];
     m.sp_r0 = c->sp_r0;
@@ -298,6 +300,11 @@ int64_t current_args(const lbm_ctx* c, StepArgs& a) {
     a.block_off[n] = off;
     a.n_active = n;
     for (int i = 0; i < L; ++i) a.rd[i] = c->cur(i, c->t);
+    if (a.aa) {
+        // one buffer: after an even number of iterations it holds layout L1 (own slot qbar = f_q)
+        a.rd[0] = 0;
+        a.aa_l1 = (c->t % 2 == 0) ? 1 : 0;
+    }
     return off;
 }
 
@@ -321,6 +328,10 @@ float bf16_round_host(float v) {
 
 // one fine iteration: the general kernel on the side stream beside the interior kernel
 void launch_step(lbm_ctx* c, const StepArgs& a) {
+    if (a.aa) {                       // in-place streaming: one launch over the single level
+        c->ks.aa(a, c->stream);
+        return;
+    }
     const int64_t nf = a.list_off[0][a.n_active], ng = a.list_off[1][a.n_active];
     if (nf && ng) {
         cudaEventRecord(c->ev_fork, c->stream);
@@ -339,7 +350,7 @@ int launch_iterations(lbm_ctx* c, int64_t n) {
         const int64_t nb = iteration_args(c, c->t, a);
         if (nb) {
             launch_step(c, a);
-            c->launches += (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
+            c->launches += a.aa ? 1 : (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
         }
         c->t++;
     }
@@ -378,7 +389,7 @@ int launches_per_span(const lbm_ctx* c) {
     int n = 0;
     for (int64_t k = 0; k < 2 * c->period(); ++k) {
         StepArgs a;
-        if (iteration_args(c, k, a)) n += (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
+        if (iteration_args(c, k, a)) n += a.aa ? 1 : (a.list_off[0][a.n_active] > 0) + (a.list_off[1][a.n_active] > 0);
     }
     return n;
 }
@@ -590,6 +601,14 @@ int lbm_set_sponge(lbm_ctx* c, const double centre[3], double r0, double r1, dou
     return LBM_OK;
 }
 
+int lbm_set_streaming(lbm_ctx* c, int mode) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (mode != LBM_STREAM_AB && mode != LBM_STREAM_AA) return fail(LBM_ERR_ARG, "unknown streaming mode");
+    if (c->built) return fail(LBM_ERR_STATE, "streaming must be set before lbm_build_grid");
+    c->streaming = mode;
+    return LBM_OK;
+}
+
 int lbm_set_precision(lbm_ctx* c, int storage) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16DEV) return fail(LBM_ERR_ARG, "unknown storage");
@@ -637,12 +656,20 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
          c->lattice != LBM_D2Q37))
         return fail(LBM_ERR_UNSUPPORTED, "lattice/model combination not built");
     if (c->sp_smax > 0 && !weak) return fail(LBM_ERR_UNSUPPORTED, "the far-field relaxation is built for the weakly compressible models");
+    if (c->streaming == LBM_STREAM_AA) {
+        if (n_levels != 1) return fail(LBM_ERR_UNSUPPORTED, "AA streaming is built for single-level grids");
+        for (int f = 0; f < 2 * c->dim; ++f)
+            if (c->faces[f].kind == LBM_EQ_DIRICHLET_RHO || c->faces[f].kind == LBM_NEUMANN)
+                return fail(LBM_ERR_UNSUPPORTED, "AA streaming takes periodic, wall and imposed-equilibrium faces");
+    }
     for (int f = 0; f < 6; ++f)
         if (c->faces[f].kind == LBM_WALL && !weak &&
             (c->faces[f].u[0] != 0.0 || c->faces[f].u[1] != 0.0 || c->faces[f].u[2] != 0.0))
             return fail(LBM_ERR_UNSUPPORTED, "moving walls are built for the weakly compressible models");
     if (!find_kernels(c->lattice, c->kmodel(), c->storage, c->block, c->params.newton_fp32 != 0, c->ks))
         return fail(LBM_ERR_UNSUPPORTED, "no kernel for this lattice/model/storage/block shape");
+    if (c->streaming == LBM_STREAM_AA && !c->ks.aa)
+        return fail(LBM_ERR_UNSUPPORTED, "AA streaming is compiled for D2Q9 and D3Q27 (BGK, RR) and D2Q37 (polynomial DDF)");
     GridInput in;
     in.dim = c->dim;
     for (int d = 0; d < 3; ++d) in.extent[d] = extent[d];
@@ -717,9 +744,15 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         d.rec_id = (int*)c->dalloc(lv.rec_id.size() * 4);
         d.recs = (CellRecDev*)c->dalloc(lv.recs.size() * sizeof(CellRecDev));
         // one extra block of zero populations stands in for missing neighbour blocks
-        for (int k = 0; k < 2; ++k) {
+        // AA streaming keeps one population buffer (both pointers name it)
+        const int nbuf = c->streaming == LBM_STREAM_AA ? 1 : 2;
+        for (int k = 0; k < nbuf; ++k) {
             d.f[k] = c->dalloc(size_t(Q) * (ncell + BS) * es);
             if (has_g) d.g[k] = c->dalloc(size_t(Q) * (ncell + BS) * es);
+        }
+        if (nbuf == 1) {
+            d.f[1] = d.f[0];
+            d.g[1] = d.g[0];
         }
         if (has_lam) d.lam = (double*)c->dalloc(size_t(2) * 8 * ncell * 8);
         if (!d.nbr || !d.type || !d.bflag || !d.rec_id || !d.recs || !d.f[0] || !d.f[1] ||
@@ -1407,6 +1440,7 @@ int lbm_batch_create(lbm_batch** out, lbm_ctx* const* cases, int n, void* stream
         if (check_ctx(cases[k])) return LBM_ERR_ARG;
         if (int r = ready(cases[k])) return r;
         if (cases[k]->device != cases[0]->device) return fail(LBM_ERR_ARG, "cases on different devices");
+        if (cases[k]->streaming != LBM_STREAM_AB) return fail(LBM_ERR_UNSUPPORTED, "batched cases use two-buffer streaming");
         for (int j = 0; j < k; ++j)
             if (cases[j] == cases[k]) return fail(LBM_ERR_ARG, "a case is listed twice");
     }

@@ -70,6 +70,8 @@ struct StepArgs {
     long long list_off[2][MAX_LEVELS + 1];    // over the simple / other block lists
     int rd[MAX_LEVELS];               // buffer index read by each level this iteration
     int sync_fg[MAX_LEVELS];          // 1: the level's fine ghosts receive an explosion now
+    int aa;                           // AA-pattern streaming: one population buffer (single level)
+    int aa_l1;                        // readout: the buffer holds layout L1 (own slot qbar = f_q)
     ModelDev m;
     int* status;                      // first error code (atomicCAS from 0)
     unsigned long long* nstat;        // newton: [0] iter sum, [1] updates, [2] nonconverged, [3..18] hist

@@ -70,6 +70,7 @@ struct D2Q37M {
     static constexpr int MINB_FAST = 4, MINB_GEN = 2;
     static constexpr bool TUNE = false;      // compile occupancy variants for the autotuner
     static constexpr bool BATCH = true;   // compile the batched multi-case launch
+    static constexpr bool AA = true;      // compile the AA-pattern (in-place) kernels
     static constexpr bool DEV = false;
     static constexpr bool HAS_G = true, HAS_LAM = false, RR = false;
     __host__ __device__ static constexpr int cx(int q) { return Lat<37>::cx(q); }

@@ -8,6 +8,7 @@ namespace lbm {
 // equilibrium) or WV_TRACE (RR with the trace of Pi equilibrated), see models.cuh
 template <bool RR_, int VAR_ = WV_PLAIN> struct D2Q9M {
     static constexpr int VAR = VAR_;
+    static constexpr bool AA = VAR_ == WV_PLAIN;   // compile the AA-pattern (in-place) kernels
     static constexpr int D = 2, Q = 9;
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = 12, MINB_GEN = 6;

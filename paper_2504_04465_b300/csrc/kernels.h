@@ -14,6 +14,9 @@ struct KernelSet {
     void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
     void (*ledger)(const StepArgs&, long long nblocks, double* partial, double* out, cudaStream_t) = nullptr;
     void (*init)(const StepArgs&, int lev, const double* rho, const double* u, const double* T, cudaStream_t) = nullptr;
+    // AA-pattern streaming (one buffer, single level): one iteration of parity a.rd[0]; null
+    // where the model is not compiled with it
+    void (*aa)(const StepArgs&, cudaStream_t) = nullptr;
     const void* step_kernel = nullptr;
     int block_threads = 0;
     // compiled variants of the step launch (occupancy targets of the simple-block kernel)

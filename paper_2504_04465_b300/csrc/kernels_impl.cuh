@@ -37,6 +37,11 @@ template <class M, class = void> struct weak_var : std::integral_constant<int, 0
 template <class M>
 struct weak_var<M, std::void_t<decltype(M::VAR)>> : std::integral_constant<int, M::VAR> {};
 
+// models compiled with the AA-pattern kernels (M::AA)
+template <class M, class = void> struct aa_capable : std::false_type {};
+template <class M>
+struct aa_capable<M, std::void_t<decltype(M::AA)>> : std::bool_constant<M::AA> {};
+
 enum Mode { MODE_STEP = 0, MODE_READ = 1, MODE_LEDGER = 2 };
 
 // largest |xi_a| of the lattice (its reach)
@@ -204,6 +209,20 @@ __device__ __forceinline__ void assemble(const StepArgs& a, int lev, long long b
     const long long cell = b * BS + l;
     const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
     *conv_out = 1;
+    if (a.aa_l1 && type == C_FLUID) {
+        // AA streaming, layout L1: the cell's own slot qbar holds f_q (bounces already in place)
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) {
+            T gv = T(0);
+            load_pop<M, ST, BX * BY * BZ>(L, rd, cell, M::Q - 1 - q, a.m, c.f[q], gv);
+            if constexpr (M::HAS_G) c.g[q] = gv;
+        }
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) c.lam[i] = L.lam[((long long)rd * 8 + i) * L.ncell + cell];
+        }
+        return;
+    }
     if (type != C_BC) {
         unsigned long long bmask = 0ull, umask = 0ull;
         long long child = -1;
@@ -780,6 +799,152 @@ k_step_batch(const StepArgs* __restrict__ args, const long long* __restrict__ of
     step_block<M, ST, BX, BY, BZ, FAST>(args[lo], bid - off[lo], nbr_s, s_nstat);
 }
 
+// ------------------------------------------------------------------ AA-pattern streaming
+// In-place streaming with one population buffer, on single-level grids.  Two layouts alternate:
+//   L1 (after an even number of iterations): slot (x, qbar) holds the pre-collision f_q(x);
+//   L0 (after an odd number): slot (x, q) holds the post-collision f*_q(x), the layout the
+//       two-buffer path gathers from, so readouts and ledgers read it unchanged.
+// Even iteration (L1 -> L0): a cell reads its own slots reversed and writes its own slots.
+// Odd iteration (L0 -> L1): cell x gathers f_q(x) = slot (x - xi_q, q) and writes f*_p(x) to
+// slot (x + xi_p, pbar), the slot it read for q = pbar: every slot is read and then written by
+// one thread, so no two threads touch a slot.  A blocked link q (solid or wall) reads and writes
+// the cell's own slot qbar, with Ladd's term at moving walls; the bounced value then already sits
+// where the even iteration reads it.
+
+// Boundary-layer cell of an equilibrium Dirichlet face (imposed rho, u, T): its pre-collision
+// state is the equilibrium (the face kinds that read an interior partner are not offered with
+// AA streaming).
+template <class M, int ST>
+__device__ __forceinline__ void bc_equilibrium(const StepArgs& a, const LevelDev& L, long long cell,
+                                               Cell<M, ST>& c, int* conv) {
+    using T = typename Store<ST>::T;
+    const CellRecDev rec = L.recs[L.rec_id[cell]];
+    const FaceDev& fd = a.m.faces[rec.b >> 4];
+    *conv = 1;
+    if constexpr (!M::HAS_G) {
+        if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(T(fd.rho), T(fd.u[0]), T(fd.u[1]), T(a.m.rho_ref), c.f);
+        else weak_feq_dev<M::D, T>(T(fd.rho), T(fd.u[0]), T(fd.u[1]), T(fd.u[2]), T(a.m.rho_ref), c.f);
+    } else {
+        int it = 0;
+        M::template feq<ST>(a.m, T(fd.rho), T(fd.u[0]), T(fd.u[1]), T(fd.T), c.lam, c.f, &it, conv);
+        const T gfac = T((2.0 * a.m.Cv - M::D) * fd.T);
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) c.g[q] = gfac * c.f[q];
+    }
+}
+
+template <class M, int ST, int BX, int BY, int BZ, bool ODD>
+__global__ void __launch_bounds__(BX * BY * BZ, step_min_blocks<M, ST, true, 0>(BX * BY * BZ))
+k_step_aa(const StepArgs a) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    __shared__ int nbr_s[27];
+    __shared__ unsigned nboff_s[27];
+    __shared__ unsigned long long s_nstat[19];
+    const LevelDev& L = a.lv[0];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    if (l < 27) {
+        const int v = L.nbr[b * 27 + l];
+        nbr_s[l] = v;
+        nboff_s[l] = (unsigned)(v < 0 ? L.nb : v) * (unsigned)(M::Q * BS);
+    }
+    if (M::HAS_LAM && l < 19) s_nstat[l] = 0ull;
+    __syncthreads();
+    const long long cell = b * BS + l;
+    const bool simple = L.bflag[b] == 1;
+    const int type = simple ? (int)C_FLUID : (int)L.type[cell];
+    int iters = -1;
+    if (type == C_FLUID || type == C_BC) {
+        const int lx = l % BX, ly = (l / BX) % BY, lz = l / (BX * BY);
+        unsigned long long bmask = 0ull;
+        bool walls = false;
+        if (!simple && type == C_FLUID) {
+            const int r = L.rec_id[cell];
+            if (r >= 0) {
+                const CellRecDev rec = L.recs[r];
+                bmask = rec.mask;
+                walls = (rec.b & 2) != 0;
+            }
+        }
+        Cell<M, ST> c;
+        int conv = 1, conv2 = 1;
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[(long long)j * L.ncell + cell];
+        }
+        if (type == C_BC) {
+            bc_equilibrium<M, ST>(a, L, cell, c, &conv);
+        } else if (ODD && simple) {
+            gather_fast<M, ST, BX, BY, BZ>(L, 0, l, nboff_s, a.m, c);     // every source exists
+        } else {
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) {
+                T gv = T(0);
+                if (!ODD || (bmask >> q & 1ull)) {
+                    load_pop<M, ST, BS>(L, 0, cell, M::Q - 1 - q, a.m, c.f[q], gv);
+                    if constexpr (ODD && !M::HAS_G) {
+                        if (walls) c.f[q] += T(wall_term<M, BX, BY, BZ>(a.m, L, b, l, q));
+                    }
+                } else {
+                    const long long s = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(q), M::cy(q), M::cz(q));
+                    load_pop<M, ST, BS>(L, 0, s, q, a.m, c.f[q], gv);
+                }
+                if constexpr (M::HAS_G) c.g[q] = gv;
+            }
+        }
+        if constexpr (!M::HAS_G && M::DEV) {
+            if (a.m.sponge_on) relax_far_field<M, ST, BX, BY, BZ>(a.m, L, 0, b, l, c);
+        }
+        const int it = collide<M, ST, false>(a.m, L, c, &conv2);
+        if (M::HAS_LAM) iters = it + (conv2 ? 0 : 1000);
+        if (!conv || !conv2) set_status(a.status, -6);
+#pragma unroll
+        for (int p = 0; p < M::Q; ++p) {
+            const T gp = M::HAS_G ? c.g[p] : T(0);
+            if (!ODD) {
+                store_pop<M, ST, BS>(L, 0, cell, p, a.m, c.f[p], gp);
+            } else if (simple) {
+                // slot (x + xi_p, pbar): the source of link pbar, by the packed per-axis offsets
+                const int pb = M::Q - 1 - p;
+                const unsigned P = axis_term<BX, 1, 1>(lx, M::cx(pb)) + axis_term<BY, BX, 3>(ly, M::cy(pb)) +
+                                   axis_term<BZ, BX * BY, 9>(lz, M::cz(pb));
+                const unsigned i = nboff_s[P >> 20] + (unsigned)(pb * BS) + (P & 0xFFFFFu);
+                Store<ST>::template store<M::DEV>(L.f[0], i, c.f[p], inv_ref_f<M, ST>(a.m, pb));
+                if constexpr (M::HAS_G) Store<ST>::template store<false>(L.g[0], i, gp, inv_ref_g<M, ST>(a.m, pb));
+            } else {
+                const int pb = M::Q - 1 - p;
+                if (bmask >> pb & 1ull) {
+                    T v = c.f[p];
+                    if constexpr (!M::HAS_G) {
+                        if (walls) v += T(wall_term<M, BX, BY, BZ>(a.m, L, b, l, pb));
+                    }
+                    store_pop<M, ST, BS>(L, 0, cell, p, a.m, v, gp);
+                } else {
+                    const long long d = src_cell<BX, BY, BZ>(nbr_s, b, lx, ly, lz, M::cx(pb), M::cy(pb), M::cz(pb));
+                    if (d >= 0) store_pop<M, ST, BS>(L, 0, d, pb, a.m, c.f[p], gp);
+                }
+            }
+        }
+        if constexpr (M::HAS_LAM) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) L.lam[(long long)j * L.ncell + cell] = c.lam[j];
+        }
+    }
+    if constexpr (M::HAS_LAM) {
+        if (iters >= 0) {
+            const int nc = iters >= 1000;
+            const int it = iters - 1000 * nc;
+            atomicAdd(&s_nstat[0], (unsigned long long)it);
+            atomicAdd(&s_nstat[1], 1ull);
+            if (nc) atomicAdd(&s_nstat[2], 1ull);
+            atomicAdd(&s_nstat[3 + (it < 15 ? it : 15)], 1ull);
+        }
+        __syncthreads();
+        if (l < 19 && s_nstat[l]) atomicAdd(&a.nstat[l], s_nstat[l]);
+    }
+}
+
 // ------------------------------------------------------------------ readout
 // out (FP64, SoA over the level's slots): which = 0 moments (rho, ux, uy, uz, T),
 // 1 populations f, 2 populations g, 3 lambda
@@ -853,7 +1018,7 @@ __device__ __forceinline__ void ledger_block(const StepArgs& a, long long bid, d
         Cell<M, ST> c;
         int conv;
         // fluid cells of simple and streaming blocks have every source: the branch-free pull
-        if (bf != 0 && type == C_FLUID) gather_fast<M, ST, BX, BY, BZ>(L, a.rd[lev], l, nboff_s, a.m, c);
+        if (bf != 0 && type == C_FLUID && !a.aa_l1) gather_fast<M, ST, BX, BY, BZ>(L, a.rd[lev], l, nboff_s, a.m, c);
         else assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
         const double V = double(1ll << (lev * M::D));
         // per-cell sums in the arithmetic type of the stored values (the deviations f - w rho_ref
@@ -961,7 +1126,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
         if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(rho, ux, uy, T(a.m.rho_ref), feq);
         else weak_feq_dev<M::D, T>(rho, ux, uy, uz, T(a.m.rho_ref), feq);
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, feq[q], T(0));
+        for (int q = 0; q < M::Q; ++q)
+            store_pop<M, ST, BX * BY * BZ>(L, 1, cell, a.aa ? M::Q - 1 - q : q, a.m, feq[q], T(0));
     } else {
         const T Tt = T(T_in[cell]);
         double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -973,7 +1139,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_eq(const StepArgs a, int 
         if (!conv) set_status(a.status, -6);
         const T gfac = T((2.0 * a.m.Cv - M::D) * (double)Tt);
 #pragma unroll
-        for (int q = 0; q < M::Q; ++q) store_pop<M, ST, BX * BY * BZ>(L, 1, cell, q, a.m, feq[q], gfac * feq[q]);
+        for (int q = 0; q < M::Q; ++q)
+            store_pop<M, ST, BX * BY * BZ>(L, 1, cell, a.aa ? M::Q - 1 - q : q, a.m, feq[q], gfac * feq[q]);
         if constexpr (M::HAS_LAM) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -1078,7 +1245,17 @@ struct Launch {
     static void init(const StepArgs& a, int lev, const double* r, const double* u, const double* t, cudaStream_t s) {
         if (!a.lv[lev].nb) return;
         k_init_eq<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb + 1, BX * BY * BZ, 0, s>>>(a, lev, r, u, t);
-        k_init_prestream<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
+        // AA streaming starts in layout L1 (one buffer, each cell's own slots reversed)
+        if (!a.aa) k_init_prestream<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
+    }
+    // one AA iteration of the single level; its parity is a.rd[0] (odd: L0 -> L1)
+    static void aa(const StepArgs& a, cudaStream_t s) {
+        if constexpr (aa_capable<M>::value) {
+            const unsigned nb = (unsigned)a.lv[0].nb;
+            if (!nb) return;
+            if (a.rd[0]) k_step_aa<M, ST, BX, BY, BZ, true><<<nb, BX * BY * BZ, 0, s>>>(a);
+            else k_step_aa<M, ST, BX, BY, BZ, false><<<nb, BX * BY * BZ, 0, s>>>(a);
+        }
     }
 };
 
@@ -1110,6 +1287,7 @@ KernelSet make_set() {
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
     k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;
     k.init = &Launch<M, ST, BX, BY, BZ>::init;
+    if constexpr (aa_capable<M>::value) k.aa = &Launch<M, ST, BX, BY, BZ>::aa;
     k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ, true, 0>;   // for occupancy queries
     k.block_threads = BX * BY * BZ;
     return k;

@@ -65,6 +65,7 @@ _sig = {
     "lbm_set_collision": [_P, C.c_int, C.POINTER(CollisionParams)],
     "lbm_set_precision": [_P, C.c_int],
     "lbm_set_sponge": [_P, _D, C.c_double, C.c_double, C.c_double, C.c_double],
+    "lbm_set_streaming": [_P, C.c_int],
     "lbm_set_boundary": [_P, C.c_int, C.c_int, _D],
     "lbm_set_block": [_P, C.c_int, C.c_int, C.c_int],
     "lbm_build_grid": [_P, C.POINTER(C.c_int64), C.c_int, C.POINTER(Box), C.c_int, C.POINTER(Shape), C.c_int],
@@ -281,6 +282,10 @@ class Context:
                             newton_max_iter, GUESS[guess], rho_ref, int(newton_fp32), int(trace_eq), trt_magic)
         _check(_lib.lbm_set_collision(self._h, MODEL[model], C.byref(p)), "lbm_set_collision")
 
+    def set_streaming(self, mode: str) -> None:
+        """'ab' (two buffers, the default) or 'aa' (one buffer updated in place); before the build."""
+        _check(_lib.lbm_set_streaming(self._h, {"ab": 0, "aa": 1}[mode]), "lbm_set_streaming")
+
     def set_sponge(self, centre, r0: float, r1: float, sigma_max: float, rho_inf: float = 1.0) -> None:
         """Far-field relaxation (Eq. relaxation_pressure), finest units; sigma_max = 0 switches it off."""
         c = np.zeros(3)
@@ -347,6 +352,9 @@ class Context:
         """Apply a grid specification (see paper_2504_04465_b300.inputs.GridSpec) and build."""
         self.set_lattice(lattice)
         sponge = coll.pop("sponge", None)
+        streaming = coll.pop("streaming", None)
+        if streaming is not None:
+            self.set_streaming(streaming)
         self.set_collision(model, **coll)
         if sponge is not None:
             self.set_sponge(sponge["centre"], sponge["r0"], sponge["r1"], sponge["sigma_max"], sponge["rho_inf"])

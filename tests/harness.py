@@ -36,7 +36,8 @@ def make_gpu(spec, latname, model, storage, fields_fn, block=None, **params):
     from paper_2504_04465_b300 import lbmtree as lt
     lat = L.LATTICES[latname]
     ctx = lt.Context(spec.dim, device=0)
-    coll = {k: v for k, v in params.items() if k in ORACLE_PARAMS + ("newton_fp32", "newton_max_iter") and v is not None}
+    coll = {k: v for k, v in params.items()
+            if k in ORACLE_PARAMS + ("newton_fp32", "newton_max_iter", "streaming") and v is not None}
     ctx.configure(spec, latname, model, storage, block=block, **coll)
     lv, xyz, ty = ctx.cells()
     n = lv.size

@@ -255,3 +255,24 @@ def test_wall_arguments(lt):
         c2.configure(I.GridSpec(2, (128, 32), 1, [], (False, True),
                                 {"x-": ("wall", 1.0, (0.0, 0.1, 0.0)), "x+": ("wall",)}), "D2Q37", "poly_ddf")
     assert e.value.code == -10
+
+
+def test_aa_streaming_arguments(lt):
+    from tests.test_gpu_aa import CASES
+    for name, spec, latname, model, _, kw in CASES:           # every AA case builds
+        c = lt.Context(spec.dim, device=-1)
+        c.configure(spec, latname, model, "f32", streaming="aa", **{k: v for k, v in kw.items()})
+    bad = [
+        (I.taylor_green_spec(64, 16, 48, 2), "D2Q9", "rr", "f64"),                      # two levels
+        (I.sod_spec(256, 32), "D2Q37", "poly_ddf", "f64"),                              # Neumann faces
+        (I.GridSpec(2, (64, 64), 1, [], (True, True)), "D2Q21", "num_ddf", "f64"),     # not compiled
+        (I.GridSpec(2, (64, 64), 1, [], (True, True)), "D2Q9", "trt", "f64"),          # not compiled
+    ]
+    for spec, latname, model, st in bad:
+        c = lt.Context(2, device=-1)
+        with pytest.raises(lt.LbmError) as e:
+            c.configure(spec, latname, model, st, streaming="aa", nu0=0.02)
+        assert e.value.code == -10, (latname, model)
+    c = lt.Context(2, device=-1)
+    with pytest.raises(lt.LbmError):
+        lt._check(lt._lib.lbm_set_streaming(c._h, 7), "lbm_set_streaming")    # unknown mode
