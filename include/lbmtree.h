@@ -226,6 +226,15 @@ int lbm_set_variant(lbm_ctx* ctx, int variant);
  * a ghost or boundary layer). */
 int lbm_build_grid(lbm_ctx* ctx, const int64_t extent[3], int n_levels,
                    const lbm_box* boxes, int n_boxes, const lbm_shape* solids, int n_solids);
+/* The same from a level map instead of boxes (the mesh density field of Sec. 8): level_map holds,
+ * for every finest-level cell (x fastest, extent[0] * extent[1] (* extent[2]) bytes, copied),
+ * the finest level wanted there, 0 (finest) to n_levels - 1.  The region of level i is every
+ * level-(i+1) cell that holds a finest cell wanting level i or finer, so the regions are nested
+ * and aligned by construction.  The map must leave room for the ghost layers (about four lattice
+ * reaches of level-i cells between the borders of regions i - 1 and i; lbm_amr_level_map
+ * grades a map so); otherwise LBM_ERR_GRID as for boxes. */
+int lbm_build_grid_map(lbm_ctx* ctx, const int64_t extent[3], int n_levels, const uint8_t* level_map,
+                       const lbm_shape* solids, int n_solids);
 /* Library-owned host view of the cells (levels ascending, then Morton order of blocks, then
  * x-fastest inside a block).  xyz is n_cells x 3 (z = 0 in 2D).  Valid until lbm_destroy(). */
 int lbm_cells(lbm_ctx* ctx, int64_t* n_cells, const int32_t** level, const int32_t** xyz,
@@ -233,6 +242,27 @@ int lbm_cells(lbm_ctx* ctx, int64_t* n_cells, const int32_t** level, const int32
 /* Velocities of the lattice: xi[Q*3] (library-owned), in the population order of the
  * readout calls. */
 int lbm_velocities(lbm_ctx* ctx, int* Q, const int32_t** xi);
+
+/* ---------------------------------------------------------------- adaptive mesh refinement (Sec. 8) */
+/* Grade a level map in place so that it can be built: for i = 0 .. n_levels - 2, every
+ * level-(i+1) cell within 3 reach + 1 level-(i+1) cells (Chebyshev, wrapping where periodic[d])
+ * of one holding a finest cell that wants level i or finer gets level i + 1 or finer.  Host only. */
+int lbm_grade_level_map(int dim, const int64_t extent[3], int n_levels, int lattice, const int periodic[3],
+                        uint8_t* level_map);
+/* Level map from the kinetic sensor (Eq. DeltaAvg of the pre-collision state, the criterion of
+ * Sec. 8's supersonic airfoil): every finest cell under a bulk or boundary cell whose eps exceeds
+ * `threshold` wants level 0; elsewhere fixed_map (NULL: the coarsest level); then graded as
+ * above.  level_map: caller-owned, one byte per finest cell, x fastest.  Synchronises. */
+int lbm_amr_level_map(lbm_ctx* ctx, double threshold, const uint8_t* fixed_map, uint8_t* level_map);
+/* Rebuild the grid from a level map and carry the state over (Sec. 8): a new cell takes the old
+ * conserved state at the same level and place (coarse ghosts with their unknown populations
+ * coalesced, a fine ghost standing for its coarse-ghost parent), else the old coarser cell
+ * holding it (uniform explosion), else the mean of its children resolved the same way
+ * (coalescence); f, g and the multipliers alike.  The new state is pre-collision at a coarse
+ * synchronisation instant and the level schedule restarts there.  Needs the context at such an
+ * instant (LBM_ERR_STATE), two-buffer streaming (LBM_ERR_UNSUPPORTED) and a map the builder
+ * accepts (LBM_ERR_GRID: the context is then left without a grid). */
+int lbm_remesh(lbm_ctx* ctx, const uint8_t* level_map);
 
 /* ---------------------------------------------------------------- fields */
 /* Initialise every cell at equilibrium (Appendix A.3) from host arrays in lbm_cells() order:

@@ -120,10 +120,32 @@ def _shift(mask: np.ndarray, off, periodic) -> np.ndarray:
     return res
 
 
+def _block_min(a: np.ndarray, f: int) -> np.ndarray:
+    """Minimum over blocks of f cells per axis."""
+    for ax in range(a.ndim):
+        sh = list(a.shape)
+        sh[ax:ax + 1] = [sh[ax] // f, f]
+        a = a.reshape(sh).min(axis=ax + 1)
+    return a
+
+
 def _region_mask(spec, level: int, shape) -> np.ndarray:
-    """Region_level at level resolution (union of that level's boxes)."""
+    """Region_level at level resolution: the union of that level's boxes, or, from a level map
+    (the finest level wanted at each finest cell, Sec. 8's mesh density field), every cell whose
+    parent holds a finest cell wanting this level or finer (aligned to parents by construction)."""
     if level >= spec.n_levels - 1:
         return np.ones(shape, dtype=bool)
+    lmap = getattr(spec, "level_map", None)
+    if lmap is not None:
+        if spec.boxes:
+            raise GridError("give refinement boxes or a level map, not both")
+        lmap = np.asarray(lmap)
+        if lmap.shape != tuple(spec.extent) or lmap.max() >= spec.n_levels or lmap.min() < 0:
+            raise GridError("level map of the wrong shape or with entries beyond the coarsest level")
+        parent = _block_min(lmap, 2 ** (level + 1)) <= level
+        for ax in range(parent.ndim):
+            parent = np.repeat(parent, 2, axis=ax)
+        return parent
     m = np.zeros(shape, dtype=bool)
     s = 2 ** level
     for (lv, lo, hi) in spec.boxes:

@@ -108,6 +108,7 @@ struct lbm_ctx {
     std::vector<void*> allocs;
     int64_t dev_bytes = 0;
     int64_t t = 0;
+    int64_t t_offset = 0;           // fine iterations done before the last remesh
     bool initialized = false;
     int64_t launches = 0;
     bool use_graph = false;
@@ -158,6 +159,11 @@ struct lbm_ctx {
     int cur(int i, int64_t tt) const { return int(((tt + (int64_t(1) << i) - 1) >> i) & 1); }
     bool comp() const { return model == LBM_COMP_POLY || model == LBM_COMP_NUMERICAL; }
     int streaming = LBM_STREAM_AB;   // lbm_set_streaming
+    std::vector<uint8_t> pending_map;  // level map of the next build (lbm_build_grid_map)
+    // what the grid was built from (the remesh rebuilds it with another level map)
+    int64_t extent[3] = {1, 1, 1};
+    int n_levels_built = 1;
+    std::vector<ShapeSpec> solids_built;
     bool weak() const { return model == LBM_BGK || model == LBM_RR || model == LBM_TRT; }
     // kernel-set code of the collision: the public model, with the trace-equilibrated RR as 6
     int kmodel() const { return (model == LBM_RR && params.trace_eq) ? KMODEL_RR_TRACE : model; }
@@ -689,6 +695,11 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     for (int f = 0; f < 6; ++f) in.faces[f] = c->faces[f];
     for (int d = 0; d < 3; ++d) in.block[d] = c->block[d];
     in.lattice = c->lattice;
+    in.level_map = std::move(c->pending_map);
+    c->pending_map.clear();
+    for (int d = 0; d < 3; ++d) c->extent[d] = extent[d];
+    c->n_levels_built = n_levels;
+    c->solids_built = in.solids;
     std::string err;
     try {
         err = build_grid(in, c->grid);
@@ -806,6 +817,260 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
     return LBM_OK;
 }
 
+namespace {
+
+// cell (type, slot) of a built grid at level i and level coordinates c (periodic axes wrap)
+uint8_t grid_cell(const BuiltGrid& g, int i, const int64_t* c, int64_t* slot) {
+    const BuiltLevel& lv = g.levels[i];
+    int64_t w[3] = {c[0], c[1], c[2]};
+    for (int d = 0; d < g.dim; ++d) {
+        if (w[d] < 0 || w[d] >= lv.shape[d]) {
+            if (!g.periodic[d]) return C_ABSENT;
+            w[d] = ((w[d] % lv.shape[d]) + lv.shape[d]) % lv.shape[d];
+        }
+    }
+    int64_t bc[3], l[3];
+    for (int d = 0; d < 3; ++d) { bc[d] = w[d] / g.block[d]; l[d] = w[d] % g.block[d]; }
+    const int32_t b = lv.bindex[(bc[2] * lv.bgrid[1] + bc[1]) * lv.bgrid[0] + bc[0]];
+    if (b < 0) return C_ABSENT;
+    *slot = int64_t(b) * g.BS + (l[2] * g.block[1] + l[1]) * g.block[0] + l[0];
+    return lv.type[*slot];
+}
+
+// Sources of the remesh transfer (Sec. 8): a new cell takes the old conserved state at the same
+// level and place (coarse ghosts with their unknowns coalesced; a fine ghost stands for its
+// coarse-ghost parent), else the old coarser cell holding it (uniform explosion), else the mean
+// of its children resolved the same way (coalescence).  Entries (old level << 40 | slot, weight).
+bool transfer_sources(const BuiltGrid& old, int i, const int64_t* c, double w,
+                      std::vector<std::pair<long long, double>>& out) {
+    int64_t s;
+    const uint8_t t = grid_cell(old, i, c, &s);
+    if (t == C_FLUID || t == C_BC || t == C_CGHOST) {
+        out.push_back({((long long)i << 40) | s, w});
+        return true;
+    }
+    if (t == C_SOLID) return true;                          // no fluid state there
+    if (t == C_FGHOST) {
+        const int64_t p[3] = {c[0] >> 1, old.dim > 1 ? c[1] >> 1 : c[1], old.dim > 2 ? c[2] >> 1 : c[2]};
+        if (grid_cell(old, i + 1, p, &s) != C_CGHOST) return false;
+        out.push_back({((long long)(i + 1) << 40) | s, w});
+        return true;
+    }
+    bool finer = false;                                      // covered by an old finer level?
+    for (int j = 0; j < i && !finer; ++j) {
+        const int sh = i - j;
+        const int64_t cj[3] = {c[0] << sh, old.dim > 1 ? c[1] << sh : c[1], old.dim > 2 ? c[2] << sh : c[2]};
+        int64_t s2;
+        finer = grid_cell(old, j, cj, &s2) != C_ABSENT;
+    }
+    if (finer) {
+        const int64_t ch[3] = {2 * c[0], old.dim > 1 ? 2 * c[1] : c[1], old.dim > 2 ? 2 * c[2] : c[2]};
+        {
+            const int nk = 1 << old.dim;
+            for (int k = 0; k < nk; ++k) {
+                const int64_t cc[3] = {ch[0] + (k & 1), ch[1] + ((k >> 1) & 1), ch[2] + ((k >> 2) & 1)};
+                if (!transfer_sources(old, i - 1, cc, w / nk, out)) return false;
+            }
+            return true;
+        }
+    }
+    for (int j = i + 1; j < old.n_levels; ++j) {             // an old coarser cell holds it
+        const int sh = j - i;
+        const int64_t p[3] = {c[0] >> sh, old.dim > 1 ? c[1] >> sh : c[1], old.dim > 2 ? c[2] >> sh : c[2]};
+        const uint8_t tj = grid_cell(old, j, p, &s);
+        if (tj == C_ABSENT) continue;
+        if (tj == C_FLUID || tj == C_BC || tj == C_CGHOST) {
+            out.push_back({((long long)j << 40) | s, w});
+            return true;
+        }
+        return transfer_sources(old, j, p, w, out);
+    }
+    return false;
+}
+
+}  // namespace
+
+int lbm_build_grid_map(lbm_ctx* c, const int64_t extent[3], int n_levels, const uint8_t* level_map,
+                       const lbm_shape* solids, int n_solids) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!extent || !level_map) return fail(LBM_ERR_ARG, "null array");
+    if (c->built) return fail(LBM_ERR_STATE, "grid already built");
+    int64_t n0 = 1;
+    for (int d = 0; d < c->dim; ++d) {
+        if (extent[d] <= 0) return fail(LBM_ERR_ARG, "non-positive extent");
+        n0 *= extent[d];
+    }
+    c->pending_map.assign(level_map, level_map + n0);
+    return lbm_build_grid(c, extent, n_levels, nullptr, 0, solids, n_solids);
+}
+
+int lbm_grade_level_map(int dim, const int64_t extent[3], int n_levels, int lattice, const int periodic[3],
+                        uint8_t* level_map) {
+    if ((dim != 2 && dim != 3) || !extent || !periodic || !level_map) return fail(LBM_ERR_ARG, "bad arguments");
+    if (n_levels < 1 || n_levels > MAX_LEVELS) return fail(LBM_ERR_ARG, "n_levels out of range");
+    int Q = 0, D = 0, R = 0;
+    double cs2 = 0;
+    if (lbm_lattice_info(lattice, &Q, &D, &R, &cs2) != LBM_OK || D != dim) return fail(LBM_ERR_ARG, "unknown lattice");
+    for (int d = 0; d < dim; ++d)
+        if (extent[d] <= 0 || extent[d] % (int64_t(1) << (n_levels - 1))) return fail(LBM_ERR_ARG, "extent not divisible by 2^(n_levels-1)");
+    bool per[3] = {periodic[0] != 0, periodic[1] != 0, periodic[2] != 0};
+    grade_level_map(dim, extent, n_levels, 3 * R + 1, per, level_map);
+    return LBM_OK;
+}
+
+int lbm_amr_level_map(lbm_ctx* c, double threshold, const uint8_t* fixed_map, uint8_t* level_map) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!level_map) return fail(LBM_ERR_ARG, "null output");
+    if (int r = ready(c)) return r;
+    const int L = c->L();
+    const int64_t* e = c->extent;
+    const int64_t n0 = e[0] * (c->dim > 1 ? e[1] : 1) * (c->dim > 2 ? e[2] : 1);
+    for (int64_t k = 0; k < n0; ++k) level_map[k] = fixed_map ? std::min<uint8_t>(fixed_map[k], (uint8_t)(L - 1)) : (uint8_t)(L - 1);
+    // kinetic sensor of every cell (pre-collision state), level by level
+    StepArgs a;
+    current_args(c, a);
+    size_t need = 0;
+    for (int i = 0; i < L; ++i) need = std::max(need, size_t(c->grid.levels[i].nb) * c->grid.BS * sizeof(double));
+    double* d = nullptr;
+    if (cudaMalloc(&d, need ? need : 8) != cudaSuccess) return fail(LBM_ERR_OOM, "sensor buffer");
+    std::vector<double> eps;
+    int status = LBM_OK;
+    for (int i = 0; i < L && status == LBM_OK; ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        const int64_t ncell = lv.nb * c->grid.BS;
+        if (!ncell) continue;
+        c->ks.read(a, i, 7, d, c->stream);
+        eps.resize(ncell);
+        if (cudaMemcpyAsync(eps.data(), d, ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            status = fail(LBM_ERR_CUDA, "sensor readout");
+            break;
+        }
+        const int64_t f = int64_t(1) << i;
+        for (int64_t slot = 0; slot < ncell; ++slot) {
+            const uint8_t t = lv.type[slot];
+            if (!(t == C_FLUID || t == C_BC) || !(eps[slot] > threshold)) continue;
+            const int64_t b = slot / c->grid.BS, l = slot % c->grid.BS;
+            const int64_t x = lv.bxyz[3 * b] * c->block[0] + l % c->block[0];
+            const int64_t y = lv.bxyz[3 * b + 1] * c->block[1] + (l / c->block[0]) % c->block[1];
+            const int64_t z = lv.bxyz[3 * b + 2] * c->block[2] + l / (c->block[0] * c->block[1]);
+            // every finest cell under a flagged cell wants the finest level
+            for (int64_t zz = (c->dim > 2 ? z * f : 0); zz < (c->dim > 2 ? (z + 1) * f : 1); ++zz)
+                for (int64_t yy = y * f; yy < (y + 1) * f; ++yy)
+                    for (int64_t xx = x * f; xx < (x + 1) * f; ++xx) level_map[(zz * e[1] + yy) * e[0] + xx] = 0;
+        }
+    }
+    cudaFree(d);
+    if (status != LBM_OK) return status;
+    bool per[3] = {c->grid.periodic[0], c->grid.periodic[1], c->grid.periodic[2]};
+    grade_level_map(c->dim, e, L, 3 * c->grid.lat.R + 1, per, level_map);
+    return LBM_OK;
+}
+
+int lbm_remesh(lbm_ctx* c, const uint8_t* level_map) {
+    if (check_ctx(c)) return LBM_ERR_ARG;
+    if (!level_map) return fail(LBM_ERR_ARG, "null level map");
+    if (int r = ready(c)) return r;
+    if (c->streaming != LBM_STREAM_AB) return fail(LBM_ERR_UNSUPPORTED, "remesh needs two-buffer streaming");
+    if (c->t % c->period()) return fail(LBM_ERR_STATE, "not at a coarse synchronisation instant");
+    if (int r = lbm_sync(c)) return r;
+    const int Q = c->grid.lat.Q;
+    const bool has_g = c->comp(), has_lam = c->model == LBM_COMP_NUMERICAL;
+    const int ncomp = Q + (has_g ? Q : 0) + (has_lam ? 8 : 0);
+    const int Lold = c->L();
+    // 1. the old conserved state, per level, slot-indexed: f, g, lambda
+    StepArgs a;
+    current_args(c, a);
+    TransferSrc src{};
+    std::vector<double*> olds(Lold, nullptr);
+    auto free_olds = [&]() { for (double* p : olds) if (p) cudaFree(p); };
+    for (int i = 0; i < Lold; ++i) {
+        const int64_t ncell = c->grid.levels[i].nb * c->grid.BS;
+        if (cudaMalloc(&olds[i], size_t(ncomp) * std::max<int64_t>(ncell, 1) * 8) != cudaSuccess) {
+            free_olds();
+            return fail(LBM_ERR_OOM, "remesh staging");
+        }
+        if (ncell) {
+            c->ks.read(a, i, 4, olds[i], c->stream);
+            if (has_g) c->ks.read(a, i, 5, olds[i] + size_t(Q) * ncell, c->stream);
+            if (has_lam) c->ks.read(a, i, 6, olds[i] + size_t(Q + (has_g ? Q : 0)) * ncell, c->stream);
+        }
+        src.ptr[i] = olds[i];
+        src.ncell[i] = ncell;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_olds(); return fail(LBM_ERR_CUDA, "remesh readout"); }
+    // 2. the new grid, from the same settings and solids
+    BuiltGrid old = std::move(c->grid);
+    const int64_t fine_it = c->t + c->t_offset, launches = c->launches;
+    c->release();
+    c->built = false;
+    c->initialized = false;
+    std::vector<lbm_shape> sh(c->solids_built.size());
+    for (size_t k = 0; k < sh.size(); ++k) {
+        sh[k].kind = c->solids_built[k].kind;
+        std::memcpy(sh[k].p, c->solids_built[k].p, sizeof(sh[k].p));
+    }
+    int64_t ext[3] = {c->extent[0], c->extent[1], c->extent[2]};
+    if (int r = lbm_build_grid_map(c, ext, c->n_levels_built, level_map, sh.empty() ? nullptr : sh.data(), (int)sh.size())) {
+        free_olds();
+        return r;                  // the context is left unbuilt; the message says why
+    }
+    // 3. transfer rows per new level, then the state into the new buffers
+    StepArgs na;
+    fill_args(c, na);
+    int status = LBM_OK;
+    for (int i = 0; i < c->L() && status == LBM_OK; ++i) {
+        const BuiltLevel& lv = c->grid.levels[i];
+        const int64_t rows = lv.nb * c->grid.BS;
+        if (!rows) continue;
+        std::vector<long long> rowptr(rows + 1, 0), col;
+        std::vector<double> w;
+        std::vector<std::pair<long long, double>> ent;
+        for (int64_t slot = 0; slot < rows && status == LBM_OK; ++slot) {
+            const uint8_t t = lv.type[slot];
+            if (t != C_ABSENT && t != C_SOLID) {
+                const int64_t b = slot / c->grid.BS, l = slot % c->grid.BS;
+                const int64_t cc[3] = {lv.bxyz[3 * b] * c->block[0] + l % c->block[0],
+                                       lv.bxyz[3 * b + 1] * c->block[1] + (l / c->block[0]) % c->block[1],
+                                       lv.bxyz[3 * b + 2] * c->block[2] + l / (c->block[0] * c->block[1])};
+                ent.clear();
+                if (!transfer_sources(old, i, cc, 1.0, ent)) status = fail(LBM_ERR_GRID, "remesh: a new cell has no old state");
+                for (auto& e : ent) { col.push_back(e.first); w.push_back(e.second); }
+            }
+            rowptr[slot + 1] = (long long)col.size();
+        }
+        if (status != LBM_OK) break;
+        long long *d_row = nullptr, *d_col = nullptr;
+        double *d_w = nullptr, *d_new = nullptr;
+        const size_t ncol = std::max<size_t>(col.size(), 1);
+        if (cudaMalloc(&d_row, rowptr.size() * 8) != cudaSuccess || cudaMalloc(&d_col, ncol * 8) != cudaSuccess ||
+            cudaMalloc(&d_w, ncol * 8) != cudaSuccess || cudaMalloc(&d_new, size_t(ncomp) * rows * 8) != cudaSuccess) {
+            status = fail(LBM_ERR_OOM, "remesh transfer");
+        } else {
+            cudaMemcpy(d_row, rowptr.data(), rowptr.size() * 8, cudaMemcpyHostToDevice);
+            if (!col.empty()) {
+                cudaMemcpy(d_col, col.data(), col.size() * 8, cudaMemcpyHostToDevice);
+                cudaMemcpy(d_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice);
+            }
+            launch_transfer(d_row, d_col, d_w, rows, src, ncomp, d_new, c->stream);
+            c->ks.load_state(na, i, d_new, c->stream);
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+                status = fail(LBM_ERR_CUDA, "remesh transfer kernels");
+        }
+        cudaFree(d_row); cudaFree(d_col); cudaFree(d_w); cudaFree(d_new);
+    }
+    free_olds();
+    if (status != LBM_OK) return status;
+    for (int i = 1; i < c->L(); ++i) c->ks.remesh_corners(na, i, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return fail(LBM_ERR_CUDA, "remesh corner kernels");
+    c->t = 0;
+    c->t_offset = fine_it;        // the schedule restarts; the counter of the stats goes on
+    c->launches = launches;
+    c->initialized = true;
+    return LBM_OK;
+}
+
 int lbm_cells(lbm_ctx* c, int64_t* n, const int32_t** level, const int32_t** xyz, const uint8_t** type) {
     if (check_ctx(c)) return LBM_ERR_ARG;
     if (!c->built) return fail(LBM_ERR_STATE, "grid not built");
@@ -886,6 +1151,7 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double
     CU(cudaMemset(c->d_status, 0, sizeof(int)));
     CU(cudaMemset(c->d_nstat, 0, 19 * sizeof(unsigned long long)));
     c->t = 0;
+    c->t_offset = 0;
     c->launches = 0;
     c->initialized = true;
     if (st) return fail(st, "initialisation: a Newton solve did not converge");
@@ -1292,7 +1558,7 @@ int lbm_stats(lbm_ctx* c, lbm_stats_t* s) {
         s->cell_updates += live << (c->L() - 1 - i);
     }
     s->n_eq = c->grid.n_eq;
-    s->fine_iterations = c->t;
+    s->fine_iterations = c->t + c->t_offset;
     s->kernel_launches = c->launches;
     s->device_bytes = c->dev_bytes;
     if (!c->host_only && c->d_nstat) {

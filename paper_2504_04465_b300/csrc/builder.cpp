@@ -45,14 +45,22 @@ struct Geo {
         }
         return true;
     }
+    // regions as dense per-level masks (from a level map), else from the boxes
+    std::vector<std::vector<uint8_t>> rmask;
+    int64_t lidx(int i, const int64_t* c) const { return (c[2] * shape[i][1] + c[1]) * shape[i][0] + c[0]; }
     bool in_region(int i, const int64_t* c) const {
         if (i >= L - 1) return true;
+        if (!rmask.empty()) return rmask[i][lidx(i, c)] != 0;
         for (auto& b : in.boxes)
             if (b.level == i && in_box(b, i, c)) return true;
         return false;
     }
     bool finer(int i, const int64_t* c) const {
         if (i == 0) return false;
+        if (!rmask.empty()) {
+            const int64_t ch[3] = {2 * c[0], D > 1 ? 2 * c[1] : c[1], D > 2 ? 2 * c[2] : c[2]};
+            return rmask[i - 1][lidx(i - 1, ch)] != 0;
+        }
         for (auto& b : in.boxes)
             if (b.level == i - 1 && in_box(b, i, c)) return true;
         return false;
@@ -237,6 +245,43 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
     }
     for (auto& s : in.solids)
         if (s.kind != 1 && s.kind != 2) return "unknown solid kind";
+    if (!in.level_map.empty()) {
+        if (!in.boxes.empty()) return "give refinement boxes or a level map, not both";
+        int64_t n0 = g.shape[0][0] * g.shape[0][1] * g.shape[0][2];
+        if ((int64_t)in.level_map.size() != n0) return "level map size differs from the finest extent";
+        // min over the finest cells under each level-j cell, then region_i = cells whose parent
+        // holds a finest cell wanting level i or finer (aligned to parents by construction)
+        std::vector<uint8_t> minmap = in.level_map;
+        for (auto v : minmap)
+            if (v >= g.L) return "level map entry beyond the coarsest level";
+        std::vector<std::vector<uint8_t>> mins(g.L);
+        mins[0] = minmap;
+        for (int j = 1; j < g.L; ++j) {
+            const int64_t* sj = g.shape[j];
+            std::vector<uint8_t> m(sj[0] * sj[1] * sj[2], 255);
+            const int64_t* sp = g.shape[j - 1];
+            for (int64_t z = 0; z < sp[2]; ++z)
+                for (int64_t y = 0; y < sp[1]; ++y)
+                    for (int64_t x = 0; x < sp[0]; ++x) {
+                        const int64_t pz = g.D > 2 ? z >> 1 : z, py = y >> 1, px = x >> 1;
+                        uint8_t& t = m[(pz * sj[1] + py) * sj[0] + px];
+                        t = std::min(t, mins[j - 1][(z * sp[1] + y) * sp[0] + x]);
+                    }
+            mins[j] = std::move(m);
+        }
+        g.rmask.resize(g.L - 1);
+        for (int i = 0; i + 1 < g.L; ++i) {
+            const int64_t* si = g.shape[i];
+            const int64_t* sp = g.shape[i + 1];
+            g.rmask[i].assign(si[0] * si[1] * si[2], 0);
+            for (int64_t z = 0; z < si[2]; ++z)
+                for (int64_t y = 0; y < si[1]; ++y)
+                    for (int64_t x = 0; x < si[0]; ++x) {
+                        const int64_t pz = g.D > 2 ? z >> 1 : z;
+                        g.rmask[i][(z * si[1] + y) * si[0] + x] = mins[i + 1][(pz * sp[1] + (y >> 1)) * sp[0] + (x >> 1)] <= i;
+                    }
+        }
+    }
 
     out = BuiltGrid{};
     out.dim = g.D; out.n_levels = g.L; out.lat = g.lat;
@@ -258,6 +303,12 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
         std::vector<uint8_t> mark(nbg, 0);
         if (i == g.L - 1) {
             std::fill(mark.begin(), mark.end(), 1);
+        } else if (!g.rmask.empty()) {
+            for (int64_t z = 0; z < lv.shape[2]; ++z)
+                for (int64_t y = 0; y < lv.shape[1]; ++y)
+                    for (int64_t x = 0; x < lv.shape[0]; ++x)
+                        if (g.rmask[i][(z * lv.shape[1] + y) * lv.shape[0] + x])
+                            mark[((z / g.B[2]) * lv.bgrid[1] + y / g.B[1]) * lv.bgrid[0] + x / g.B[0]] = 1;
         } else {
             for (auto& b : in.boxes) {
                 if (b.level != i) continue;
@@ -295,7 +346,15 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                 if (e0[d] < 0 || e1[d] > lv.shape[d]) pl = false;
             }
             for (int d = g.D; d < 3; ++d) { e0[d] = 0; e1[d] = 1; }
-            if (pl && i < g.L - 1) {
+            if (pl && !g.rmask.empty()) {
+                // every cell of the expanded block in region i and none covered by region i-1
+                for (int64_t z = e0[2]; z < e1[2] && pl; ++z)
+                    for (int64_t y = e0[1]; y < e1[1] && pl; ++y)
+                        for (int64_t x = e0[0]; x < e1[0] && pl; ++x) {
+                            const int64_t cc[3] = {x, y, z};
+                            if (!g.in_region(i, cc) || g.finer(i, cc)) pl = false;
+                        }
+            } else if (pl && i < g.L - 1) {
                 bool inside = false;
                 for (auto& b : in.boxes) {
                     if (b.level != i) continue;
@@ -305,7 +364,7 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                 }
                 pl = inside;
             }
-            if (pl && i >= 1) {
+            if (pl && i >= 1 && g.rmask.empty()) {
                 for (auto& b : in.boxes) {
                     if (b.level != i - 1) continue;
                     bool overlap = true;
@@ -560,6 +619,49 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                     double(int64_t(1) << i);
     }
     return std::string();
+}
+
+void grade_level_map(int dim, const int64_t* extent, int n_levels, int width, const bool* periodic, uint8_t* map) {
+    int64_t e[3] = {1, 1, 1};
+    for (int d = 0; d < dim; ++d) e[d] = extent[d];
+    for (int i = 0; i + 1 < n_levels; ++i) {
+        const int64_t f = int64_t(1) << (i + 1);          // finest cells per level-(i+1) cell
+        int64_t s[3] = {1, 1, 1};
+        for (int d = 0; d < dim; ++d) s[d] = e[d] / f;
+        // footprint of region i at level-(i+1) resolution
+        std::vector<uint8_t> foot(s[0] * s[1] * s[2], 0);
+        for (int64_t z = 0; z < e[2]; ++z)
+            for (int64_t y = 0; y < e[1]; ++y)
+                for (int64_t x = 0; x < e[0]; ++x)
+                    if (map[(z * e[1] + y) * e[0] + x] <= i)
+                        foot[((dim > 2 ? z / f : 0) * s[1] + y / f) * s[0] + x / f] = 1;
+        // Chebyshev dilation by `width`, one axis at a time
+        for (int d = 0; d < dim; ++d) {
+            std::vector<uint8_t> nxt(foot.size(), 0);
+            for (int64_t z = 0; z < s[2]; ++z)
+                for (int64_t y = 0; y < s[1]; ++y)
+                    for (int64_t x = 0; x < s[0]; ++x) {
+                        if (!foot[(z * s[1] + y) * s[0] + x]) continue;
+                        int64_t c[3] = {x, y, z};
+                        for (int64_t o = -width; o <= width; ++o) {
+                            int64_t t[3] = {c[0], c[1], c[2]};
+                            t[d] += o;
+                            if (t[d] < 0 || t[d] >= s[d]) {
+                                if (!periodic[d]) continue;
+                                t[d] = ((t[d] % s[d]) + s[d]) % s[d];
+                            }
+                            nxt[(t[2] * s[1] + t[1]) * s[0] + t[0]] = 1;
+                        }
+                    }
+            foot.swap(nxt);
+        }
+        for (int64_t z = 0; z < e[2]; ++z)
+            for (int64_t y = 0; y < e[1]; ++y)
+                for (int64_t x = 0; x < e[0]; ++x) {
+                    uint8_t& v = map[(z * e[1] + y) * e[0] + x];
+                    if (foot[((dim > 2 ? z / f : 0) * s[1] + y / f) * s[0] + x / f] && v > i + 1) v = (uint8_t)(i + 1);
+                }
+    }
 }
 
 }  // namespace lbm

@@ -47,6 +47,10 @@ struct GridInput {
     int64_t extent[3] = {1, 1, 1};
     int n_levels = 1;
     std::vector<BoxSpec> boxes;
+    // alternative to boxes: the finest level wanted at every finest-level cell (x fastest, 0 =
+    // finest, n_levels - 1 = coarsest); the region of level i is then every level-(i+1) cell
+    // holding a finest cell that wants level i or finer
+    std::vector<uint8_t> level_map;
     std::vector<ShapeSpec> solids;
     FaceSpec faces[6];
     int block[3] = {16, 16, 1};
@@ -81,5 +85,11 @@ struct BuiltGrid {
 
 // Returns an empty string on success, else a message (the grid is then unusable).
 std::string build_grid(const GridInput& in, BuiltGrid& out);
+
+// Grade a level map in place (finest resolution, x fastest): for i = 0 .. n_levels - 2, every
+// level-(i+1) cell within `width` level-(i+1) cells (Chebyshev, wrapping across periodic axes) of
+// a level-(i+1) cell holding a finest cell that wants level i or finer gets level i + 1 or finer,
+// so that the ghost layers of consecutive interfaces keep apart (width = 3 reach + 1).
+void grade_level_map(int dim, const int64_t* extent, int n_levels, int width, const bool* periodic, uint8_t* map);
 
 }  // namespace lbm

@@ -11,7 +11,13 @@ struct KernelSet {
     // interior-kernel launch on s_fast, general-kernel launch on s_gen (they touch disjoint cells
     // and may run concurrently)
     void (*step)(const StepArgs&, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) = nullptr;
+    // which: 0 moments, 1 f, 2 g, 3 lambda, 4..6 the same three with coarse-ghost unknowns
+    // coalesced (the conserved state), 7 the kinetic sensor eps
     void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
+    // full-value pre-collision state (f, g, lambda; slot-indexed) into a level's buffers
+    void (*load_state)(const StepArgs&, int lev, const double* full, cudaStream_t) = nullptr;
+    // after a remesh: concave-corner coarse ghosts of level lev reproduce their carried state
+    void (*remesh_corners)(const StepArgs&, int lev, cudaStream_t) = nullptr;
     void (*ledger)(const StepArgs&, long long nblocks, double* partial, double* out, cudaStream_t) = nullptr;
     void (*init)(const StepArgs&, int lev, const double* rho, const double* u, const double* T, cudaStream_t) = nullptr;
     // AA-pattern streaming (one buffer, single level): one iteration of parity a.rd[0]; null
@@ -43,6 +49,13 @@ bool find_kernels_d2q13(int model, int storage, const int* block, bool newton_fp
 
 int mlp_train_device(const double* d_uT, const double* d_lam, int64_t n, double T0, const lbm_mlp_train_params& p,
                      float* d_master, float* d_rounded, double* h_ms, float* h_loss, cudaStream_t s);
+// per-level sources of the remesh transfer (old conserved state, slot-indexed components)
+struct TransferSrc {
+    const double* ptr[MAX_LEVELS];
+    long long ncell[MAX_LEVELS];
+};
+void launch_transfer(const long long* rowptr, const long long* col, const double* w, long long rows,
+                     const TransferSrc& src, int ncomp, double* dst, cudaStream_t s);
 void launch_scatter(const int* slot, long long count, const double* src, long long src_stride, int ncomp, double* dst,
                     long long dst_stride, cudaStream_t s);
 void launch_gather(const int* slot, long long count, const double* src, long long src_stride, int ncomp, double* dst,

@@ -964,7 +964,34 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
     if (type == C_ABSENT || type == C_SOLID) return;
     Cell<M, ST> c;
     int conv;
-    assemble<M, ST, BX, BY, BZ, MODE_READ>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+    // which 4..6: the conserved (ledger) state, coarse ghosts with their unknowns coalesced
+    if (which >= 4 && which <= 6) assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+    else assemble<M, ST, BX, BY, BZ, MODE_READ>(a, lev, b, l, type, simple, nbr_s, c, &conv);
+    if (which >= 4 && which <= 6) which -= 3;
+    if (which == 7) {
+        // kinetic sensor eps = (1/V) sum |f - f_eq| / f_eq of the pre-collision state (Eq.
+        // DeltaAvg; the refinement criterion of Sec. 8), terms with f_eq <= tiny skipped
+        using T = typename Store<ST>::T;
+        T rho, u[3], Tt;
+        moments<M, ST>(a.m, c, rho, u, Tt);
+        T fe[M::Q];
+        if constexpr (!M::HAS_G) {
+            if constexpr (hermite_weak<M>::value) M::template feq_dev<T>(rho, u[0], u[1], T(a.m.rho_ref), fe);
+            else weak_feq_dev<M::D, T>(rho, u[0], u[1], u[2], T(a.m.rho_ref), fe);
+        } else {
+            int it = 0, cv = 1;
+            M::template feq<ST>(a.m, rho, u[0], u[1], Tt, c.lam, fe, &it, &cv);
+        }
+        double eps = 0.0;
+#pragma unroll
+        for (int q = 0; q < M::Q; ++q) {
+            const double ref = M::DEV ? M::w(q) * a.m.rho_ref : 0.0;
+            const double fq = double(c.f[q]) + ref, eq = double(fe[q]) + ref;
+            if (eq > 1e-300) eps += fabs(fq - eq) / eq;
+        }
+        out[cell] = eps / M::Q;
+        return;
+    }
     if (which == 0) {
         T rho, u[3], Tt;
         moments<M, ST>(a.m, c, rho, u, Tt);
@@ -1092,6 +1119,88 @@ static __global__ void __launch_bounds__(1024) k_ledger_final(const double* part
         __syncthreads();
     }
     if (l < 5) out[l] = red[l][0];
+}
+
+// ------------------------------------------------------------------ state upload
+// Pre-collision state given in full values (f: Q x ncell, then g: Q x ncell for the double
+// distribution, then lambda: 8 x ncell, slot-indexed) into buffer 1, lambda into both buffers;
+// absent and solid slots get zero populations.  The prestream pass then writes buffer 0.
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_load_state(const StepArgs a, int lev, const double* __restrict__ full) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    const LevelDev& L = a.lv[lev];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    const long long cell = b * BS + l;
+    const long long n = L.ncell;
+    const int type = (b == L.nb) ? (int)C_ABSENT : (L.bflag[b] == 1 ? (int)C_FLUID : (int)L.type[cell]);
+    const bool zero = type == C_ABSENT || type == C_SOLID;
+#pragma unroll 1
+    for (int q = 0; q < M::Q; ++q) {
+        const T ref = M::DEV ? ref_f<M, ST>(a.m, q) : T(0);
+        const T fv = zero ? -ref : T(full[(long long)q * n + cell]) - ref;
+        const T gv = (M::HAS_G && !zero) ? T(full[(long long)(M::Q + q) * n + cell]) : T(0);
+        store_pop<M, ST, BS>(L, 1, cell, q, a.m, fv, gv);
+        if (zero) store_pop<M, ST, BS>(L, 0, cell, q, a.m, fv, gv);
+    }
+    if constexpr (M::HAS_LAM) {
+        if (b < L.nb) {
+            const long long o = (long long)(M::HAS_G ? 2 * M::Q : M::Q) * n;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const double v = zero ? 0.0 : full[o + (long long)i * n + cell];
+                L.lam[((long long)0 * 8 + i) * n + cell] = v;
+                L.lam[((long long)1 * 8 + i) * n + cell] = v;
+            }
+        }
+    }
+}
+
+// After a remesh (level lev >= 1, state just loaded): a coarse ghost at a concave corner lets
+// its own streamed population stand in for children whose history leaves the finer level; those
+// populations are set to (2^D v - sum of the other children) / (number of such children), v the
+// ghost's carried state, so that its coalesced state is v and the ledger is kept exactly.
+template <class M, int ST, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_remesh_corners(const StepArgs a, int lev) {
+    using T = typename Store<ST>::T;
+    constexpr int BS = BX * BY * BZ;
+    constexpr int NK = (M::D == 3) ? 8 : 4;
+    const LevelDev& L = a.lv[lev];
+    const LevelDev& F = a.lv[lev - 1];
+    const long long b = blockIdx.x;
+    const int l = threadIdx.x;
+    const long long cell = b * BS + l;
+    if (L.bflag[b] == 1 || L.type[cell] != C_CGHOST) return;
+    const CellRecDev rec = L.recs[L.rec_id[cell]];
+    if (!(rec.b & 1)) return;
+#pragma unroll 1
+    for (int q = 0; q < M::Q; ++q) {
+        if (!(rec.mask >> q & 1ull)) continue;
+        int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+        for (int qq = 0; qq < M::Q; ++qq)
+            if (qq == q) { cx = M::cx(qq); cy = M::cy(qq); cz = M::cz(qq); }
+        const long long s = src_cell_g<BX, BY, BZ>(L.nbr, cell, cx, cy, cz);
+        T vf, vg;
+        load_pop<M, ST, BS>(L, 0, s, q, a.m, vf, vg);
+        T rf = T(0), rg = T(0);
+        int nb = 0;
+#pragma unroll 1
+        for (int k = 0; k < NK; ++k) {
+            const long long ch = rec.a + (k & 1) + ((k >> 1) & 1) * BX + ((k >> 2) & 1) * BX * BY;
+            if (history_leaves<M, BX, BY, BZ>(F, ch, cx, cy, cz)) {
+                ++nb;
+                continue;
+            }
+            T cf, cg;
+            load_pop<M, ST, BS>(F, 0, src_cell_g<BX, BY, BZ>(F.nbr, ch, cx, cy, cz), q, a.m, cf, cg);
+            rf += cf;
+            rg += cg;
+        }
+        if (!nb) continue;
+        store_pop<M, ST, BS>(L, 0, s, q, a.m, (T(NK) * vf - rf) / T(nb), (T(NK) * vg - rg) / T(nb));
+    }
 }
 
 // ------------------------------------------------------------------ initialisation
@@ -1238,6 +1347,14 @@ struct Launch {
     static void read(const StepArgs& a, int lev, int which, double* out, cudaStream_t s) {
         if (a.lv[lev].nb) k_read<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev, which, out);
     }
+    static void load_state(const StepArgs& a, int lev, const double* full, cudaStream_t s) {
+        if (!a.lv[lev].nb) return;
+        k_load_state<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb + 1, BX * BY * BZ, 0, s>>>(a, lev, full);
+        k_init_prestream<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
+    }
+    static void remesh_corners(const StepArgs& a, int lev, cudaStream_t s) {
+        if (lev >= 1 && a.lv[lev].nb) k_remesh_corners<M, ST, BX, BY, BZ><<<(unsigned)a.lv[lev].nb, BX * BY * BZ, 0, s>>>(a, lev);
+    }
     static void ledger(const StepArgs& a, long long nblocks, double* partial, double* out, cudaStream_t s) {
         if (nblocks) k_ledger<M, ST, BX, BY, BZ><<<(unsigned)nblocks, BX * BY * BZ, 0, s>>>(a, partial);
         k_ledger_final<<<1, 1024, 0, s>>>(partial, nblocks, out);
@@ -1287,6 +1404,8 @@ KernelSet make_set() {
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
     k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;
     k.init = &Launch<M, ST, BX, BY, BZ>::init;
+    k.load_state = &Launch<M, ST, BX, BY, BZ>::load_state;
+    k.remesh_corners = &Launch<M, ST, BX, BY, BZ>::remesh_corners;
     if constexpr (aa_capable<M>::value) k.aa = &Launch<M, ST, BX, BY, BZ>::aa;
     k.step_kernel = (const void*)&k_step<M, ST, BX, BY, BZ, true, 0>;   // for occupancy queries
     k.block_threads = BX * BY * BZ;

@@ -26,6 +26,9 @@ class GridSpec:
     periodic: tuple = (True, True, True)
     faces: dict = field(default_factory=dict)   # face -> (kind, rho, (ux, uy, uz), T)
     solids: list = field(default_factory=list)  # dicts: sphere / naca
+    # instead of boxes: the finest level wanted at each finest cell, an integer array of shape
+    # extent (0 finest .. n_levels - 1 coarsest)
+    level_map: object = None
 
 
 def cell_centres(coords: np.ndarray, level) -> np.ndarray:

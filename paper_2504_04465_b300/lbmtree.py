@@ -66,9 +66,13 @@ _sig = {
     "lbm_set_precision": [_P, C.c_int],
     "lbm_set_sponge": [_P, _D, C.c_double, C.c_double, C.c_double, C.c_double],
     "lbm_set_streaming": [_P, C.c_int],
+    "lbm_grade_level_map": [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint8)],
+    "lbm_amr_level_map": [_P, C.c_double, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8)],
+    "lbm_remesh": [_P, C.POINTER(C.c_uint8)],
     "lbm_set_boundary": [_P, C.c_int, C.c_int, _D],
     "lbm_set_block": [_P, C.c_int, C.c_int, C.c_int],
     "lbm_build_grid": [_P, C.POINTER(C.c_int64), C.c_int, C.POINTER(Box), C.c_int, C.POINTER(Shape), C.c_int],
+    "lbm_build_grid_map": [_P, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_uint8), C.POINTER(Shape), C.c_int],
     "lbm_cells": [_P, C.POINTER(C.c_int64), C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.POINTER(C.c_int32)),
                   C.POINTER(C.POINTER(C.c_uint8))],
     "lbm_velocities": [_P, C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_int32))],
@@ -200,6 +204,17 @@ def lattice_cs2(name: str) -> float:
 PIPE_KIND = {"fp32": 0, "fp64": 1, "fp32x2": 2}
 
 
+def grade_level_map(level_map, n_levels: int, lattice: str, periodic) -> np.ndarray:
+    """The library's grading of a level map (array of shape extent), returned as a new array."""
+    m = np.asarray(level_map, dtype=np.uint8)
+    ext = (C.c_int64 * 3)(*(list(m.shape) + [1, 1, 1])[:3])
+    per = (C.c_int * 3)(*(list(int(bool(p)) for p in periodic) + [1, 1, 1])[:3])
+    flat = np.ascontiguousarray(m.ravel(order="F"))
+    _check(_lib.lbm_grade_level_map(m.ndim, ext, n_levels, LATTICE[lattice], per, flat.ctypes.data_as(C.POINTER(C.c_uint8))),
+           "lbm_grade_level_map")
+    return flat.reshape(m.shape, order="F")
+
+
 def pipe_peak(kind: str, device: int = 0, iters: int = 8192) -> tuple[float, float]:
     """(flop/s, ms) of a fused multiply-add pipe of ``device`` (lbm_pipe_peak): "fp32", "fp64"
     or "fp32x2" (packed FP32 pairs)."""
@@ -328,8 +343,50 @@ class Context:
     def set_block(self, bx: int, by: int, bz: int = 1) -> None:
         _check(_lib.lbm_set_block(self._h, bx, by, bz), "lbm_set_block")
 
+    @staticmethod
+    def _shapes(solids):
+        sh = (Shape * max(1, len(solids)))()
+        for k, s in enumerate(solids):
+            if s["kind"] == "sphere":
+                sh[k].kind = 1
+                p = list(s["center"]) + [0.0] * (3 - len(s["center"])) + [s["radius"]]
+            elif s["kind"] == "naca":
+                sh[k].kind = 2
+                p = [s["chord"], s["x0"], s["y0"], s.get("t", 0.12)]
+            else:
+                raise ValueError(s["kind"])
+            sh[k].p[: len(p)] = p
+        return sh
+
+    def build_grid_map(self, extent, n_levels: int, level_map, solids=()) -> None:
+        """Build from a level map (array of shape extent: the finest level wanted per finest cell)."""
+        ext = (C.c_int64 * 3)(*(list(extent) + [1, 1, 1])[:3])
+        self._extent = tuple(int(e) for e in extent)
+        m = np.ascontiguousarray(np.asarray(level_map, dtype=np.uint8).ravel(order="F"))
+        _check(_lib.lbm_build_grid_map(self._h, ext, n_levels, m.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                       self._shapes(solids), len(solids)), "lbm_build_grid_map")
+
+    def amr_level_map(self, threshold: float, fixed_map=None) -> np.ndarray:
+        """Graded level map (array of shape extent) from the kinetic sensor: finest level where eps
+        exceeds threshold, fixed_map (or the coarsest level) elsewhere."""
+        ext = self._extent
+        n = int(np.prod(ext))
+        out = np.zeros(n, dtype=np.uint8)
+        fx = None
+        if fixed_map is not None:
+            fx = np.ascontiguousarray(np.asarray(fixed_map, dtype=np.uint8).ravel(order="F"))
+        _check(_lib.lbm_amr_level_map(self._h, threshold, fx.ctypes.data_as(C.POINTER(C.c_uint8)) if fx is not None else None,
+                                      out.ctypes.data_as(C.POINTER(C.c_uint8))), "lbm_amr_level_map")
+        return out.reshape(ext, order="F")
+
+    def remesh(self, level_map) -> None:
+        """Rebuild the grid from a level map and carry the state over (coalescence / explosion)."""
+        m = np.ascontiguousarray(np.asarray(level_map, dtype=np.uint8).ravel(order="F"))
+        _check(_lib.lbm_remesh(self._h, m.ctypes.data_as(C.POINTER(C.c_uint8))), "lbm_remesh")
+
     def build_grid(self, extent, n_levels: int, boxes=(), solids=()) -> None:
         ext = (C.c_int64 * 3)(*(list(extent) + [1, 1, 1])[:3])
+        self._extent = tuple(int(e) for e in extent)
         bx = (Box * max(1, len(boxes)))()
         for k, (lv, lo, hi) in enumerate(boxes):
             bx[k].level = lv
@@ -373,7 +430,10 @@ class Context:
                     self.set_boundary(f, kind, rho, u, T)
         if block is not None:
             self.set_block(*block)
-        self.build_grid(spec.extent, spec.n_levels, spec.boxes, spec.solids)
+        if getattr(spec, "level_map", None) is not None:
+            self.build_grid_map(spec.extent, spec.n_levels, spec.level_map, spec.solids)
+        else:
+            self.build_grid(spec.extent, spec.n_levels, spec.boxes, spec.solids)
 
     # -------------------------------------------------------------- cells
     def n_cells(self) -> int:
