@@ -49,6 +49,7 @@ struct DevLevel {
     int* blist[2] = {nullptr, nullptr};
     int64_t nlist[2] = {0, 0};
     int* bxyz = nullptr;
+    int* blist_all = nullptr;       // every block, for the general kernel alone (far-field relaxation on)
 };
 
 struct Constants {
@@ -212,6 +213,13 @@ void fill_args(const lbm_ctx* c, StepArgs& a) {
             d.blist[k] = c->dl[i].blist[k];
             d.nlist[k] = c->dl[i].nlist[k];
         }
+        if (c->sp_smax > 0) {
+            // the far-field relaxation runs in the general kernel only (the interior kernel keeps
+            // its register budget): every block goes through the general list
+            d.blist[1] = c->dl[i].blist_all;
+            d.nlist[0] = 0;
+            d.nlist[1] = bl.nb;
+        }
         const double nu = c->params.nu0 / double(int64_t(1) << i);
         d.tau = nu / theta + 0.5;
         d.omega = 1.0 / d.tau;
@@ -279,7 +287,7 @@ int64_t iteration_args(const lbm_ctx* c, int64_t t, StepArgs& a) {
         int64_t o = 0;
         for (int j = 0; j < n; ++j) {
             a.list_off[k][j] = o;
-            o += c->dl[a.active[j]].nlist[k];
+            o += a.lv[a.active[j]].nlist[k];
         }
         a.list_off[k][n] = o;
     }
@@ -802,6 +810,17 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         }
         if (!lv.recs.empty())
             CU(cudaMemcpy(d.recs, lv.recs.data(), lv.recs.size() * sizeof(CellRecDev), cudaMemcpyHostToDevice));
+        {
+            std::vector<int32_t> all(lv.nb);
+            for (int64_t b = 0; b < lv.nb; ++b) all[b] = (int32_t)b;
+            d.blist_all = (int*)c->dalloc(std::max<size_t>(all.size(), 1) * 4);
+            if (!d.blist_all) {
+                c->release();
+                c->built = false;
+                return fail(LBM_ERR_OOM, "device allocation of the block lists");
+            }
+            if (!all.empty()) CU(cudaMemcpy(d.blist_all, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
+        }
     }
     c->d_status = (int*)c->dalloc(sizeof(int));
     c->d_nstat = (unsigned long long*)c->dalloc(19 * sizeof(unsigned long long));

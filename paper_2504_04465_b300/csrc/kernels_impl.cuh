@@ -675,7 +675,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         // interior kernel, binary16 deviations, recursive regularization: the collision writes
         // the storage value directly (fine ghosts, which do not collide, are scaled instead)
         constexpr bool REL = FAST && ST == ST_F16DEV && !M::HAS_G && M::RR && M::DEV;
-        if constexpr (!M::HAS_G && M::DEV) {
+        if constexpr (!M::HAS_G && M::DEV && !FAST) {   // every block takes this kernel then
             if (a.m.sponge_on && type != C_FGHOST) relax_far_field<M, ST, BX, BY, BZ>(a.m, L, lev, b, l, c);
         }
         if (type != C_FGHOST) {
