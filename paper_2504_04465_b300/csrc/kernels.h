@@ -12,9 +12,10 @@ struct KernelSet {
     // and may run concurrently)
     void (*step)(const StepArgs&, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) = nullptr;
     // which: 0 moments, 1 f, 2 g, 3 lambda, 4..6 the same three with coarse-ghost unknowns
-    // coalesced (the conserved state), 7 the kinetic sensor eps
+    // coalesced (the conserved state; f as stored: deviations in the deviation formats), 7 the
+    // kinetic sensor eps
     void (*read)(const StepArgs&, int lev, int which, double* out, cudaStream_t) = nullptr;
-    // full-value pre-collision state (f, g, lambda; slot-indexed) into a level's buffers
+    // pre-collision state as stored (f, g, lambda; slot-indexed) into a level's buffers
     void (*load_state)(const StepArgs&, int lev, const double* full, cudaStream_t) = nullptr;
     // after a remesh: concave-corner coarse ghosts of level lev reproduce their carried state
     void (*remesh_corners)(const StepArgs&, int lev, cudaStream_t) = nullptr;

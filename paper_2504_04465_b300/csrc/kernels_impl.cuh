@@ -967,7 +967,10 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
     // which 4..6: the conserved (ledger) state, coarse ghosts with their unknowns coalesced
     if (which >= 4 && which <= 6) assemble<M, ST, BX, BY, BZ, MODE_LEDGER>(a, lev, b, l, type, simple, nbr_s, c, &conv);
     else assemble<M, ST, BX, BY, BZ, MODE_READ>(a, lev, b, l, type, simple, nbr_s, c, &conv);
-    if (which >= 4 && which <= 6) which -= 3;
+    // the conserved state is handed on as stored (deviations for the deviation formats), so
+    // that a copy is exact
+    const bool raw = which >= 4 && which <= 6;
+    if (raw) which -= 3;
     if (which == 7) {
         // kinetic sensor eps = (1/V) sum |f - f_eq| / f_eq of the pre-collision state (Eq.
         // DeltaAvg; the refinement criterion of Sec. 8), terms with f_eq <= tiny skipped
@@ -1003,7 +1006,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_read(const StepArgs a, int lev
     } else if (which == 1) {
 #pragma unroll
         for (int q = 0; q < M::Q; ++q)
-            out[(long long)q * L.ncell + cell] = M::DEV ? (double)c.f[q] + M::w(q) * a.m.rho_ref : (double)c.f[q];
+            out[(long long)q * L.ncell + cell] = (M::DEV && !raw) ? (double)c.f[q] + M::w(q) * a.m.rho_ref : (double)c.f[q];
     } else if (which == 2) {
         if constexpr (M::HAS_G) {
 #pragma unroll
@@ -1122,9 +1125,10 @@ static __global__ void __launch_bounds__(1024) k_ledger_final(const double* part
 }
 
 // ------------------------------------------------------------------ state upload
-// Pre-collision state given in full values (f: Q x ncell, then g: Q x ncell for the double
-// distribution, then lambda: 8 x ncell, slot-indexed) into buffer 1, lambda into both buffers;
-// absent and solid slots get zero populations.  The prestream pass then writes buffer 0.
+// Pre-collision state as stored (f: Q x ncell, deviations f - w rho_ref for the deviation formats,
+// then g: Q x ncell for the double distribution, then lambda: 8 x ncell, slot-indexed) into
+// buffer 1, lambda into both buffers; absent and solid slots get zero populations.  The prestream
+// pass then writes buffer 0.
 template <class M, int ST, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ) k_load_state(const StepArgs a, int lev, const double* __restrict__ full) {
     using T = typename Store<ST>::T;
@@ -1139,7 +1143,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_load_state(const StepArgs a, i
 #pragma unroll 1
     for (int q = 0; q < M::Q; ++q) {
         const T ref = M::DEV ? ref_f<M, ST>(a.m, q) : T(0);
-        const T fv = zero ? -ref : T(full[(long long)q * n + cell]) - ref;
+        const T fv = zero ? -ref : T(full[(long long)q * n + cell]);
         const T gv = (M::HAS_G && !zero) ? T(full[(long long)(M::Q + q) * n + cell]) : T(0);
         store_pop<M, ST, BS>(L, 1, cell, q, a.m, fv, gv);
         if (zero) store_pop<M, ST, BS>(L, 0, cell, q, a.m, fv, gv);

@@ -132,3 +132,24 @@ def test_vortex_follows_the_refinement():
     assert err["rho"] < 1e-12 and err["u"] < 1e-12, err
     assert abs(ctx.conserved()[0] - mass0) <= 1e-13 * mass0
     ctx.close()
+
+
+def test_remesh_identity_at_size():
+    """A 2048^2 D2Q9 RR state on a three-level disc map, remeshed onto the same map: bulk and
+    boundary cells keep their moments bit for bit and the totals are unchanged (a property at
+    any size)."""
+    lat, n, levels = "D2Q9", 2048, 3
+    m = disc_map(n, (0.5 * n, 0.5 * n), 200, levels, lat)
+    spec = _spec(n, m, levels)
+    ctx = H.make_gpu(spec, lat, "rr", "f64", vortex_fields(n), nu0=0.01)
+    ctx.step(4)
+    ctx.sync()
+    r0 = ctx.moments()
+    t0 = ctx.conserved()
+    _, _, ty = ctx.cells()
+    ctx.remesh(m)
+    r1 = ctx.moments()
+    keep = np.isin(ty, (1, 4))
+    assert np.array_equal(r0[0][keep], r1[0][keep]) and np.array_equal(r0[1][:, keep], r1[1][:, keep])
+    assert np.abs(ctx.conserved()[:3] - t0[:3]).max() <= 1e-13 * t0[0]
+    ctx.close()

@@ -129,3 +129,31 @@ def test_concave_corners_d3q27_f64():
     t1 = ctx.conserved()
     assert abs(t1[0] - t0[0]) <= 1e-13 * abs(t0[0])
     ctx.close()
+
+
+def test_riemann12_full_size_keeps_the_diagonal_symmetry():
+    """At the bench's size (N_c = 512, 2048^2 finest cells) on the optim grid, which is symmetric
+    under x <-> y like the initial state: after 24 fine iterations of the FP64 numerical DDF the
+    density is symmetric to 1e-10 relative (the arithmetic of mirrored cells differs only in the
+    order of sums).  A property that holds at any size, where the oracle cannot run."""
+    nc = 512
+    spec = I.riemann12_spec(nc, "optim")
+
+    def f(level, coords, c):
+        return I.riemann12_fields(c, nc, T0["D2Q21"])
+    ctx = H.make_gpu(spec, "D2Q21", "num_ddf", "f64", f, nu0=0.0, T0=T0["D2Q21"], sensor_A=1.5)
+    ctx.step_fine(24)
+    ctx.sync()
+    lv, xyz, ty = ctx.cells()
+    rho = ctx.moments()[0]
+    worst = 0.0
+    for level in (0, 1):
+        m = (lv == level) & (ty == 1)
+        side = 4 * nc >> level
+        dense = np.full((side, side), np.nan)
+        dense[xyz[m, 0], xyz[m, 1]] = rho[m]
+        both = ~np.isnan(dense) & ~np.isnan(dense.T)
+        worst = max(worst, float(np.abs(dense - dense.T)[both].max()))
+    assert worst < 1e-10 * np.abs(rho).max(), worst
+    assert ctx.stats().newton_nonconverged == 0
+    ctx.close()

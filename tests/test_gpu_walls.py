@@ -82,3 +82,16 @@ def test_closed_box_d2q37_f64():
     t1 = ctx.conserved()
     assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
     ctx.close()
+
+
+def test_cavity_mass_at_size():
+    """A 1024^2 lid-driven cavity with a centred refined patch (two levels, RR, FP64): the mass
+    stays constant to round-off over 50 coarse steps while the lid drives the flow."""
+    spec = I.cavity_spec(1024, 0.1, 2, (256, 768))
+    ctx = H.make_gpu(spec, "D2Q9", "rr", "f64", rest, nu0=0.05)
+    t0 = ctx.conserved()
+    ctx.step(50)
+    t1 = ctx.conserved()
+    assert abs(t1[0] - t0[0]) <= 1e-12 * t0[0]
+    assert abs(t1[1]) > 1e-3
+    ctx.close()
