@@ -160,7 +160,8 @@ typedef struct {
 int lbm_lattice_info(int lattice, int* Q, int* D, int* reach, double* cs2);
 /* Device memory of the grid's arrays (populations, tables, multipliers) from the caller's
  * allocator, for instance a framework's caching allocator: alloc(bytes, user) returns device
- * memory on the context's device (NULL on failure), free(ptr, user) returns it.  Set before
+ * memory on the context's device, aligned to at least 16 bytes (NULL on failure; a less aligned
+ * block is returned to free() and the build fails), free(ptr, user) returns it.  Set before
  * lbm_build_grid; NULL restores cudaMalloc.  Temporary buffers of initialisation, readout and
  * training still use cudaMalloc. */
 typedef struct {
@@ -210,8 +211,11 @@ int lbm_set_block(lbm_ctx* ctx, int bx, int by, int bz);
 
 /* Compiled variants of the step kernels (occupancy targets): *n variants; minb[k] encodes the
  * resident 128-thread blocks per SM variant k is compiled for as 10 * interior + general
- * (0 = the model's defaults; minb may be NULL, else holds 4 ints).  The variants compute the same
- * result; lbm_set_variant() picks one (an autotuner times them).  Both need a built grid. */
+ * (0 = the model's defaults; minb may be NULL, else holds 8 ints).  Codes of 100 and above are the
+ * same targets with the interior blocks gathered directly from global memory instead of staged
+ * through shared memory (the D3Q27 regularized model in binary16 storage stages by default).  The
+ * variants compute the same result; lbm_set_variant() picks one (an autotuner times them).  Both
+ * need a built grid. */
 int lbm_variants(lbm_ctx* ctx, int* n, int* minb);
 int lbm_set_variant(lbm_ctx* ctx, int variant);
 

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -131,6 +132,10 @@ struct lbm_ctx {
         if (alloc_cb.alloc) {
             p = alloc_cb.alloc(bytes, alloc_cb.user);
             if (!p) return nullptr;
+            if ((uintptr_t)p & 15) {                        // the kernels copy 16-byte rows
+                alloc_cb.free(p, alloc_cb.user);
+                return nullptr;
+            }
         } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
             return nullptr;
         }

@@ -7,6 +7,8 @@
 
 namespace lbm {
 
+constexpr int MAX_VARIANTS = 8;     // lbm_variants() fills at most this many codes
+
 struct KernelSet {
     // interior-kernel launch on s_fast, general-kernel launch on s_gen (they touch disjoint cells
     // and may run concurrently)
@@ -26,14 +28,14 @@ struct KernelSet {
     void (*aa)(const StepArgs&, cudaStream_t) = nullptr;
     const void* step_kernel = nullptr;
     int block_threads = 0;
-    // compiled variants of the step launch (occupancy targets of the simple-block kernel)
-    void (*variant[4])(const StepArgs&, long long, long long, cudaStream_t, cudaStream_t) = {nullptr, nullptr, nullptr,
-                                                                                            nullptr};
-    int variant_minb[4] = {0, 0, 0, 0};
+    // compiled variants of the step launch (occupancy targets of the simple-block kernel; codes
+    // >= 100: the same target with the simple blocks gathered directly instead of staged)
+    void (*variant[MAX_VARIANTS])(const StepArgs&, long long, long long, cudaStream_t, cudaStream_t) = {};
+    int variant_minb[MAX_VARIANTS] = {};
     int n_variants = 1;
     // batched launches of several cases (per variant; null where the lattice has none)
-    void (*batch[4])(const StepArgs*, const long long*, const long long*, int, long long, long long, cudaStream_t,
-                     cudaStream_t) = {nullptr, nullptr, nullptr, nullptr};
+    void (*batch[MAX_VARIANTS])(const StepArgs*, const long long*, const long long*, int, long long, long long,
+                                cudaStream_t, cudaStream_t) = {};
 };
 
 // Kernel-set code of the recursive-regularized collision with the trace of the second-order

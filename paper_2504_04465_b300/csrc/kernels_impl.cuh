@@ -16,6 +16,7 @@
 //   static void init_guess(ux, uy, T, lam)
 #pragma once
 #include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -799,6 +800,201 @@ k_step_batch(const StepArgs* __restrict__ args, const long long* __restrict__ of
     step_block<M, ST, BX, BY, BZ, FAST>(args[lo], bid - off[lo], nbr_s, s_nstat);
 }
 
+// ------------------------------------------------------------------ staged binary16 interior kernel
+// Interior (simple and streaming) blocks of the D3Q27 regularized model in binary16 deviation
+// storage, with the pull staged in shared memory and two cells per thread.  A block's cells are
+// BY * BZ = 16 rows of 8 cells, and one row of one population is 16 bytes of storage, so the pull
+// of population q for the whole block is 16 row copies (cp.async, 16 bytes each), plus 16 more
+// from the x-neighbour block when xi_x != 0.  The staged region of q holds, per destination row:
+//   xi_x = +1: [row of the x-1 neighbour | own-side row]  (source x = lx - 1 at byte 14 + 2 lx)
+//   xi_x = -1: [own-side row | row of the x+1 neighbour]  (source x = lx + 1 at byte  2 + 2 lx)
+//   xi_x =  0: [own-side row]                             (source x = lx     at byte      2 lx)
+// ("own side": the row (ly - xi_y, lz - xi_z) of whichever block holds it), so every thread reads
+// its sources at fixed offsets from two shared-memory addresses.  A thread owns the x-neighbours
+// (2k, 2k + 1) of a row: the collision (rr_rel_q27) runs on both at once in packed FP32 pairs,
+// directly on the stored relative deviations, and each population of the pair is stored as one
+// 32-bit word.  A thread block takes NB cell blocks (a stride of the grid apart) in turn, with two
+// staging buffers: the rows of the next cell block and the neighbour list of the one after are
+// copied while the current one collides, so the copies' latency is hidden behind arithmetic.
+template <class M, int ST, int BX, int BY, int BZ>
+struct staged_f16 : std::bool_constant<ST == ST_F16DEV && M::D == 3 && M::Q == 27 && !M::HAS_G && !M::HAS_LAM &&
+                                       M::DEV && M::RR && !hermite_weak<M>::value && weak_var<M>::value == 0 &&
+                                       BX == 8 && BY * BZ == 16> {};
+
+__device__ __forceinline__ void cp_async16(unsigned smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// staged bytes of population q (16 rows of 16 or 32 bytes) and its offset in a staging buffer
+template <class M>
+__host__ __device__ constexpr int stg_bytes(int q) { return M::cx(q) == 0 ? 256 : 512; }
+template <class M>
+__host__ __device__ constexpr int stg_off(int q) {
+    int o = 0;
+    for (int k = 0; k < q; ++k) o += stg_bytes<M>(k);
+    return o;
+}
+
+// Row copy of population Q for destination row r (y, z terms ty, tz of that row) and part p
+// (0: own side, 1: x-neighbour side, only for xi_x != 0); nbo: the 27 neighbour blocks' element
+// offsets.
+template <class M, int BX, int BY, int BZ, int Q>
+__device__ __forceinline__ void stage_pop(const char* fsrc, const unsigned* nbo, unsigned sbase, int r, int p,
+                                          const unsigned* ty, const unsigned* tz) {
+    constexpr int BS = BX * BY * BZ;
+    constexpr int cx = M::cx(Q), cy = M::cy(Q), cz = M::cz(Q);
+    if (cx == 0 && p) return;
+    // neighbour digit of x: 1 (own column of blocks) or 1 - xi_x (the x-neighbour, at -xi_x)
+    const unsigned P = ((unsigned)(p ? 1 - cx : 1) << 20) + ty[cy + 1] + tz[cz + 1];
+    const unsigned idx = nbo[P >> 20] + (unsigned)(Q * BS) + (P & 0xFFFFFu);
+    const unsigned dst = sbase + (unsigned)(stg_off<M>(Q) + r * (cx == 0 ? 16 : 32)) +
+                         ((cx != 0 && (p == 0) == (cx == 1)) ? 16u : 0u);
+    cp_async16(dst, fsrc + 2ull * idx);
+}
+template <class M, int BX, int BY, int BZ, int NW, int W, int... I>
+__device__ __forceinline__ void stage_warp(std::integer_sequence<int, I...>, const char* fsrc, const unsigned* nbo,
+                                           unsigned sbase, int r, int p, const unsigned* ty, const unsigned* tz) {
+    (
+        [&] {
+            if constexpr (W + NW * I < M::Q) stage_pop<M, BX, BY, BZ, W + NW * I>(fsrc, nbo, sbase, r, p, ty, tz);
+        }(),
+        ...);
+}
+
+// Eight resident thread blocks per SM (shared memory for eight; registers without spilling: nine
+// blocks spilled and ran slower).
+template <class M, int ST, int BX, int BY, int BZ, int MINB, int NB>
+__global__ void __launch_bounds__(BX * BY * BZ / 2, 8)
+k_step_staged(const StepArgs a) {
+    constexpr int BS = BX * BY * BZ;
+    constexpr int NT = BS / 2;                              // threads: two cells each
+    constexpr int NW = NT / 32;                             // warps
+    constexpr int ROWS = BY * BZ;
+    static_assert(NW == 2 && ROWS == 16, "two warps; a warp's 32 lanes cover 16 rows x 2 parts");
+    static_assert(NB >= 1 && NB <= NT, "cell blocks per thread block");
+    constexpr int SB = stg_off<M>(M::Q);                    // bytes of one staging buffer
+    __shared__ __align__(16) unsigned char stg[2][SB];
+    __shared__ int nbr3[3][28];                             // neighbour lists of three cell blocks
+    __shared__ unsigned nbo[27];                            // element offsets, cell block being staged
+    __shared__ int ent_s[NB], lev_s[NB];
+    const long long n = a.list_off[0][a.n_active];
+    const int t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    const int r = lane & (ROWS - 1), p = lane >> 4;
+    // slot j: cell block blockIdx.x + j * gridDim.x of this iteration's interior list
+    auto slot_ok = [&](int j) { return (long long)blockIdx.x + (long long)j * gridDim.x < n; };
+    if (t < NB) {
+        const long long g = (long long)blockIdx.x + (long long)t * gridDim.x;
+        int lev = 0, e = 0;
+        if (g < n) {
+            long long i;
+            lev = find_level_list(a, 0, g, &i);
+            e = a.lv[lev].blist[0][i];
+        }
+        ent_s[t] = e;
+        lev_s[t] = lev;
+    }
+    __syncthreads();
+    auto nbr_src = [&](int j) { return a.lv[lev_s[j]].nbr + (long long)(ent_s[j] >> 1) * 27 + t; };
+    if (t < 27) nbr3[0][t] = *nbr_src(0);
+    if (NB > 1 && t < 27 && slot_ok(1)) cp_async4((unsigned)__cvta_generic_to_shared(&nbr3[1][t]), nbr_src(1));
+    unsigned ty[3], tz[3];
+    {
+        const int ry = r % BY, rz = r / BY;
+#pragma unroll
+        for (int c = -1; c <= 1; ++c) {
+            ty[c + 1] = axis_term<BY, BX, 3>(ry, c);
+            tz[c + 1] = axis_term<BZ, BX * BY, 9>(rz, c);
+        }
+    }
+    // copies of the rows of slot j into buffer j & 1 (its neighbour list landed in nbr3[j % 3])
+    auto stage = [&](int j) {
+        const LevelDev& L = a.lv[lev_s[j]];
+        if (t < 27) {
+            const int v = nbr3[j % 3][t];
+            nbo[t] = (unsigned)(v < 0 ? L.nb : v) * (unsigned)(M::Q * BS);
+        }
+        __syncthreads();
+        const char* fsrc = (const char*)L.f[a.rd[lev_s[j]]];
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(stg[j & 1]);
+        using Seq = std::make_integer_sequence<int, (27 + NW - 1) / NW>;
+        if (w == 0) stage_warp<M, BX, BY, BZ, NW, 0>(Seq{}, fsrc, nbo, sbase, r, p, ty, tz);
+        else stage_warp<M, BX, BY, BZ, NW, 1>(Seq{}, fsrc, nbo, sbase, r, p, ty, tz);
+    };
+    __syncthreads();
+    stage(0);
+    cp_async_commit();
+    // cells (2k, row) and (2k + 1, row) of each cell block
+    const int k2 = 2 * (t % (BX / 2)), row = t / (BX / 2);
+    const int l0 = k2 + BX * row;
+#pragma unroll 1
+    for (int j = 0; j < NB && slot_ok(j); ++j) {
+        cp_async_wait_all();
+        __syncthreads();          // slot j's rows and slot j + 1's neighbour list are in place
+        if (j + 2 < NB && t < 27 && slot_ok(j + 2))
+            cp_async4((unsigned)__cvta_generic_to_shared(&nbr3[(j + 2) % 3][t]), nbr_src(j + 2));
+        if (j + 1 < NB && slot_ok(j + 1)) stage(j + 1);
+        cp_async_commit();
+        // collide slot j from buffer j & 1
+        const int lev = lev_s[j];
+        const LevelDev& L = a.lv[lev];
+        const long long b = (long long)(ent_s[j] >> 1);
+        const bool streaming = ent_s[j] & 1;
+        const long long cell = b * BS + l0;
+        bool work0 = true, work1 = true, fg0 = false, fg1 = false;
+        if (streaming) {
+            const int t0 = L.type[cell], t1 = L.type[cell + 1];
+            work0 = !(t0 == C_ABSENT || t0 == C_SOLID || (t0 == C_FGHOST && a.sync_fg[lev]));
+            work1 = !(t1 == C_ABSENT || t1 == C_SOLID || (t1 == C_FGHOST && a.sync_fg[lev]));
+            fg0 = t0 == C_FGHOST;
+            fg1 = t1 == C_FGHOST;
+        }
+        const unsigned char* buf = stg[j & 1];
+        const unsigned char* s16 = buf + row * 16 + 2 * k2;    // populations with xi_x = 0
+        const unsigned char* s32 = buf + row * 32 + 2 * k2;    // the others
+        __half* out = (__half*)L.f[a.rd[lev] ^ 1];
+        const long long base = b * (long long)(M::Q * BS) + l0;
+        // fine ghosts stream purely: their staged values are stored as gathered
+        if (streaming && ((work0 && fg0) || (work1 && fg1))) {
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) {
+                const __half* sq = (const __half*)(M::cx(q) == 0 ? s16 + stg_off<M>(q)
+                                                                 : s32 + stg_off<M>(q) + (M::cx(q) == 1 ? 14 : 2));
+                if (work0 && fg0) out[base + q * BS] = sq[0];
+                if (work1 && fg1) out[base + q * BS + 1] = sq[1];
+            }
+        }
+        const bool c0 = work0 && !fg0, c1 = work1 && !fg1;
+        if (c0 || c1) {
+            F2 h[M::Q];
+#pragma unroll
+            for (int q = 0; q < M::Q; ++q) {
+                if (M::cx(q) == 0) {
+                    h[q].v = __half22float2(*(const __half2*)(s16 + stg_off<M>(q)));    // 4-byte aligned pair
+                } else {
+                    const __half* sq = (const __half*)(s32 + stg_off<M>(q) + (M::cx(q) == 1 ? 14 : 2));
+                    h[q].v = make_float2(__half2float(sq[0]), __half2float(sq[1]));
+                }
+            }
+            const bool both = c0 && c1;
+            rr_rel_q27<F2>(h, 1.0f - L.omega_f, [&](int q, F2 v) {
+                if (both) {
+                    *(__half2*)(out + base + q * BS) = __float22half2_rn(v.v);
+                } else {
+                    if (c0) out[base + q * BS] = __float2half_rn(v.v.x);
+                    if (c1) out[base + q * BS + 1] = __float2half_rn(v.v.y);
+                }
+            });
+        }
+    }
+    cp_async_wait_all();
+}
+
 // ------------------------------------------------------------------ AA-pattern streaming
 // In-place streaming with one population buffer, on single-level grids.  Two layouts alternate:
 //   L1 (after an even number of iterations): slot (x, qbar) holds the pre-collision f_q(x);
@@ -1334,12 +1530,21 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
 }
 
 // ------------------------------------------------------------------ host launchers
+constexpr int STAGED_NB = 8;      // cell blocks per thread block of the staged binary16 kernel
+
 template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
-    template <int MINB_F, int MINB_G>
+    // DIRECT: the simple blocks gather straight from global memory also where a staged kernel exists
+    template <int MINB_F, int MINB_G, bool DIRECT = false>
     static void step(const StepArgs& a, long long n_fast, long long n_gen, cudaStream_t s_fast, cudaStream_t s_gen) {
         // interior sweep first; the few, latency-bound general blocks fill in as its blocks retire
-        if (n_fast) k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(a);
+        if (n_fast) {
+            if constexpr (staged_f16<M, ST, BX, BY, BZ>::value && !DIRECT)
+                k_step_staged<M, ST, BX, BY, BZ, MINB_F, STAGED_NB>
+                    <<<(unsigned)((n_fast + STAGED_NB - 1) / STAGED_NB), BX * BY * BZ / 2, 0, s_fast>>>(a);
+            else
+                k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(a);
+        }
         if (n_gen) k_step<M, ST, BX, BY, BZ, false, MINB_G><<<(unsigned)n_gen, BX * BY * BZ, 0, s_gen>>>(a);
     }
     template <int MINB_F, int MINB_G>
@@ -1404,6 +1609,17 @@ KernelSet make_set() {
         k.variant_minb[2] = V1;
         k.variant_minb[3] = V2;
         k.n_variants = 4;
+        if constexpr (staged_f16<M, ST, BX, BY, BZ>::value) {   // the direct-gather forms, codes 100 + target
+            k.variant[4] = &LS::template step<0, 0, true>;
+            k.variant[5] = &LS::template step<V0 / 10, V0 % 10, true>;
+            k.variant[6] = &LS::template step<V1 / 10, V1 % 10, true>;
+            k.variant[7] = &LS::template step<V2 / 10, V2 % 10, true>;
+            k.variant_minb[4] = 100;
+            k.variant_minb[5] = 100 + V0;
+            k.variant_minb[6] = 100 + V1;
+            k.variant_minb[7] = 100 + V2;
+            k.n_variants = 8;
+        }
     }
     k.read = &Launch<M, ST, BX, BY, BZ>::read;
     k.ledger = &Launch<M, ST, BX, BY, BZ>::ledger;

@@ -224,6 +224,120 @@ __host__ __device__ __forceinline__ void weak_collide(T* f, T omega, T rho_ref, 
     (void)fe;
 }
 
+// ------------------------------------------------------------------ relative form, binary16 storage
+// Scalar (float) or packed two-cell (F2: a float2 per value, fma.rn.f32x2 and friends) arithmetic
+// for the collision of the binary16 interior kernel.
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+template <class V> struct Ar;
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float c(float s) { return s; }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+};
+template <> struct Ar<F2> {
+    static __device__ __forceinline__ F2 c(float s) { return {make_float2(s, s)}; }
+    static __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+    static __device__ __forceinline__ F2 rcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+};
+
+// D3Q27 recursive regularization (Eq. GenRegCollision with the a_neq of Eq. a1Rec) in the
+// variables of the binary16 format: in h_q = f_q / (w_q rho_ref) - 1, out the same of f*_q
+// (emit(q, value) receives each); keep = 1 - 1/tau.  With W18 = 18 w1d = {3, 12, 3} per axis and every factor of the
+// factorised form above divided by W18 of its velocity component (E' = E / W18 = 1 + e', X1',
+// X2' = {3, -1.5, 3}),
+//   h*_q = (1 + R) E'_x E'_y E'_z - 1 + K_xx X2'_x E'_y E'_z + ... + K_yz E'_x X1'_y X1'_z
+// with R = (rho - rho_ref) / rho_ref and K_ab = (1 - 1/tau) Pi_ab / rho_ref, and
+//   (1 + R) E'E'E' - 1 = (R E'_x E'_y + e'_x E'_y + e'_y) E'_z + e'_z,
+// so that a velocity costs three FMAs after nine products per (xi_x, xi_y) pair.  The moments
+// of w_q h_q (w_q = W(xi_x) W(xi_y) W(xi_z) / 216, W = {1, 4, 1}) come from the same separable
+// sums as tp_moments, scaled by 1/216 at the end.
+template <class V, class Emit>
+__device__ __forceinline__ void rr_rel_q27(const V* h, float keep, Emit&& emit) {
+    using A = Ar<V>;
+    const V four = A::c(4.0f);
+    V s[3][3][3];     // [a][y][z]: sum_x W(x) x^a h
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const int b = 3 * y + 9 * z;
+            const V u = h[b + 2] + h[b];
+            s[2][y][z] = u;
+            s[1][y][z] = h[b + 2] - h[b];
+            s[0][y][z] = A::fma(four, h[b + 1], u);
+        }
+    V t[3][3][3];     // [a][b][z]: sum_y W(y) y^b s[a][y][z], a + b <= 2
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const V u = s[a][2][z] + s[a][0][z];
+            t[a][0][z] = A::fma(four, s[a][1][z], u);
+            if (a <= 1) t[a][1][z] = s[a][2][z] - s[a][0][z];
+            if (a == 0) t[a][2][z] = u;
+        }
+    // sum_z W(z) z^c t[a][b][z]
+    auto z0 = [&](int a, int b) { return A::fma(four, t[a][b][1], t[a][b][2] + t[a][b][0]); };
+    const V r216 = A::c(1.0f / 216.0f);
+    const V R = z0(0, 0) * r216;
+    const V Jx = z0(1, 0) * r216, Jy = z0(0, 1) * r216, Jz = (t[0][0][2] - t[0][0][0]) * r216;
+    const V Mxx = z0(2, 0) * r216, Myy = z0(0, 2) * r216, Mzz = (t[0][0][2] + t[0][0][0]) * r216;
+    const V Mxy = z0(1, 1) * r216, Mxz = (t[1][0][2] - t[1][0][0]) * r216, Myz = (t[0][1][2] - t[0][1][0]) * r216;
+    const V ir = A::rcp(A::c(1.0f) + R);
+    const V ux = Jx * ir, uy = Jy * ir, uz = Jz * ir;
+    // K_ab = keep (M_ab - J_a u_b - delta_ab R / 3)
+    const V kp = A::c(keep), r3 = R * A::c(1.0f / 3.0f);
+    const V Kxx = kp * (Mxx - A::fma(Jx, ux, r3)), Kyy = kp * (Myy - A::fma(Jy, uy, r3)),
+            Kzz = kp * (Mzz - A::fma(Jz, uz, r3));
+    const V Kxy = kp * A::fma(A::c(0.0f) - Jx, uy, Mxy), Kxz = kp * A::fma(A::c(0.0f) - Jx, uz, Mxz),
+            Kyz = kp * A::fma(A::c(0.0f) - Jy, uz, Myz);
+    // per axis and component i = xi + 1: e', E' = 1 + e', X1'
+    V ex[3], Ex[3], Xx[3], ey[3], Ey[3], Xy[3], ez[3], Ez[3], Xz[3];
+    auto axis = [&](V u, V* e, V* E, V* X) {
+        const V a = A::c(3.0f) * (u * u), t3 = A::c(3.0f) * u;
+        e[0] = a - t3;
+        e[1] = a * A::c(-0.5f);
+        e[2] = a + t3;
+        E[0] = A::c(1.0f) + e[0];
+        E[1] = A::c(1.0f) + e[1];
+        E[2] = A::c(1.0f) + e[2];
+        X[0] = A::fma(A::c(2.0f), t3, A::c(-3.0f));
+        X[1] = A::c(0.0f) - t3;
+        X[2] = A::fma(A::c(2.0f), t3, A::c(3.0f));
+    };
+    axis(ux, ex, Ex, Xx);
+    axis(uy, ey, Ey, Xy);
+    axis(uz, ez, Ez, Xz);
+    // K with the X2' and X1' factors of one axis folded in
+    const V kx2[2] = {Kxx * A::c(3.0f), Kxx * A::c(-1.5f)}, ky2[2] = {Kyy * A::c(3.0f), Kyy * A::c(-1.5f)},
+            kz2[2] = {Kzz * A::c(3.0f), Kzz * A::c(-1.5f)};
+    V kxy[3], kxz[3], kyz[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        kxy[i] = Kxy * Xx[i];
+        kxz[i] = Kxz * Xx[i];
+        kyz[i] = Kyz * Xy[i];
+    }
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix)
+#pragma unroll
+        for (int iy = 0; iy < 3; ++iy) {
+            const V Exy = Ex[ix] * Ey[iy];
+            const V dE = A::fma(ex[ix], Ey[iy], ey[iy]);
+            const V N0 = A::fma(kx2[ix == 1], Ey[iy], A::fma(ky2[iy == 1], Ex[ix], kxy[ix] * Xy[iy]));
+            const V P = A::fma(R, Exy, dE + N0);
+            const V N2 = A::fma(kxz[ix], Ey[iy], kyz[iy] * Ex[ix]);
+#pragma unroll
+            for (int iz = 0; iz < 3; ++iz)
+                emit(ix + 3 * iy + 9 * iz, A::fma(P, Ez[iz], A::fma(Exy, kz2[iz == 1], A::fma(N2, Xz[iz], ez[iz]))));
+        }
+}
+
 // Weakly compressible equilibrium as deviations f_eq,i - w_i rho_ref (boundary cells,
 // initialisation)
 template <int D, typename T>

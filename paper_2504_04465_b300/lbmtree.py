@@ -477,9 +477,10 @@ class Context:
         _check(_lib.lbm_step_fine(self._h, n_fine), "lbm_step_fine")
 
     def variants(self) -> list[int]:
-        """Occupancy targets of the compiled step-kernel variants (0 = model default)."""
+        """Occupancy targets of the compiled step-kernel variants (0 = model default; 100 + target:
+        the interior blocks gathered directly instead of staged through shared memory)."""
         n = C.c_int()
-        mb = (C.c_int * 4)()
+        mb = (C.c_int * 8)()
         _check(_lib.lbm_variants(self._h, C.byref(n), mb), "lbm_variants")
         return list(mb[: n.value])
 
