@@ -804,18 +804,19 @@ k_step_batch(const StepArgs* __restrict__ args, const long long* __restrict__ of
 // Interior (simple and streaming) blocks of the D3Q27 regularized model in binary16 deviation
 // storage, with the pull staged in shared memory and two cells per thread.  A block's cells are
 // BY * BZ = 16 rows of 8 cells, and one row of one population is 16 bytes of storage, so the pull
-// of population q for the whole block is 16 row copies (cp.async, 16 bytes each), plus 16 more
-// from the x-neighbour block when xi_x != 0.  The staged region of q holds, per destination row:
-//   xi_x = +1: [row of the x-1 neighbour | own-side row]  (source x = lx - 1 at byte 14 + 2 lx)
-//   xi_x = -1: [own-side row | row of the x+1 neighbour]  (source x = lx + 1 at byte  2 + 2 lx)
-//   xi_x =  0: [own-side row]                             (source x = lx     at byte      2 lx)
-// ("own side": the row (ly - xi_y, lz - xi_z) of whichever block holds it), so every thread reads
-// its sources at fixed offsets from two shared-memory addresses.  A thread owns the x-neighbours
-// (2k, 2k + 1) of a row: the collision (rr_rel_q27) runs on both at once in packed FP32 pairs,
-// directly on the stored relative deviations, and each population of the pair is stored as one
-// 32-bit word.  A thread block takes NB cell blocks (a stride of the grid apart) in turn, with two
-// staging buffers: the rows of the next cell block and the neighbour list of the one after are
-// copied while the current one collides, so the copies' latency is hidden behind arithmetic.
+// of population q for the whole block is 16 row copies (cp.async, 16 bytes each): destination
+// row (ly, lz) receives the row (ly - xi_y, lz - xi_z) of whichever block holds it (its "own-side"
+// row).  When xi_x != 0 one cell of each row sources from the x-neighbour block: a 4-byte copy of
+// that neighbour's edge pair (elements 6, 7 of the x-1 neighbour for xi_x = +1, elements 0, 1 of
+// the x+1 neighbour for xi_x = -1) lands in a word per row after the 16 own-side rows.  Each
+// population's staged region is at a fixed offset, and each thread reads it at offsets fixed per
+// thread, so the gather is one shared-memory load per population and cell.  A thread owns the
+// x-neighbours (2k, 2k + 1) of a row: the collision (rr_rel_q27) runs on both at once in packed
+// FP32 pairs, directly on the stored relative deviations, and each population of the pair is
+// stored as one 32-bit word.  A thread block takes NB cell blocks (a stride of the grid apart) in
+// turn, with two staging buffers: the rows of the next cell block and the neighbour list of the one
+// after are copied while the current one collides, so the copies' latency is hidden behind
+// arithmetic.
 template <class M, int ST, int BX, int BY, int BZ>
 struct staged_f16 : std::bool_constant<ST == ST_F16DEV && M::D == 3 && M::Q == 27 && !M::HAS_G && !M::HAS_LAM &&
                                        M::DEV && M::RR && !hermite_weak<M>::value && weak_var<M>::value == 0 &&
@@ -830,9 +831,10 @@ __device__ __forceinline__ void cp_async4(unsigned smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// staged bytes of population q (16 rows of 16 or 32 bytes) and its offset in a staging buffer
+// staged bytes of population q (16 own-side rows of 16 bytes, and 16 edge words when xi_x != 0)
+// and its offset in a staging buffer
 template <class M>
-__host__ __device__ constexpr int stg_bytes(int q) { return M::cx(q) == 0 ? 256 : 512; }
+__host__ __device__ constexpr int stg_bytes(int q) { return M::cx(q) == 0 ? 256 : 320; }
 template <class M>
 __host__ __device__ constexpr int stg_off(int q) {
     int o = 0;
@@ -840,9 +842,9 @@ __host__ __device__ constexpr int stg_off(int q) {
     return o;
 }
 
-// Row copy of population Q for destination row r (y, z terms ty, tz of that row) and part p
-// (0: own side, 1: x-neighbour side, only for xi_x != 0); nbo: the 27 neighbour blocks' element
-// offsets.
+// Copy of population Q for destination row r (y, z terms ty, tz of that row) and part p
+// (0: the own-side row, 1: the x-neighbour's edge word, only for xi_x != 0); nbo: the 27
+// neighbour blocks' element offsets.
 template <class M, int BX, int BY, int BZ, int Q>
 __device__ __forceinline__ void stage_pop(const char* fsrc, const unsigned* nbo, unsigned sbase, int r, int p,
                                           const unsigned* ty, const unsigned* tz) {
@@ -852,9 +854,12 @@ __device__ __forceinline__ void stage_pop(const char* fsrc, const unsigned* nbo,
     // neighbour digit of x: 1 (own column of blocks) or 1 - xi_x (the x-neighbour, at -xi_x)
     const unsigned P = ((unsigned)(p ? 1 - cx : 1) << 20) + ty[cy + 1] + tz[cz + 1];
     const unsigned idx = nbo[P >> 20] + (unsigned)(Q * BS) + (P & 0xFFFFFu);
-    const unsigned dst = sbase + (unsigned)(stg_off<M>(Q) + r * (cx == 0 ? 16 : 32)) +
-                         ((cx != 0 && (p == 0) == (cx == 1)) ? 16u : 0u);
-    cp_async16(dst, fsrc + 2ull * idx);
+    if (p == 0) {
+        cp_async16(sbase + (unsigned)(stg_off<M>(Q) + r * 16), fsrc + 2ull * idx);
+    } else {
+        // elements 6, 7 of the x-1 neighbour's row (xi_x = +1) or 0, 1 of the x+1 neighbour's
+        cp_async4(sbase + (unsigned)(stg_off<M>(Q) + 256 + r * 4), fsrc + 2ull * (idx + (cx == 1 ? BX - 2 : 0)));
+    }
 }
 template <class M, int BX, int BY, int BZ, int NW, int W, int... I>
 __device__ __forceinline__ void stage_warp(std::integer_sequence<int, I...>, const char* fsrc, const unsigned* nbo,
@@ -866,10 +871,14 @@ __device__ __forceinline__ void stage_warp(std::integer_sequence<int, I...>, con
         ...);
 }
 
-// Eight resident thread blocks per SM (shared memory for eight; registers without spilling: nine
-// blocks spilled and ran slower).
+// The staged kernel's variants, by the occupancy code of the direct kernel they stand in for:
+// ten resident thread blocks per SM (96 registers, 16.6 KB of shared memory each) taking 4 (model
+// default), 8 (targets of 8 direct blocks) or 16 (6) cell blocks each.
+constexpr int staged_min_blocks(int) { return 10; }
+constexpr int staged_nb(int minb) { return minb == 8 ? 8 : (minb == 6 ? 16 : 4); }
+
 template <class M, int ST, int BX, int BY, int BZ, int MINB, int NB>
-__global__ void __launch_bounds__(BX * BY * BZ / 2, 8)
+__global__ void __launch_bounds__(BX * BY * BZ / 2, staged_min_blocks(MINB))
 k_step_staged(const StepArgs a) {
     constexpr int BS = BX * BY * BZ;
     constexpr int NT = BS / 2;                              // threads: two cells each
@@ -954,19 +963,24 @@ k_step_staged(const StepArgs a) {
             fg0 = t0 == C_FGHOST;
             fg1 = t1 == C_FGHOST;
         }
+        // byte offsets of the pair's sources within a population's staged region: xi_x = 0 (both),
+        // xi_x = +1 (x = 2k - 1: the edge word's upper half for k = 0; x = 2k), xi_x = -1 (x = 2k + 1;
+        // x = 2k + 2: the edge word's lower half for the last pair)
         const unsigned char* buf = stg[j & 1];
-        const unsigned char* s16 = buf + row * 16 + 2 * k2;    // populations with xi_x = 0
-        const unsigned char* s32 = buf + row * 32 + 2 * k2;    // the others
+        const int o0 = row * 16 + 2 * k2;
+        const int op0 = k2 == 0 ? 256 + row * 4 + 2 : o0 - 2, op1 = o0;
+        const int om0 = o0 + 2, om1 = k2 == BX - 2 ? 256 + row * 4 : o0 + 4;
         __half* out = (__half*)L.f[a.rd[lev] ^ 1];
         const long long base = b * (long long)(M::Q * BS) + l0;
         // fine ghosts stream purely: their staged values are stored as gathered
         if (streaming && ((work0 && fg0) || (work1 && fg1))) {
 #pragma unroll
             for (int q = 0; q < M::Q; ++q) {
-                const __half* sq = (const __half*)(M::cx(q) == 0 ? s16 + stg_off<M>(q)
-                                                                 : s32 + stg_off<M>(q) + (M::cx(q) == 1 ? 14 : 2));
-                if (work0 && fg0) out[base + q * BS] = sq[0];
-                if (work1 && fg1) out[base + q * BS + 1] = sq[1];
+                const unsigned char* sq = buf + stg_off<M>(q);
+                const int a0 = M::cx(q) == 0 ? o0 : (M::cx(q) == 1 ? op0 : om0);
+                const int a1 = M::cx(q) == 0 ? o0 + 2 : (M::cx(q) == 1 ? op1 : om1);
+                if (work0 && fg0) out[base + q * BS] = *(const __half*)(sq + a0);
+                if (work1 && fg1) out[base + q * BS + 1] = *(const __half*)(sq + a1);
             }
         }
         const bool c0 = work0 && !fg0, c1 = work1 && !fg1;
@@ -974,11 +988,12 @@ k_step_staged(const StepArgs a) {
             F2 h[M::Q];
 #pragma unroll
             for (int q = 0; q < M::Q; ++q) {
+                const unsigned char* sq = buf + stg_off<M>(q);
                 if (M::cx(q) == 0) {
-                    h[q].v = __half22float2(*(const __half2*)(s16 + stg_off<M>(q)));    // 4-byte aligned pair
+                    h[q].v = __half22float2(*(const __half2*)(sq + o0));    // 4-byte aligned pair
                 } else {
-                    const __half* sq = (const __half*)(s32 + stg_off<M>(q) + (M::cx(q) == 1 ? 14 : 2));
-                    h[q].v = make_float2(__half2float(sq[0]), __half2float(sq[1]));
+                    const int a0 = M::cx(q) == 1 ? op0 : om0, a1 = M::cx(q) == 1 ? op1 : om1;
+                    h[q].v = make_float2(__half2float(*(const __half*)(sq + a0)), __half2float(*(const __half*)(sq + a1)));
                 }
             }
             const bool both = c0 && c1;
@@ -1530,8 +1545,6 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_init_prestream(const StepArgs 
 }
 
 // ------------------------------------------------------------------ host launchers
-constexpr int STAGED_NB = 8;      // cell blocks per thread block of the staged binary16 kernel
-
 template <class M, int ST, int BX, int BY, int BZ>
 struct Launch {
     // DIRECT: the simple blocks gather straight from global memory also where a staged kernel exists
@@ -1540,8 +1553,8 @@ struct Launch {
         // interior sweep first; the few, latency-bound general blocks fill in as its blocks retire
         if (n_fast) {
             if constexpr (staged_f16<M, ST, BX, BY, BZ>::value && !DIRECT)
-                k_step_staged<M, ST, BX, BY, BZ, MINB_F, STAGED_NB>
-                    <<<(unsigned)((n_fast + STAGED_NB - 1) / STAGED_NB), BX * BY * BZ / 2, 0, s_fast>>>(a);
+                k_step_staged<M, ST, BX, BY, BZ, MINB_F, staged_nb(MINB_F)>
+                    <<<(unsigned)((n_fast + staged_nb(MINB_F) - 1) / staged_nb(MINB_F)), BX * BY * BZ / 2, 0, s_fast>>>(a);
             else
                 k_step<M, ST, BX, BY, BZ, true, MINB_F><<<(unsigned)n_fast, BX * BY * BZ, 0, s_fast>>>(a);
         }

@@ -296,46 +296,44 @@ __device__ __forceinline__ void rr_rel_q27(const V* h, float keep, Emit&& emit) 
             Kzz = kp * (Mzz - A::fma(Jz, uz, r3));
     const V Kxy = kp * A::fma(A::c(0.0f) - Jx, uy, Mxy), Kxz = kp * A::fma(A::c(0.0f) - Jx, uz, Mxz),
             Kyz = kp * A::fma(A::c(0.0f) - Jy, uz, Myz);
-    // per axis and component i = xi + 1: e', E' = 1 + e', X1'
-    V ex[3], Ex[3], Xx[3], ey[3], Ey[3], Xy[3], ez[3], Ez[3], Xz[3];
-    auto axis = [&](V u, V* e, V* E, V* X) {
-        const V a = A::c(3.0f) * (u * u), t3 = A::c(3.0f) * u;
-        e[0] = a - t3;
-        e[1] = a * A::c(-0.5f);
-        e[2] = a + t3;
-        E[0] = A::c(1.0f) + e[0];
-        E[1] = A::c(1.0f) + e[1];
-        E[2] = A::c(1.0f) + e[2];
-        X[0] = A::fma(A::c(2.0f), t3, A::c(-3.0f));
-        X[1] = A::c(0.0f) - t3;
-        X[2] = A::fma(A::c(2.0f), t3, A::c(3.0f));
+    // per axis and component i = xi + 1: e', E' = 1 + e', X1' (the x axis one component at a
+    // time, inside the loop below, which keeps fewer values live)
+    auto axis_i = [&](V a, V t3, int i, V& e, V& E, V& X) {
+        e = i == 0 ? a - t3 : (i == 1 ? a * A::c(-0.5f) : a + t3);
+        E = A::c(1.0f) + e;
+        X = i == 0 ? A::fma(A::c(2.0f), t3, A::c(-3.0f)) : (i == 1 ? A::c(0.0f) - t3 : A::fma(A::c(2.0f), t3, A::c(3.0f)));
     };
-    axis(ux, ex, Ex, Xx);
-    axis(uy, ey, Ey, Xy);
-    axis(uz, ez, Ez, Xz);
-    // K with the X2' and X1' factors of one axis folded in
-    const V kx2[2] = {Kxx * A::c(3.0f), Kxx * A::c(-1.5f)}, ky2[2] = {Kyy * A::c(3.0f), Kyy * A::c(-1.5f)},
-            kz2[2] = {Kzz * A::c(3.0f), Kzz * A::c(-1.5f)};
-    V kxy[3], kxz[3], kyz[3];
+    const V ax = A::c(3.0f) * (ux * ux), tx = A::c(3.0f) * ux;
+    const V ay = A::c(3.0f) * (uy * uy), t3y = A::c(3.0f) * uy;
+    const V az = A::c(3.0f) * (uz * uz), t3z = A::c(3.0f) * uz;
+    V ey[3], Ey[3], Xy[3], ez[3], Ez[3], Xz[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        kxy[i] = Kxy * Xx[i];
-        kxz[i] = Kxz * Xx[i];
-        kyz[i] = Kyz * Xy[i];
+        axis_i(ay, t3y, i, ey[i], Ey[i], Xy[i]);
+        axis_i(az, t3z, i, ez[i], Ez[i], Xz[i]);
     }
+    // K with the X2' and X1' factors of one axis folded in
+    const V ky2[2] = {Kyy * A::c(3.0f), Kyy * A::c(-1.5f)}, kz2[2] = {Kzz * A::c(3.0f), Kzz * A::c(-1.5f)};
+    V kyz[3];
 #pragma unroll
-    for (int ix = 0; ix < 3; ++ix)
+    for (int i = 0; i < 3; ++i) kyz[i] = Kyz * Xy[i];
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+        V exi, Exi, Xxi;
+        axis_i(ax, tx, ix, exi, Exi, Xxi);
+        const V kx2 = Kxx * A::c(ix == 1 ? -1.5f : 3.0f), kxy = Kxy * Xxi, kxz = Kxz * Xxi;
 #pragma unroll
         for (int iy = 0; iy < 3; ++iy) {
-            const V Exy = Ex[ix] * Ey[iy];
-            const V dE = A::fma(ex[ix], Ey[iy], ey[iy]);
-            const V N0 = A::fma(kx2[ix == 1], Ey[iy], A::fma(ky2[iy == 1], Ex[ix], kxy[ix] * Xy[iy]));
+            const V Exy = Exi * Ey[iy];
+            const V dE = A::fma(exi, Ey[iy], ey[iy]);
+            const V N0 = A::fma(kx2, Ey[iy], A::fma(ky2[iy == 1], Exi, kxy * Xy[iy]));
             const V P = A::fma(R, Exy, dE + N0);
-            const V N2 = A::fma(kxz[ix], Ey[iy], kyz[iy] * Ex[ix]);
+            const V N2 = A::fma(kxz, Ey[iy], kyz[iy] * Exi);
 #pragma unroll
             for (int iz = 0; iz < 3; ++iz)
                 emit(ix + 3 * iy + 9 * iz, A::fma(P, Ez[iz], A::fma(Exy, kz2[iz == 1], A::fma(N2, Xz[iz], ez[iz]))));
         }
+    }
 }
 
 // Weakly compressible equilibrium as deviations f_eq,i - w_i rho_ref (boundary cells,
