@@ -42,7 +42,7 @@ template <> struct Store<ST_F16DEV> {
     using T = float;
     using S = __half;
     template <bool DEV> static __device__ __forceinline__ T load(const void* p, long long i, T ref) {
-        const float h = __half2float(((const __half*)p)[i]);
+        const float h = __half2float(__ldg((const __half*)p + i));
         return DEV ? ref * h : ref * (1.0f + h);
     }
     template <bool DEV> static __device__ __forceinline__ void store(void* p, long long i, T v, T inv_ref) {
