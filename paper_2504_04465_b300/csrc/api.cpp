@@ -800,7 +800,7 @@ int lbm_build_grid(lbm_ctx* c, const int64_t extent[3], int n_levels, const lbm_
         // simple blocks; list 1: the general blocks
         std::vector<int32_t> lists[2];
         for (int64_t b = 0; b < lv.nb; ++b) {
-            if (lv.bflag[b]) lists[0].push_back((int32_t)(2 * b + (lv.bflag[b] == 2 ? 1 : 0)));
+            if (lv.bflag[b]) lists[0].push_back((int32_t)(4 * b + (lv.bflag[b] >= 2 ? 1 : 0) + (lv.bflag[b] == 3 ? 2 : 0)));
             else lists[1].push_back((int32_t)b);
         }
         for (int k = 0; k < 2; ++k) {

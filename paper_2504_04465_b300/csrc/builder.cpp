@@ -14,6 +14,8 @@
 // the finer level; such a child enters the coalescence with the ghost's own streamed
 // population, which keeps the coupling conservative there too (record flag b bit 0).  Boundary layers are the `reach` outer layers on non-periodic faces (Appendix A.3); a
 // boundary cell's partner is the cell obtained by clamping its coordinates into the interior.
+// Blocks whose only special cells are fine ghosts, absent slots and Neumann boundary cells with
+// their partner in the block are streaming blocks of the interior kernels.
 // A link is blocked by a solid when any cell met on the lattice segment is solid, taking both
 // roundings where the segment passes between cells.
 #include "builder.h"
@@ -494,12 +496,14 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
             if (lv.bflag[b]) continue;
             int tid = omp_get_thread_num();
             bool simple = true;
-            bool stream = true;     // only record-free fluid cells, fine ghosts and absent slots
+            // only record-free fluid cells, fine ghosts, absent slots and Neumann boundary cells
+            // whose partner lies in the block (the interior kernels pull those at the partner)
+            bool stream = true, neumann = false;
             for (int l = 0; l < BS; ++l) {
                 int64_t cell = b * BS + l;
                 uint8_t t = lv.type[cell];
                 if (t != C_FLUID) simple = false;
-                if (!(t == C_FLUID || t == C_FGHOST || t == C_ABSENT)) stream = false;
+                if (!(t == C_FLUID || t == C_FGHOST || t == C_ABSENT || t == C_BC)) stream = false;
                 if (t == C_ABSENT || t == C_SOLID) continue;
                 int lx = l % g.B[0], ly = (l / g.B[0]) % g.B[1], lz = l / (g.B[0] * g.B[1]);
                 int64_t c[3] = {int64_t(lv.bxyz[3 * b]) * g.B[0] + lx, int64_t(lv.bxyz[3 * b + 1]) * g.B[1] + ly,
@@ -602,10 +606,11 @@ std::string build_grid(const GridInput& in, BuiltGrid& out) {
                 }
                 if (need) {
                     trec[tid].push_back({cell, r});
-                    stream = false;
+                    if (t == C_BC && in.faces[r.b >> 4].kind == BCK_NEUMANN && r.a / BS == b) neumann = true;
+                    else stream = false;
                 }
             }
-            lv.bflag[b] = simple ? 1 : (stream ? 2 : 0);
+            lv.bflag[b] = simple ? 1 : (stream ? (neumann ? 3 : 2) : 0);
         }
         for (auto& e : errs)
             if (!e.empty()) return e + " (level " + std::to_string(i) + ")";

@@ -18,7 +18,7 @@ struct LevelDev {
     long long ncell;         // nb * BS: SoA stride
     const int* nbr;          // nb * 27
     const unsigned char* type;
-    const unsigned char* bflag;   // 1 simple, 2 streaming, 0 general
+    const unsigned char* bflag;   // 1 simple, 2 streaming, 3 streaming with Neumann boundary cells, 0 general
     const int* rec_id;
     const CellRecDev* recs;
     void* f[2];
@@ -31,7 +31,8 @@ struct LevelDev {
     float omega_m_f;
     const int* bxyz;         // block coordinates (3 per block), for position-dependent terms
     int shape[3];            // cells per axis of the level
-    const int* blist[2];     // [0] 2 * block + s: simple (s = 0) and streaming (s = 1) blocks, [1] the others
+    const int* blist[2];     // [0] 4 * block + s: simple (s = 0), streaming (s = 1) and streaming blocks with
+                             // Neumann boundary cells (s = 3), [1] the others
                              // (block nb of f/g holds zero populations: the missing-neighbour stand-in)
     long long nlist[2];
 };

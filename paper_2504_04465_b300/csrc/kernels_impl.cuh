@@ -618,10 +618,10 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
     const int lev = find_level_list(a, FAST ? 0 : 1, bid, &i);
     const LevelDev& L = a.lv[lev];
     const int entry = L.blist[FAST ? 0 : 1][i];
-    // FAST list entries carry a streaming-block bit: such blocks hold fine ghosts and absent
-    // slots besides record-free fluid cells, so the cell types are read and a missing
-    // neighbour block reads the zero-population block nb
-    const long long b = FAST ? (long long)(entry >> 1) : (long long)entry;
+    // FAST list entries carry a streaming-block bit: such blocks hold fine ghosts, absent slots
+    // and Neumann boundary cells (partner in the block) besides record-free fluid cells, so the
+    // cell types are read and a missing neighbour block reads the zero-population block nb
+    const long long b = FAST ? (long long)(entry >> 2) : (long long)entry;
     const bool streaming = FAST && (entry & 1);
     const int l = threadIdx.x;
     // element offset of each neighbour block's populations (the zero block for a missing one)
@@ -665,10 +665,19 @@ __device__ __forceinline__ void step_block(const StepArgs& a, long long bid, int
         // fluid cells without a record (no bounce-back link) have every source live: gather
         // them branch-free also inside the general blocks
         if (FAST || (type == C_FLUID && L.rec_id[cell] < 0)) {
-            gather_fast<M, ST, BX, BY, BZ>(L, rd, l, nboff_s, a.m, c);
+            // a Neumann boundary cell of an interior block pulls at its partner, which lies in
+            // the block (Appendix A.3: the partner's streamed state, multipliers included)
+            long long src = cell;
+            int ls = l;
+            if (FAST && (entry & 2) && type == C_BC) {
+                src = L.recs[L.rec_id[cell]].a;
+                ls = int(src - b * BS);
+                __builtin_assume(ls >= 0 && ls < BS);
+            }
+            gather_fast<M, ST, BX, BY, BZ>(L, rd, ls, nboff_s, a.m, c);
             if constexpr (M::HAS_LAM) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + cell];
+                for (int j = 0; j < 8; ++j) c.lam[j] = L.lam[((long long)rd * 8 + j) * L.ncell + src];
             }
         } else if constexpr (!FAST) {
             assemble<M, ST, BX, BY, BZ, MODE_STEP>(a, lev, b, l, type, false, nbr_s, c, &conv, stage_ptr(sx));
@@ -816,7 +825,8 @@ k_step_batch(const StepArgs* __restrict__ args, const long long* __restrict__ of
 // stored as one 32-bit word.  A thread block takes NB cell blocks (a stride of the grid apart) in
 // turn, with two staging buffers: the rows of the next cell block and the neighbour list of the one
 // after are copied while the current one collides, so the copies' latency is hidden behind
-// arithmetic.
+// arithmetic.  A Neumann boundary cell pulls its partner's populations, so it receives the
+// partner's stored result after a block barrier (only in blocks whose list entry has bit 1).
 template <class M, int ST, int BX, int BY, int BZ>
 struct staged_f16 : std::bool_constant<ST == ST_F16DEV && M::D == 3 && M::Q == 27 && !M::HAS_G && !M::HAS_LAM &&
                                        M::DEV && M::RR && !hermite_weak<M>::value && weak_var<M>::value == 0 &&
@@ -909,7 +919,7 @@ k_step_staged(const StepArgs a) {
         lev_s[t] = lev;
     }
     __syncthreads();
-    auto nbr_src = [&](int j) { return a.lv[lev_s[j]].nbr + (long long)(ent_s[j] >> 1) * 27 + t; };
+    auto nbr_src = [&](int j) { return a.lv[lev_s[j]].nbr + (long long)(ent_s[j] >> 2) * 27 + t; };
     if (t < 27) nbr3[0][t] = *nbr_src(0);
     if (NB > 1 && t < 27 && slot_ok(1)) cp_async4((unsigned)__cvta_generic_to_shared(&nbr3[1][t]), nbr_src(1));
     unsigned ty[3], tz[3];
@@ -952,16 +962,18 @@ k_step_staged(const StepArgs a) {
         // collide slot j from buffer j & 1
         const int lev = lev_s[j];
         const LevelDev& L = a.lv[lev];
-        const long long b = (long long)(ent_s[j] >> 1);
+        const long long b = (long long)(ent_s[j] >> 2);
         const bool streaming = ent_s[j] & 1;
         const long long cell = b * BS + l0;
-        bool work0 = true, work1 = true, fg0 = false, fg1 = false;
+        bool work0 = true, work1 = true, fg0 = false, fg1 = false, bc0 = false, bc1 = false;
         if (streaming) {
             const int t0 = L.type[cell], t1 = L.type[cell + 1];
             work0 = !(t0 == C_ABSENT || t0 == C_SOLID || (t0 == C_FGHOST && a.sync_fg[lev]));
             work1 = !(t1 == C_ABSENT || t1 == C_SOLID || (t1 == C_FGHOST && a.sync_fg[lev]));
             fg0 = t0 == C_FGHOST;
             fg1 = t1 == C_FGHOST;
+            bc0 = t0 == C_BC;
+            bc1 = t1 == C_BC;
         }
         // byte offsets of the pair's sources within a population's staged region: xi_x = 0 (both),
         // xi_x = +1 (x = 2k - 1: the edge word's upper half for k = 0; x = 2k), xi_x = -1 (x = 2k + 1;
@@ -983,7 +995,7 @@ k_step_staged(const StepArgs a) {
                 if (work1 && fg1) out[base + q * BS + 1] = *(const __half*)(sq + a1);
             }
         }
-        const bool c0 = work0 && !fg0, c1 = work1 && !fg1;
+        const bool c0 = work0 && !fg0 && !bc0, c1 = work1 && !fg1 && !bc1;
         if (c0 || c1) {
             F2 h[M::Q];
 #pragma unroll
@@ -1005,6 +1017,19 @@ k_step_staged(const StepArgs a) {
                     if (c1) out[base + q * BS + 1] = __float2half_rn(v.v.y);
                 }
             });
+        }
+        // Neumann boundary cells (Appendix A.3) pull the partner's populations, in the block,
+        // so their collided state is the partner's: copied once every partner has been stored
+        if (ent_s[j] & 2) {
+            __syncthreads();
+#pragma unroll 1
+            for (int i = 0; i < 2; ++i) {
+                if (!(i ? bc1 : bc0)) continue;
+                const long long P = L.recs[L.rec_id[cell + i]].a;
+                const long long pb = b * (long long)(M::Q * BS) + (P - b * BS);
+#pragma unroll
+                for (int q = 0; q < M::Q; ++q) out[base + q * BS + i] = out[pb + q * BS];
+            }
         }
     }
     cp_async_wait_all();
