@@ -49,59 +49,59 @@ CSRC = os.path.join(ROOT, "paper_2504_04465_b300", "csrc")
 #          FP32 pairs 2 fadd2 + 2 fmul2 + 4 ffma2, and the same for FP64), both step kernels,
 #          one coarse step of the captured case
 COUNTERS = {
-    ('d2q13n32:band', "flops"): {"value": 4595.7, "source_hash": '219c743cc6075784',
+    ('d2q13n32:band', "flops"): {"value": 4595.7, "source_hash": '6306a43a84286b15',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 2.07 Newton iterations per update'},
-    ('d2q13n32:sqr', "flops"): {"value": 4355.5, "source_hash": '219c743cc6075784',
+    ('d2q13n32:sqr', "flops"): {"value": 4355.5, "source_hash": '6306a43a84286b15',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.92 Newton iterations per update'},
-    ('d2q13n32:unif', "flops"): {"value": 3137.4, "source_hash": '219c743cc6075784',
+    ('d2q13n32:unif', "flops"): {"value": 3137.4, "source_hash": '6306a43a84286b15',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.29 Newton iterations per update'},
-    ('d2q21n32:band', "flops"): {"value": 4005.8, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:band', "flops"): {"value": 4006.0, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.15 Newton iterations per update'},
-    ('d2q21n32:riemann_axes', "flops"): {"value": 2905.7, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:riemann_axes', "flops"): {"value": 2905.7, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of the step kernels over one coarse step of the 2D Riemann configuration 12 on the axes grid at N_c = 256 from the eighth coarse step, 0.73 Newton iterations per update'},
-    ('d2q21n32:riemann_diag', "flops"): {"value": 2444.7, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:riemann_diag', "flops"): {"value": 2444.7, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of the step kernels over one coarse step of the 2D Riemann configuration 12 on the diag grid at N_c = 256 from the eighth coarse step, 0.54 Newton iterations per update'},
-    ('d2q21n32:riemann_optim', "flops"): {"value": 2741.9, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:riemann_optim', "flops"): {"value": 2741.9, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of the step kernels over one coarse step of the 2D Riemann configuration 12 on the optim grid at N_c = 256 from the eighth coarse step, 0.65 Newton iterations per update'},
-    ('d2q21n32:sqr', "flops"): {"value": 3778.0, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:sqr', "flops"): {"value": 3778.2, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.07 Newton iterations per update'},
-    ('d2q21n32:unif', "flops"): {"value": 2879.7, "source_hash": '5c4e0c290ce4f533',
+    ('d2q21n32:unif', "flops"): {"value": 2880.1, "source_hash": 'c6ba864d30f43d25',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 0.68 Newton iterations per update'},
-    ('d2q21n64:poly', "flops"): {"value": 37858.4, "source_hash": '67a4f07126148d6c',
+    ('d2q21n64:poly', "flops"): {"value": 37858.4, "source_hash": 'e195a62c6c1fc144',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256, Mach 1.5, after 3 coarse steps, 11.74 Newton iterations per update'},
-    ('d2q21n64:warm', "flops"): {"value": 8578.6, "source_hash": '67a4f07126148d6c',
+    ('d2q21n64:warm', "flops"): {"value": 8578.6, "source_hash": 'e195a62c6c1fc144',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256, Mach 1.5, after 3 coarse steps, 2.66 Newton iterations per update'},
-    ('d2q21w:f32', "flops"): {"value": 546.0, "source_hash": '02f2d417967f05d6',
+    ('d2q21w:f32', "flops"): {"value": 546.0, "source_hash": '9de5e6796561a88c',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 1024^2 shear layer'},
-    ('d2q37n32:band', "flops"): {"value": 6318.2, "source_hash": '8844617ab13a343b',
+    ('d2q37n32:band', "flops"): {"value": 6318.2, "source_hash": 'a8312b3c4a57c778',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.13 Newton iterations per update'},
-    ('d2q37n32:sqr', "flops"): {"value": 5964.2, "source_hash": '8844617ab13a343b',
+    ('d2q37n32:sqr', "flops"): {"value": 5964.3, "source_hash": 'a8312b3c4a57c778',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 1.04 Newton iterations per update'},
-    ('d2q37n32:unif', "flops"): {"value": 4487.4, "source_hash": '8844617ab13a343b',
+    ('d2q37n32:unif', "flops"): {"value": 4487.5, "source_hash": 'a8312b3c4a57c778',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 2048^2 Sod tube from t = 0.1 L / c_s, 0.63 Newton iterations per update'},
-    ('d2q37p:naca_f32', "flops"): {"value": 961.5, "source_hash": 'd3649c240531cec4',
+    ('d2q37p:naca_f32', "flops"): {"value": 961.5, "source_hash": '93aef3942399df86',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256'},
-    ('d2q37p:naca_f64', "flops"): {"value": 1361.6, "source_hash": 'd3649c240531cec4',
+    ('d2q37p:naca_f64', "flops"): {"value": 1361.6, "source_hash": '93aef3942399df86',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 5-level NACA0012 grid at chord 256'},
-    ('d2q37p:sod_f32', "flops"): {"value": 1095.0, "source_hash": 'd3649c240531cec4',
+    ('d2q37p:sod_f32', "flops"): {"value": 1095.0, "source_hash": '93aef3942399df86',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 4096x64 Sod tube'},
-    ('d2q37p:sod_f64', "flops"): {"value": 1661.2, "source_hash": 'd3649c240531cec4',
+    ('d2q37p:sod_f64', "flops"): {"value": 1661.2, "source_hash": '93aef3942399df86',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the 4096x64 Sod tube'},
-    ('d2q9:f32', "flops"): {"value": 243.0, "source_hash": 'fa0b51c44d37ed80',
+    ('d2q9:f32', "flops"): {"value": 243.0, "source_hash": '8883843697529bb4',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 2048^2 Taylor-Green grid'},
-    ('d2q9:f64', "flops"): {"value": 253.0, "source_hash": 'fa0b51c44d37ed80',
+    ('d2q9:f64', "flops"): {"value": 253.0, "source_hash": '8883843697529bb4',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of a uniform periodic 2048^2 Taylor-Green grid'},
-    ('d3q27:f16dev', "dram"): {"value": 113.3, "source_hash": '17104c1060914ae1',
+    ('d3q27:f16dev', "dram"): {"value": 113.3, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
-    ('d3q27:f16dev', "flops"): {"value": 468.7, "source_hash": '17104c1060914ae1',
+    ('d3q27:f16dev', "flops"): {"value": 468.7, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2, packed FP32-pair FADD2/FMUL2/FFMA2 as 2/2/4) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
-    ('d3q27:f32', "dram"): {"value": 225.4, "source_hash": '17104c1060914ae1',
+    ('d3q27:f32', "dram"): {"value": 225.4, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
-    ('d3q27:f32', "flops"): {"value": 612.5, "source_hash": '17104c1060914ae1',
+    ('d3q27:f32', "flops"): {"value": 612.5, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, executed FP32 FADD/FMUL/FFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
-    ('d3q27:f64', "dram"): {"value": 447.1, "source_hash": '17104c1060914ae1',
+    ('d3q27:f64', "dram"): {"value": 447.1, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, dram__bytes_read.sum + dram__bytes_write.sum of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
-    ('d3q27:f64', "flops"): {"value": 621.8, "source_hash": '17104c1060914ae1',
+    ('d3q27:f64', "flops"): {"value": 621.8, "source_hash": 'df291c05bd403b18',
                    "capture": 'ncu, executed FP64 DADD/DMUL/DFMA thread instructions (FMA as 2) of both step kernels over one coarse step of the D3Q27 sphere at half extents (512x256x256, 5.68 M cells)'},
 }
 
