@@ -276,3 +276,19 @@ def test_aa_streaming_arguments(lt):
     c = lt.Context(2, device=-1)
     with pytest.raises(lt.LbmError):
         lt._check(lt._lib.lbm_set_streaming(c._h, 7), "lbm_set_streaming")    # unknown mode
+
+
+def test_neumann_end_blocks_are_interior_blocks():
+    """Blocks whose only boundary cells are Neumann cells with their partner in the block run in
+    the interior kernel (list entries with the streaming bit): a Sod tube with Neumann ends has
+    no general block; imposing the density at one end makes that end's blocks general."""
+    from paper_2504_04465_b300 import lbmtree as lt
+    ny = 32
+    c = lt.Context(2, device=-1)
+    c.configure(I.sod_spec(256, ny), "D2Q37", "poly_ddf", "f32", nu0=0.0, sensor_A=1.5)
+    assert c.stats().n_general_blocks[0] == 0
+    spec = I.GridSpec(2, (256, ny), 1, [], (False, True),
+                      {"x-": ("dirichlet_rho", 1.0, (0.05, 0.0, 0.0), 0.0), "x+": ("neumann",)})
+    c2 = lt.Context(2, device=-1)
+    c2.configure(spec, "D2Q37", "poly_ddf", "f32", nu0=0.0, sensor_A=1.5)
+    assert c2.stats().n_general_blocks[0] == ny // 16

@@ -112,3 +112,35 @@ def test_ten_coarse_steps_within_binary16_error():
     ra, ua, _ = a.moments()
     rb, ub, _ = b.moments()
     assert H.rel_l2(ra, rb) < 1e-4 and H.rel_l2(ua, ub) < 2e-3
+
+
+# Neumann faces across y: their boundary cells' partners sit in other threads of the block, so
+# the staged kernel hands the partner's result over through a block barrier
+D3_YN_SPEC = I.GridSpec(3, (64, 32, 32), 2, [(0, (16, 8, 8), (48, 24, 24))], (False, False, True),
+                        {"x-": ("dirichlet_rho", 1.0, (0.04, 0.0, 0.0)), "x+": ("neumann",),
+                         "y-": ("neumann",), "y+": ("neumann",)},
+                        [{"kind": "sphere", "center": (32.0, 16.0, 16.0), "radius": 4.0}])
+
+
+@pytest.mark.parametrize("n_fine", [1, 4])
+def test_neumann_faces_across_y(n_fine):
+    _agreement(D3_YN_SPEC, d3_fields, 0.01, 86, n_fine)
+
+
+def test_neumann_faces_across_y_against_oracle():
+    sol = H.run_oracle(D3_YN_SPEC, "D3Q27", "rr", d3_fields, 2 * 6, nu0=0.01)
+    ctx = _ctx(D3_YN_SPEC, d3_fields, 0.01, 86)
+    ctx.step(6)
+    err = H.compare_moments(sol, ctx)
+    assert err["rho"] < 3e-2 and err["u"] < 3e-2, err
+    # a Neumann boundary cell of the y- face (coarse level, away from the x faces) holds its
+    # partner's state exactly: the same binary16 bits
+    lv, xyz, ty = ctx.cells()
+    f = ctx.populations("f")
+    m = (lv == 1) & (xyz[:, 1] == 0) & (xyz[:, 0] >= 4) & (xyz[:, 0] < 28)
+    key = {(int(a), int(b), int(c), int(d)): i for i, (a, (b, c, d)) in enumerate(zip(lv, xyz))}
+    idx = np.nonzero(m)[0]
+    assert idx.size > 0
+    for i in idx:
+        j = key[(1, int(xyz[i, 0]), 1, int(xyz[i, 2]))]
+        assert np.array_equal(f[:, i], f[:, j])
