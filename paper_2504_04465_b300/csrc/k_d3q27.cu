@@ -13,7 +13,7 @@ template <bool RR_, int VAR_ = WV_PLAIN> struct D3Q27M {
     // resident 128-thread blocks per SM the step kernels are compiled for (simple / other blocks)
     static constexpr int MINB_FAST = 6, MINB_GEN = 6;
     static constexpr bool TUNE = VAR_ == WV_PLAIN;   // compile occupancy variants for the autotuner
-    static constexpr int TUNE_V[3] = {84, 86, 66};   // their targets, 10 * interior + general
+    static constexpr int TUNE_V[3] = {88, 86, 66};   // their targets, 10 * interior + general
     static constexpr bool BATCH = false; // compile the batched multi-case launch
     static constexpr bool DEV = true;
     static constexpr bool HAS_G = false, HAS_LAM = false, RR = RR_;

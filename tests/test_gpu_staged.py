@@ -81,7 +81,7 @@ def test_variant_codes():
     assert all(c < 100 for c in ctx32.variants())
 
 
-@pytest.mark.parametrize("code", [0, 86])
+@pytest.mark.parametrize("code", [0, 86, 88])
 @pytest.mark.parametrize("n_fine", [1, 4])
 def test_two_level_sphere(code, n_fine):
     _agreement(D3_SPEC, d3_fields, 0.01, code, n_fine)
