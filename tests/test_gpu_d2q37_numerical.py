@@ -154,7 +154,10 @@ def test_learned_guess_on_d2q37():
     at high Mach numbers): a network trained by the project's kernels on equilibria of a D2Q37
     run reaches the same roots as the zero guess in fewer iterations than the polynomial guess,
     and the solver run from it equals the oracle's run from the same network (1e-12) and the
-    oracle's polynomial-guess run within the Newton tolerance accumulated over the run (1e-11)."""
+    oracle's polynomial-guess run within the Newton tolerance accumulated over the run: solves
+    from different guesses stop at different iterates within the residual tolerance 1e-12, so
+    the two runs may part by up to that much per fine iteration, 3e-11 over the 30 iterations
+    (the GPU training is not bitwise reproducible, and its networks gave 0.4e-11 to 1.9e-11)."""
     from oracle import mlp
     from tests.test_gpu_mlp import unflat
     from tests.test_gpu_parity import SUP_SPEC, sup_fields
@@ -202,5 +205,5 @@ def test_learned_guess_on_d2q37():
     assert err["rho"] < 1e-12 and err["u"] < 1e-12 and err["T"] < 1e-12, err
     sol_poly = H.run_oracle(SUP_SPEC, "D2Q37", "num_ddf", sup_fields, 30, guess="poly", **kw)
     err = H.compare_moments(sol_poly, g)
-    assert err["rho"] < 1e-11 and err["u"] < 1e-11 and err["T"] < 1e-11, err
+    assert err["rho"] < 3e-11 and err["u"] < 3e-11 and err["T"] < 3e-11, err
     g.close()
